@@ -1,0 +1,70 @@
+"""One-call oracle: S_k(A) (or the radix-15 framework result) in FP64 on the CPU.
+
+radix 1  naive (Sec. 2.1)
+radix 2  repeated squaring for k = 2^t, binary digits of k otherwise (Sec. 2.1)
+radix 3, 5, 9  exact radix-m splitting with kernels T_3, T_5, T_9 (Sec. 2.2, Thm 3.1)
+radix 15 residual framework with the approximate T~_15 (Sec. 5.3, App. B)
+radix 0  exact kernels over the factorisation of k into 9, 5, 3 and 2 (block
+         concatenation holds for any factor order, Sec. 2.2)
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import circuits as C
+from . import radix15 as R15
+from . import schemes as SC
+
+
+def kernels(coef15: str = "refined") -> dict:
+    coef = R15.load_refined(float) if coef15 == "refined" else R15.printed(float)
+    return {2: C.kernel_t2, 3: C.kernel_t3, 5: C.kernel_t5, 9: C.kernel_t9,
+            15: C.kernel_t15(coef)}
+
+
+def auto_levels(k: int) -> list:
+    """Factor k over {9, 5, 3, 2}: a 9 for each pair of 3s, then 5s, a lone 3, 2s."""
+    levels, q = [], k
+    for m in (9, 5, 3, 2):
+        while q % m == 0:
+            levels.append(m)
+            q //= m
+    if q != 1:
+        raise ValueError(f"k={k} has a prime factor above 5")
+    return levels
+
+
+def evaluate(A: np.ndarray, k: int, radix: int, coef15: str = "refined",
+             form: str = "paper"):
+    """Returns (result, products executed)."""
+    A = np.asarray(A, dtype=np.float64)
+    alg = C.matrix_algebra(A.shape[0])
+    ks = kernels(coef15)
+    if radix == 1:
+        S = SC.naive(A, k, alg)
+    elif radix == 2:
+        S = SC.binary_pow2(A, k, alg) if k & (k - 1) == 0 else SC.binary_exact(A, k, alg)
+    elif radix in (3, 5, 9):
+        S = SC.radix_exact(A, SC.pure_levels(k, radix), ks, alg)
+    elif radix == 15:
+        S = SC.radix_residual(A, SC.pure_levels(k, 15), ks, alg, form)
+    elif radix == 0:
+        S = SC.radix_exact(A, auto_levels(k), ks, alg)
+    else:
+        raise ValueError(f"radix {radix}")
+    return np.asarray(S, dtype=np.float64), alg.products
+
+
+def planted_reference(V, lam, k: int, radix: int, coef15: str = "refined", rows=None):
+    """Closed form on a planted symmetric spectrum (closed_form.py): S_k for the
+    exact schemes, Y_t of Lemma 5.7 for radix 15. `rows` selects rows only."""
+    from . import closed_form as CF
+
+    if radix == 15:
+        f = CF.radix_scalar(lam, SC.pure_levels(k, 15), kernels(coef15))
+    else:
+        f = CF.sk_scalar(lam, k)
+    if rows is None:
+        return CF.symmetric_function(V, lam, f)
+    return CF.symmetric_function_rows(V, lam, f, rows)

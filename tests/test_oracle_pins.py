@@ -1,0 +1,354 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/*.json), exact identities over the rationals,
+closed forms, brute force on tiny inputs, or a library routine.
+"""
+
+import math
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+
+from oracle import circuits as C
+from oracle import closed_form as CF
+from oracle import counts as CT
+from oracle import evaluate as EV
+from oracle import radix15 as R15
+from oracle import schemes as SC
+from oracle.poly import Poly
+from workloads import generators as G
+
+
+def _exact_poly_alg(deg):
+    return C.poly_algebra(deg)
+
+
+# ---------------------------------------------------------------- kernels
+
+def test_t9_is_exact_rational_identity():
+    """Thm 3.1: T_9(B) = I + B + ... + B^8 exactly, in 3 products."""
+    alg = _exact_poly_alg(24)
+    T = C.kernel_t9(Poly.z(24), alg)
+    assert alg.products == 3
+    assert T.coeffs(24) == [1] * 9 + [0] * 16
+    assert all(isinstance(c, (int, F)) for c in T.c.values())
+
+
+def test_t9_proof_vectors(golden):
+    """Proof of Thm 3.1: with p, q over B..B^4, p*q has coefficient 1 at B^5..B^8,
+    and the U, V corrections make B^2..B^4 equal to 1."""
+    g = golden("paper_radix9.json")
+    p = [F(0)] + [F(s) for s in g["p_in_powers_B1_to_B4"]]
+    q = [F(0)] + [F(s) for s in g["q_in_powers_B1_to_B4"]]
+    assert [float(x) for x in p[1:]] == g["p_decimal"]
+    assert [float(x) for x in q[1:]] == g["q_decimal"]
+    w = [sum(p[i] * q[d - i] for i in range(max(0, d - 4), min(d, 4) + 1)) for d in range(9)]
+    assert w[5:] == [1, 1, 1, 1]
+    cu, cv = F(g["U_coefficient"]), F(g["V_coefficient"])
+    assert float(cu) == g["U_coefficient_decimal"] and float(cv) == g["V_coefficient_decimal"]
+    vv = [F(0)] + [F(x) for x in g["V_in_powers_B1_to_B4"]]  # V = B^3 + 2 B^4
+    total = [w[d] + (1 if d in (0, 1) else 0) + (cu if d == 2 else 0) + cv * (vv[d] if d <= 4 else 0)
+             for d in range(9)]
+    assert total == [1] * 9
+
+
+def test_t5_exact():
+    """App. A.1: quinary kernel, 2 products, all five coefficients 1."""
+    alg = _exact_poly_alg(12)
+    T = C.kernel_t5(Poly.z(12), alg)
+    assert alg.products == 2 and T.coeffs(12) == [1] * 5 + [0] * 8
+
+
+def test_t3_t2_and_naive_kernels_exact():
+    for kern, m, mu in ((C.kernel_t2, 2, 0), (C.kernel_t3, 3, 1), (C.kernel_naive(7), 7, 5)):
+        alg = _exact_poly_alg(10)
+        T = kern(Poly.z(10), alg)
+        assert alg.products == mu and T.coeffs(10) == [1] * m + [0] * (11 - m)
+
+
+def test_mu_matches_lower_bound(golden):
+    """Sec. 2.2 lower bound mu_m >= ceil(log2(m-1)) is attained by T_5, T_9, T~_15."""
+    g = golden("paper_coefficients.json")
+    for m in (5, 9, 15):
+        assert C.MU[m] == math.ceil(math.log2(m - 1)) == g["lower_bound"][str(m)]
+    assert {str(k): v for k, v in C.MU.items()} == g["mu"]
+
+
+# ---------------------------------------------------------------- radix 15
+
+def test_radix15_printed_transcription(golden):
+    g = golden("paper_radix15.json")["printed"]
+    pr = R15.printed(float)
+    for name, _ in R15.LAYOUT:
+        assert pr[name] == pytest.approx(g[name], abs=0), name
+
+
+def test_radix15_refined_rounds_to_printed(golden):
+    """The refined solution is the paper's kernel: each of the 28 values is within
+    the three-decimal rounding (plus 1e-4) of the printed one (App. B)."""
+    g = golden("paper_radix15.json")["printed"]
+    ref = R15.load_refined(float)
+    for name, _ in R15.LAYOUT:
+        assert np.max(np.abs(np.array(ref[name]) - np.array(g[name]))) < 6e-4, name
+
+
+def test_radix15_printed_prefix_error_reading():
+    """Reading: at three decimals the printed circuit has prefix error ~2.8e-3,
+    far above the claimed 9e-7, so the printed values are a rounding."""
+    val = R15.circuit_poly(R15.flatten(R15.printed(float)))
+    err = max(abs(v) for v in R15.prefix_residual(val))
+    assert 2e-3 < err < 4e-3
+
+
+def test_radix15_refined_float_prefix(golden):
+    """Refined circuit in float64: prefix 1 to rounding; spillover as in Sec. 4.2."""
+    g = golden("paper_radix15.json")
+    val = R15.circuit_poly(R15.flatten(R15.load_refined(float)))
+    assert max(abs(v) for v in R15.prefix_residual(val)) < 1e-14
+    assert abs(val[15] - g["spillover_15"]) < 1e-3
+    assert abs(val[16] - g["spillover_16"]) < 1e-3
+    assert abs((1 - val[15]) - g["c_approx"]) < 1e-2
+
+
+def test_radix15_refined_multiprecision(golden):
+    """Refined circuit run through kernel_t15 on mpmath polynomials: prefix error
+    < 1e-30 (well inside the claimed 9e-7), degree exactly 16."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    coef = R15.load_refined(mp.mpf)
+    alg = C.poly_algebra(20, num=lambda q: mp.mpf(q.numerator) / q.denominator)
+    T = C.kernel_t15(coef)(Poly.z(20, mp.mpf(1)), alg)
+    assert alg.products == 4
+    cs = T.coeffs(20)
+    assert max(abs(c - 1) for c in cs[:15]) < 1e-30
+    assert all(abs(c) < 1e-40 for c in cs[17:])
+    assert abs(cs[16]) > 0.4
+    assert max(abs(c - 1) for c in cs[:15]) < golden("paper_radix15.json")["claimed_prefix_error_bound"]
+
+
+def test_radix15_stored_file_reproducible():
+    """The stored refined set is what the committed refinement script produces."""
+    mp = pytest.importorskip("mpmath")
+    xm, rep = R15.refine()
+    stored = R15.flatten(R15.load_refined(mp.mpf))
+    assert max(abs(a - b) for a, b in zip(xm, stored)) < mp.mpf(10) ** -40
+    assert rep["prefix_error"] < mp.mpf(10) ** -50
+
+
+def test_lemma_5_6_leading_coefficient():
+    """Lemma 5.6 (error propagation): E^[2](z) = c^{16} z^{225} + O(z^226) with
+    c = 1 - [T~15]_15; Lemma 5.7: Y_2 matches (1-z)^{-1} through degree 224.
+    Checked on the matrix scheme run over mpmath polynomials."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    deg = 226
+    coef = R15.load_refined(mp.mpf)
+    num = lambda q: mp.mpf(q.numerator) / q.denominator  # noqa: E731
+    alg = C.poly_algebra(deg, num=num)
+    ks = {15: C.kernel_t15(coef)}
+    Y = SC.radix_residual(Poly.z(deg, mp.mpf(1)), [15, 15], ks, alg, form="error-map")
+    ycs = Y.coeffs(deg)
+    assert max(abs(c - 1) for c in ycs[:225]) < 1e-25
+    one_minus_z = Poly({0: mp.mpf(1), 1: mp.mpf(-1)}, deg)
+    E2 = Poly.one(deg, mp.mpf(1)) - (one_minus_z @ Y)
+    ecs = E2.coeffs(deg)
+    val = R15.circuit_poly(R15.flatten(R15.load_refined(mp.mpf)), mp.mpf(0), mp.mpf(1))
+    c = 1 - val[15]
+    assert max(abs(x) for x in ecs[:225]) < 1e-25
+    assert abs(ecs[225] - c ** 16) < 1e-25
+    assert abs(c ** 16 - 0.03774) < 5e-5  # value quoted for n = 2
+
+
+# ---------------------------------------------------------------- schemes on polynomials
+
+@pytest.mark.parametrize("scheme,k", [
+    ("naive", 1), ("naive", 2), ("naive", 7), ("naive", 30),
+    ("pow2", 1), ("pow2", 2), ("pow2", 64),
+    ("exact", 1), ("exact", 2), ("exact", 81), ("exact", 100), ("exact", 225),
+    ("r9", 9), ("r9", 81), ("r9", 729), ("r5", 125), ("r3", 27), ("r2", 32), ("auto", 360), ("auto", 405),
+])
+def test_exact_schemes_give_all_ones(scheme, k):
+    """Exact schemes compute I + z + ... + z^{k-1} exactly (Sec. 2.1-2.2)."""
+    deg = k + 6
+    alg = _exact_poly_alg(deg)
+    z = Poly.z(deg)
+    ks = EV.kernels()
+    if scheme == "naive":
+        Y = SC.naive(z, k, alg)
+    elif scheme == "pow2":
+        Y = SC.binary_pow2(z, k, alg)
+    elif scheme == "exact":
+        Y = SC.binary_exact(z, k, alg)
+    elif scheme == "auto":
+        Y = SC.radix_exact(z, EV.auto_levels(k), ks, alg)
+    else:
+        m = int(scheme[1:])
+        Y = SC.radix_exact(z, SC.pure_levels(k, m), ks, alg)
+    assert Y.coeffs(deg) == [1] * k + [0] * (deg + 1 - k)
+
+
+@pytest.mark.parametrize("k", [9, 81, 729])
+def test_residual_framework_with_exact_kernel_is_exact(k):
+    """Sec. 5.5 'Exact radix-m': with f = T_9 the framework returns S_k exactly,
+    in both residual forms."""
+    deg = k + 4
+    for form in ("paper", "error-map"):
+        alg = _exact_poly_alg(deg)
+        Y = SC.radix_residual(Poly.z(deg), SC.pure_levels(k, 9), EV.kernels(), alg, form)
+        assert Y.coeffs(deg) == [1] * k + [0] * (deg + 1 - k)
+
+
+def test_hensel_special_case():
+    """Sec. 5.5: f = 1 + z gives E(z) = z^2 (Hensel lifting)."""
+    alg = _exact_poly_alg(8)
+    z = Poly.z(8)
+    E = Poly.one(8) - (Poly.one(8) - z) @ C.kernel_t2(z, alg)
+    assert E.coeffs(8) == [0, 0, 1, 0, 0, 0, 0, 0, 0]
+
+
+# ---------------------------------------------------------------- product counts
+
+def test_counts_match_table_results(golden):
+    g = golden("paper_product_counts.json")
+    for k, binary, quin, r9, r15 in g["rows"]:
+        assert CT.binary_formula(k) == binary
+        if quin is not None:
+            assert CT.radix_formula(k, 5) == quin
+        if r9 is not None:
+            assert CT.radix_formula(k, 9) == r9
+        if r15 is not None:
+            assert CT.radix_formula(k, 15) == r15
+    ex = g["large_k_example"]
+    assert CT.radix_formula(ex["k"], 9) == ex["radix9"]
+    assert CT.binary_formula(ex["k"]) - 1 == ex["binary"]
+
+
+def test_asymptotic_coefficients(golden):
+    g = golden("paper_coefficients.json")
+    for m, c in g["coefficient_2dp"].items():
+        assert round(CT.coefficient(int(m)), 2) == c
+        assert CT.update_cost(int(m)) == g["cost"][m]
+
+
+@pytest.mark.parametrize("k,radix", [(81, 9), (729, 9), (6561, 9), (225, 15), (3375, 15),
+                                     (125, 5), (625, 5), (64, 2), (1024, 2), (4096, 2)])
+def test_executed_counts_elide_two(k, radix):
+    """Executed = paper formula - 2: the first concatenation multiplies by S_1 = I
+    and the last power is never read (Sec. 2.2 counts both)."""
+    n = 4
+    A = G.gaussian_scaled(n, 0.5, 3)["A"]
+    _, p = EV.evaluate(A, k, radix)
+    formula = CT.binary_formula(k) if radix == 2 else CT.radix_formula(k, radix)
+    assert p == formula - 2
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 81, 100, 225, 729, 3375, 6561, 1000])
+def test_exact_binary_count_closed_form(k):
+    """Digit scheme: (L-2) concatenations + (L-1) squarings + (ones-1) steps
+    P <- P A, minus the one unused power at the end: 2L + ones - 5."""
+    L, ones = k.bit_length(), bin(k).count("1")
+    alg = C.matrix_algebra(3)
+    SC.binary_exact(np.zeros((3, 3)), k, alg)
+    assert alg.products == 2 * L + ones - 5
+
+
+def test_naive_count():
+    alg = C.matrix_algebra(3)
+    SC.naive(np.zeros((3, 3)), 81, alg)
+    assert alg.products == CT.naive_formula(81) - 1 == 79
+
+
+# ---------------------------------------------------------------- matrices
+
+@pytest.mark.parametrize("n,k", [(1, 5), (3, 1), (3, 2), (5, 17), (8, 81), (8, 100)])
+def test_naive_equals_bruteforce(n, k):
+    """Definition (Eq. neumann) by explicit powers from numpy.linalg.matrix_power."""
+    A = G.gaussian_scaled(n, 0.6, 10 + n)["A"]
+    ref = sum(np.linalg.matrix_power(A, j) for j in range(k))
+    for radix in (1, 2):
+        S, _ = EV.evaluate(A, k, radix)
+        assert CF.rel_fro(S, ref) < 1e-14
+
+
+@pytest.mark.parametrize("k,radix", [(81, 9), (81, 1), (81, 2), (128, 2), (125, 5), (27, 3), (360, 0)])
+def test_telescoping_identity(k, radix):
+    """(I - A) S_k = I - A^k (Sec. 2.2, telescoping) on a nonsymmetric A."""
+    A = G.gaussian_scaled(40, 0.7, 77)["A"]
+    S, _ = EV.evaluate(A, k, radix)
+    lhs = (np.eye(40) - A) @ S
+    rhs = np.eye(40) - np.linalg.matrix_power(A, k)
+    assert np.linalg.norm(lhs - rhs) < 1e-13 * np.linalg.norm(rhs)
+
+
+def test_closed_form_matches_definition():
+    """Q diag((1 - l^k)/(1 - l)) Q^T equals Horner on a planted spectrum."""
+    p = G.planted_symmetric(64, 0.9, 5)
+    eig = np.sort(np.linalg.eigvalsh(p["A"]))
+    assert np.max(np.abs(eig - np.sort(p["lam"]))) < 1e-13
+    for k in (1, 2, 50, 200):
+        S, _ = EV.evaluate(p["A"], k, 1)
+        assert CF.rel_fro(EV.planted_reference(p["V"], p["lam"], k, 1), S) < 1e-13
+
+
+def test_closed_form_rows():
+    p = G.planted_symmetric(50, 0.9, 6)
+    full = EV.planted_reference(p["V"], p["lam"], 33, 9)
+    rows = [0, 7, 49]
+    part = EV.planted_reference(p["V"], p["lam"], 33, 9, rows=rows)
+    assert np.max(np.abs(full[rows] - part)) < 1e-13
+
+
+@pytest.mark.parametrize("k", [15, 225, 3375])
+def test_radix15_matrix_iteration_matches_lemma_5_7(k):
+    """eq. generalradix run on matrices equals the Lemma 5.7 closed form
+    (I - A)^{-1} (I - E^[t](A)) evaluated on the planted eigenvalues."""
+    p = G.planted_symmetric(64, 0.9, 8)
+    ref = EV.planted_reference(p["V"], p["lam"], k, 15)
+    for form in ("paper", "error-map"):
+        S, _ = EV.evaluate(p["A"], k, 15, form=form)
+        assert CF.rel_fro(S, ref) < 1e-13
+
+
+def test_radix15_distance_to_sk_small_inside_region():
+    """For |l| <= 0.9 three radix-15 levels agree with S_3375 to ~1e-15 relative."""
+    lam = np.linspace(-0.9, 0.9, 101)
+    y = CF.radix_scalar(lam, [15, 15, 15], EV.kernels())
+    s = CF.sk_scalar(lam, 3375)
+    assert np.max(np.abs(y - s) / np.abs(s)) < 1e-13
+
+
+def test_rational_radix9_equals_naive():
+    """Exact rational 3x3 matrices: radix-9 (k = 81) equals naive summation exactly."""
+    A = np.array(G.rational_small(3, 42), dtype=object)
+    one = np.eye(3, dtype=int).astype(object)
+    alg = C.Algebra(one, lambda x, y: x @ y, lambda q: q)
+    S9 = SC.radix_exact(A, [9, 9], EV.kernels(), alg)
+    alg2 = C.Algebra(one, lambda x, y: x @ y, lambda q: q)
+    Sn = SC.naive(A, 81, alg2)
+    assert all(S9[i, j] == Sn[i, j] for i in range(3) for j in range(3))
+    assert all(isinstance(S9[i, j], F) for i in range(3) for j in range(3))
+
+
+def test_probe_horner():
+    A = G.gaussian_scaled(30, 0.5, 9)["A"]
+    X = np.random.default_rng(0).standard_normal((30, 4))
+    S, _ = EV.evaluate(A, 40, 1)
+    assert CF.rel_fro(CF.horner_probes(A, X, 40), S @ X) < 1e-14
+
+
+# ---------------------------------------------------------------- generators
+
+def test_generators_shapes_and_spectra():
+    g = G.gaussian_scaled(64, 0.5, 1)
+    assert abs(np.linalg.norm(g["A"], 2) - 0.5) < 1e-14
+    p = G.planted_perturbed(96, 0.95, 2, rank=4, n_probes=3)
+    D = p["X"] @ p["Y"].T
+    assert abs(np.linalg.norm(D, 2) - 0.01) < 1e-14 and p["probes"].shape == (96, 3)
+    b = G.jacobi_batch(6, 3, sizes=(16, 32))
+    for m in b:
+        rho = np.max(np.abs(np.linalg.eigvals(m["A"])))
+        assert rho < 0.999
+    bu = G.jacobi_batch(3, 3, sizes=(32,), damped=False)
+    assert all(np.max(np.abs(np.linalg.eigvals(m["A"]))) > 1.2 for m in bu)
