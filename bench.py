@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of S_k(A) evaluation on GB300, one JSON line on stdout.
+
+Default workload (the precision form): n = 8192, planted symmetric spectrum
+lam ~ U[-0.97, 0.97], k = 3375 = 15^3 by the radix-15 kernel in the residual
+framework, products on the tcgen05 tensor cores from split hi+lo BF16
+operands. A step is one evaluation (16 products and their fused epilogues).
+The line also reports repeated squaring (k = 4096, the paper's binary
+comparator) on the same input and arithmetic.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Under torchrun every rank evaluates its own replica (independent seeds); the
+evaluations do not communicate ("replicas only"), so scaling is weak.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "S_k(A) evals/s & % tensor peak: radix-15/9 vs squaring, split-BF16 vs FP64"
+UNIT = "S_k/s"
+
+WORKLOADS = {
+    "precision-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096),
+    "precision-r9-bf16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_bf16", sq_k=8192),
+    "plain-r9-fp32-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
+    "plain-r15-fp32-n4096-k225": dict(cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
+    "plain-r9-fp64-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
+}
+DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
+
+# DRAM bytes per launch of the tensor-core product at n = 8192 from one ncu
+# capture (profiles/tc_split_gemm_n8192.md), valid for the kernel source whose
+# SHA-1 prefix is recorded beside it; None when no capture matches the source.
+TC_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _src_sha(name):
+    p = os.path.join(ROOT, "paper_2602_11843_gb300", "csrc", name)
+    with open(p, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of this GPU's clocks and throttle reasons."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.tmp.flush()
+        rows = []
+        try:
+            with open(self.tmp.name) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 10:
+                        continue
+                    if self.uuid and self.uuid not in parts[1]:
+                        continue
+                    rows.append(parts)
+        finally:
+            os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][3]),
+                "power_w_max": max((num(r[4]) or 0.0) for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def make_input(wl, seed_rep):
+    from workloads import generators as G
+
+    return G.config_inputs(wl["cfg"], r=seed_rep, n=wl["n"])
+
+
+def cpu_baseline(wl, A_np, budget_products=None):
+    """The oracle as it stands, on a bounded sample: the first `p` products of the
+    same scheme at the same n (FP64, NumPy/BLAS on the host cores), scaled to
+    S_k/s by the oracle's product count for the whole evaluation."""
+    import numpy as np
+
+    from oracle import circuits as C
+    from oracle import evaluate as EV
+    from oracle import schemes as SC
+
+    n = A_np.shape[0]
+    alg = C.matrix_algebra(n)
+    ks = EV.kernels()
+    levels = SC.pure_levels(wl["k"], wl["radix"])
+    count_alg = C.matrix_algebra(2)
+    (SC.radix_residual if wl["radix"] == 15 else SC.radix_exact)(np.eye(2), levels, ks, count_alg)
+    total = count_alg.products
+    t0 = time.perf_counter()
+    ks[wl["radix"]](A_np, alg)  # first level's kernel: mu_m products of the oracle
+    dt = time.perf_counter() - t0
+    per_product = dt / alg.products
+    return {"value": 1.0 / (per_product * total), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first-level radix-{wl['radix']} kernel ({alg.products} of {total} products) at n={n}, "
+                      f"FP64 NumPy/BLAS, scaled by product count; {dt:.1f} s"}
+
+
+def run_reference(args, wl):
+    """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import circuits as C
+    from oracle import evaluate as EV
+
+    inp = make_input(wl, 0)
+    A = np.asarray(inp["A"], dtype=np.float64)
+    ks = EV.kernels()
+    info_products = None
+    times = []
+    for it in range(args.warmup + args.steps):
+        alg = C.matrix_algebra(A.shape[0])
+        t0 = time.perf_counter()
+        ks[wl["radix"]](A, alg)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt / alg.products)
+        info_products = alg.products
+    from oracle import schemes as SC
+
+    calg = C.matrix_algebra(2)
+    levels = SC.pure_levels(wl["k"], wl["radix"])
+    (SC.radix_residual if wl["radix"] == 15 else SC.radix_exact)(np.eye(2), levels, ks, calg)
+    per_eval = statistics.median(times) * calg.products
+    value = 1.0 / per_eval
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": wl["n"], "k": wl["k"], "radix": wl["radix"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"each step: one radix-{wl['radix']} kernel ({info_products} products) at "
+                                   f"n={wl['n']}, scaled to a full evaluation ({calg.products} products)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2602_11843_gb300 as nm
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    inp = make_input(wl, rank)
+    A_np = np.asarray(inp["A"], dtype=np.float64)
+    n, k = wl["n"], wl["k"]
+    plan = nm.Plan(n, k, wl["radix"], wl["dtype"], nm.FLAG_TIMING)
+    io = plan.io_dtype
+    A = torch.tensor(A_np, dtype=io, device=dev)
+    S = torch.empty_like(A)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan(A, out=S)
+    torch.cuda.synchronize()
+    plan.timing()  # discard warm-up records
+    assert plan.status() == 0, "device status set during warm-up"
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan(A, out=S)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    prod_ms = plan.timing()
+    status = plan.status()
+    info = plan.info
+    value = args.steps * world / (ms_max / 1e3)
+
+    # repeated squaring on the same input and arithmetic (the paper's binary comparator)
+    sq = nm.Plan(n, wl["sq_k"], 2, wl["dtype"])
+    for _ in range(args.warmup):
+        sq(A, out=S)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sq(A, out=S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sq_ms = e0.elapsed_time(e1) / args.steps
+
+    # end to end through the C ABI: pinned host A in, host S out, every step
+    A_host = torch.tensor(A_np, dtype=io).pin_memory()
+    S_host = torch.empty_like(A_host).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        A.copy_(A_host, non_blocking=True)
+        plan(A, out=S)
+        S_host.copy_(S, non_blocking=True)
+    torch.cuda.synchronize()
+    plan.timing()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        A.copy_(A_host, non_blocking=True)
+        plan(A, out=S)
+        S_host.copy_(S, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = args.steps * world / (float(te.item()) / 1e3)
+    plan.timing()
+
+    peaks, peak_src = _peaks()
+    tc = wl["dtype"].startswith("split")
+    mean_prod_ms = statistics.mean(prod_ms) if prod_ms else float("nan")
+    if tc:
+        flops = 3 * 2.0 * n ** 3  # three BF16 products per split product
+        peak = peaks["bf16_tflops_sustained"]
+        sha = _src_sha("kernels_tc.cu")
+        traffic = TC_TRAFFIC["bytes_per_launch"] if TC_TRAFFIC["sha1"] == sha and n == 8192 else None
+        roof = {"bound": "tensor", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": None, "traffic": traffic,
+                "kernel": "tc_split_gemm_kernel", "peak_source": f"bf16_tflops_sustained ({peak_src})",
+                "work_per_launch": "3 x 2n^3 BF16 tensor flops", "launches_timed": len(prod_ms)}
+    else:
+        flops = 2.0 * n ** 3
+        # CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes (x 2 flop) at the
+        # maximum SM clock; FP64 at 1/64 of the FP32 rate
+        clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        fp32_peak = 152 * 128 * 2 * clk / 1e12
+        peak = fp32_peak if wl["dtype"] == "fp32" else fp32_peak / 64
+        roof = {"bound": "alu", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "kernel": "simt_gemm_kernel",
+                "peak_source": "derived: 152 SM x 128 lanes x 2 flop x max SM clock (FP64: /64)",
+                "work_per_launch": "2n^3 flops", "launches_timed": len(prod_ms)}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["effective_tflops"] = 2.0 * n ** 3 / (mean_prod_ms / 1e3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if tc else ("f32" if wl["dtype"] == "fp32" else "f64"),
+        "precision": {"split_bf16": "hi+lo BF16 operands, 3 products, FP32 accumulate, FP64 Y and R",
+                      "fp32": "FP32 products, FP64 Y and R", "fp64": "FP64"}[wl["dtype"]],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "k": k, "radix": wl["radix"], "scheme": wl["dtype"],
+                   "products_per_step": info["products_executed"], "products_formula": info["products_formula"],
+                   "l2": "inputs larger than L2 (A, S and every workspace matrix exceed 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "vs_squaring": {"k": wl["sq_k"], "ms_per_step": sq_ms, "speedup": sq_ms / (ms_max / args.steps),
+                        "products_executed": sq.info["products_executed"],
+                        "formula_ratio": sq.info["products_formula"] / info["products_formula"]},
+        "status": status,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": A_host.numel() * A_host.element_size(),
+                "d2h_bytes_per_step": S_host.numel() * S_host.element_size()},
+        "gpu_launches": args.steps * info["launches"],
+        "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, A_np)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

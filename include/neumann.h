@@ -1,0 +1,190 @@
+/*
+ * neumann.h - C ABI of the GB300 (sm_103a) truncated Neumann series library.
+ *
+ * Computes S_k(A) = I + A + A^2 + ... + A^{k-1} for a dense n x n matrix A
+ * with spectral radius rho(A) < 1 (Sec. 1, Eq. neumann; Sec. 2, Eq. series),
+ * by one of the paper's schemes:
+ *   radix 1   naive accumulation of powers, k-2 products      (Sec. 2.1)
+ *   radix 2   repeated squaring (k = 2^t), or the binary digits of k with
+ *             NEUMANN_FLAG_EXACT_K                             (Sec. 2.1)
+ *   radix 3,5 exact ternary / quinary kernels                  (Sec. 2.1, Sec. 2.3)
+ *   radix 9   exact 3-product radix-9 kernel, k = 9^t          (Thm 3.1)
+ *   radix 15  approximate 4-product radix-15 kernel inside the residual
+ *             framework, k = 15^t                             (Sec. 4, Sec. 5.3)
+ *   radix 0   exact kernels over the factorisation of k into 9, 5, 3, 2
+ *             (block concatenation, Sec. 2.2, eq. decomposition)
+ * Every level applies a kernel f to the current residual R (R_0 = A), updates
+ * the partial sum Y <- Y f(R) (Y_0 = I) and the residual R <- I - (I - R) f(R)
+ * (Sec. 5.3, eq. generalradix and the proof of Lemma 5.7). For an exact
+ * kernel f = T_m this residual is the next power A^{m n} (telescoping,
+ * Sec. 2.2), so all schemes share one level loop.
+ *
+ * Result of radix 15: the residual-framework value Y_t = (I-A)^{-1}(I - E^[t](A))
+ * of Lemma 5.7, which agrees with S_k through the degree-(k-1) term.
+ *
+ * Arithmetic (neumann_dtype_t):
+ *   FP64        every product in FP64 on the CUDA cores; A and S are double.
+ *   FP32        every product in FP32 on the CUDA cores; the partial sum Y and
+ *               the residual R are accumulated in FP64; A and S are float.
+ *   SPLIT_BF16  every product on the tcgen05 tensor cores from hi+lo BF16
+ *               operands (x = hi + lo, three products hi*hi + hi*lo + lo*hi,
+ *               FP32 accumulation in tensor memory); Y and R accumulated in
+ *               FP64. A and S are double unless NEUMANN_FLAG_IO_FP32.
+ *   SPLIT_FP16  reserved; neumann_plan_create returns NEUMANN_ENOTSUP.
+ *
+ * Conventions shared by every call:
+ *   - Matrices are dense, row-major, n x n, with a leading dimension (in
+ *     elements, >= n) given per pointer. Device pointers are CUDA device
+ *     memory of the current device; host pointers are named as such.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *   - Calls return NEUMANN_OK (0) or an error code below; nothing throws.
+ *   - Work is stream-ordered and asynchronous: a call returns once its kernels
+ *     are queued. Conditions detected on the device (non-finite values,
+ *     a bounded wait that expired) are read with neumann_last_status.
+ *   - Precondition rho(A) < 1 is documented, not checked. Radix 15 converges
+ *     for real eigenvalues |l| < ~0.97.
+ */
+#ifndef NEUMANN_GB300_H
+#define NEUMANN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct neumann_plan_s* neumann_plan_t;
+
+typedef enum {
+  NEUMANN_FP64 = 0,
+  NEUMANN_FP32 = 1,
+  NEUMANN_SPLIT_BF16 = 2,
+  NEUMANN_SPLIT_FP16 = 3
+} neumann_dtype_t;
+
+/* Return codes. */
+#define NEUMANN_OK 0
+#define NEUMANN_EINVAL 1  /* bad argument: n < 1, k < 1, k not a power of the radix, ld < n, aliasing, NULL */
+#define NEUMANN_ENOMEM 2  /* device or host allocation failed */
+#define NEUMANN_ECUDA 3   /* a CUDA call or kernel launch failed */
+#define NEUMANN_ENOTSUP 4 /* dtype / radix combination not supported */
+
+/* Device status bits reported by neumann_last_status. */
+#define NEUMANN_STATUS_NONFINITE 1u /* an epilogue produced Inf/NaN (in practice rho(A) >= 1) */
+#define NEUMANN_STATUS_TIMEOUT 2u   /* a bounded device wait expired; the result is invalid */
+
+/* Plan flags. */
+#define NEUMANN_FLAG_EXACT_K 0x1u         /* radix 2: any k >= 1 by the binary digits of k */
+#define NEUMANN_FLAG_RESIDUAL_PAPER 0x2u  /* residual R' = I - (I - A) Y' (eq. generalradix) instead of R' = R + R G - G */
+#define NEUMANN_FLAG_PRINTED_COEFFS 0x4u  /* radix 15: the three-decimal coefficients printed in App. B */
+#define NEUMANN_FLAG_TIMING 0x8u          /* record CUDA events around every product (neumann_plan_timing) */
+#define NEUMANN_FLAG_IO_FP32 0x10u        /* split dtypes: A and S are float instead of double */
+
+#define NEUMANN_MAX_LEVELS 64
+
+typedef struct {
+  int64_t n, k;
+  int radix;                    /* as requested */
+  int dtype;                    /* neumann_dtype_t */
+  uint32_t flags;
+  int levels;                   /* radix levels (0 for the naive chain and for k <= 2) */
+  int level_radix[NEUMANN_MAX_LEVELS];
+  int64_t products_formula;     /* the paper's count: k-1 (naive), 2 ceil(log2 k) (binary, Sec. 6),
+                                   sum of mu_m + 2 over levels (Sec. 2.2 cost model) */
+  int64_t products_executed;    /* products this plan launches (no product with I, no unused power) */
+  int64_t launches;             /* kernel launches per neumann_eval */
+  size_t workspace_bytes;       /* device workspace the plan needs */
+  int64_t padded_n;             /* workspace matrices are padded_n x padded_n */
+} neumann_plan_info_t;
+
+/* Create a plan for S_k(A) with A n x n. Host-only: no device memory is
+ * touched. The plan owns a device workspace of info.workspace_bytes that is
+ * allocated on the first neumann_eval unless the caller supplies one with
+ * neumann_plan_set_workspace.
+ *   out    receives the plan (set to NULL on error)
+ *   n      matrix order, >= 1
+ *   k      number of series terms, >= 1; for radix 3, 5, 9, 15 a power of the radix;
+ *          for radix 2 a power of two unless NEUMANN_FLAG_EXACT_K; for radix 0 of the
+ *          form 2^a 3^b 5^c
+ *   radix  0, 1, 2, 3, 5, 9 or 15 (see above)
+ *   dtype  neumann_dtype_t
+ *   flags  NEUMANN_FLAG_*
+ * Errors: NEUMANN_EINVAL, NEUMANN_ENOTSUP, NEUMANN_ENOMEM (host). */
+int neumann_plan_create(neumann_plan_t* out, int64_t n, int64_t k, int radix, int dtype, uint32_t flags);
+
+/* Fill *info for a plan. Errors: NEUMANN_EINVAL (NULL). */
+int neumann_plan_info(neumann_plan_t plan, neumann_plan_info_t* info);
+
+/* Give the plan a caller-owned device workspace of at least
+ * info.workspace_bytes bytes, 256-byte aligned. The caller keeps ownership and
+ * must keep it alive until the plan is destroyed or another workspace is set.
+ * No initial contents are required: the call clears the device status word (the
+ * first 256 bytes, synchronously) and every evaluation rewrites each buffer it
+ * reads, padding included. Errors: NEUMANN_EINVAL (too small, misaligned),
+ * NEUMANN_ECUDA. */
+int neumann_plan_set_workspace(neumann_plan_t plan, void* workspace, size_t bytes);
+
+/* S <- S_k(A) for the plan's n, k, radix and dtype.
+ *   A    device, n x n row-major, leading dimension lda >= n (double for FP64 and
+ *        split dtypes, float for FP32 and with NEUMANN_FLAG_IO_FP32); read only
+ *   S    device, n x n row-major, leading dimension lds >= n, same element type as A;
+ *        must not overlap A
+ * Stream-ordered. Allocates the workspace with cudaMalloc on first use when none
+ * was set. Two evaluations with the same plan must not run concurrently.
+ * Errors: NEUMANN_EINVAL, NEUMANN_ENOMEM, NEUMANN_ECUDA. */
+int neumann_eval(neumann_plan_t plan, const void* A, int64_t lda, void* S, int64_t lds, void* stream);
+
+/* C <- A B in the plan's arithmetic (the product every scheme step uses), for
+ * n x n row-major device matrices with leading dimension n, element type as in
+ * neumann_eval. Uses the plan's workspace for split operands. Stream-ordered.
+ * Errors as neumann_eval. */
+int neumann_plan_matmul(neumann_plan_t plan, const void* A, const void* B, void* C, void* stream);
+
+/* Batched plan: `count` independent evaluations with n_i <= max_n, the same k,
+ * radix and dtype. Host-only, like neumann_plan_create. */
+int neumann_plan_create_batched(neumann_plan_t* out, int count, int64_t max_n, int64_t k, int radix,
+                                int dtype, uint32_t flags);
+
+/* S_i <- S_k(A_i), i < count.
+ *   n  HOST array of count orders (1 <= n_i <= max_n)
+ *   A  HOST array of count device pointers (n_i x n_i, leading dimension n_i)
+ *   S  HOST array of count device pointers (same shapes; no overlap with any A_j)
+ * Stream-ordered. Errors: NEUMANN_EINVAL (count or n_i out of range),
+ * NEUMANN_ENOMEM, NEUMANN_ECUDA. */
+int neumann_eval_batched(neumann_plan_t plan, int count, const int64_t* n, const void* const* A,
+                         void* const* S, void* stream);
+
+/* Synchronise the plan's last stream and return the OR of the device status
+ * bits (NEUMANN_STATUS_*) set since the previous call, then clear them.
+ * Errors: NEUMANN_EINVAL, NEUMANN_ECUDA. */
+int neumann_last_status(neumann_plan_t plan, unsigned* status);
+
+/* With NEUMANN_FLAG_TIMING every product launched by neumann_eval is bracketed
+ * by two CUDA events on the evaluation's stream. This call synchronises on the
+ * last of them, copies the device time (ms) of each product recorded since the
+ * previous call into ms[0..cap-1] (in launch order), sets *count to the number
+ * recorded, and starts a new record. At most 65536 products are kept; an
+ * evaluation that would exceed that returns NEUMANN_EINVAL.
+ * Errors: NEUMANN_EINVAL (no timing flag), NEUMANN_ECUDA. */
+int neumann_plan_timing(neumann_plan_t plan, float* ms, int cap, int* count);
+
+/* The 28 radix-15 circuit parameters the library uses (Sec. 4.1, App. B), in
+ * the order l2[3], r2[3], l3[4], r3[4], l4[5], r4[5], gamma[4]; set 0 = refined
+ * on the host by minimum-norm Gauss-Newton from the printed values, 1 = as printed.
+ * Also returns max_{j<15} |[T~15]_j - 1| and the spillover [T~15]_15, [T~15]_16.
+ * Errors: NEUMANN_EINVAL. */
+int neumann_radix15_coefficients(int set, double* coef28, double* prefix_error, double* spill15,
+                                 double* spill16);
+
+/* Release a plan and the workspace it allocated (not a caller-set one). NULL is ignored. */
+void neumann_plan_destroy(neumann_plan_t plan);
+
+/* Static string for a return code. */
+const char* neumann_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEUMANN_GB300_H */

@@ -1,0 +1,113 @@
+"""Truncated Neumann series S_k(A) = I + A + ... + A^{k-1} on one GB300 (sm_103a).
+
+The computation lives in libneumann_gb300.so (C ABI in include/neumann.h);
+this package is its Python binding. `Plan` and `evaluate` add PyTorch tensor
+marshalling (device memory and the current stream) on top of the C calls.
+"""
+
+from __future__ import annotations
+
+from ._capi import *  # noqa: F401,F403
+from ._capi import (DTYPES, FP32, FP64, SPLIT_BF16, LIB_PATH, neumann_eval, neumann_eval_batched,  # noqa: F401
+                    neumann_last_status, neumann_plan_create, neumann_plan_create_batched,
+                    neumann_plan_destroy, neumann_plan_info, neumann_plan_matmul, neumann_plan_timing)
+
+
+def _torch_dtype(dtype: int, flags: int):
+    import torch
+
+    from ._capi import FLAG_IO_FP32
+
+    if dtype == FP32 or (dtype != FP64 and flags & FLAG_IO_FP32):
+        return torch.float32
+    return torch.float64
+
+
+class Plan:
+    """Owns a C plan handle; `__call__` evaluates S_k(A) for a CUDA tensor A."""
+
+    def __init__(self, n: int, k: int, radix: int, dtype="fp64", flags: int = 0):
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.flags = flags
+        self.handle = neumann_plan_create(n, k, radix, self.dtype, flags)
+        self.info = neumann_plan_info(self.handle)
+
+    @property
+    def io_dtype(self):
+        return _torch_dtype(self.dtype, self.flags)
+
+    def __call__(self, A, out=None, stream=None):
+        import torch
+
+        n = self.info["n"]
+        if A.device.type != "cuda" or A.dtype != self.io_dtype or A.shape != (n, n) or A.stride(1) != 1:
+            raise ValueError(f"A must be a CUDA {self.io_dtype} ({n}, {n}) tensor with unit column stride")
+        S = torch.empty((n, n), dtype=self.io_dtype, device=A.device) if out is None else out
+        s = torch.cuda.current_stream(A.device) if stream is None else stream
+        neumann_eval(self.handle, A.data_ptr(), A.stride(0), S.data_ptr(), S.stride(0), s.cuda_stream)
+        return S
+
+    def matmul(self, A, B, out=None, stream=None):
+        import torch
+
+        C = torch.empty_like(A) if out is None else out
+        s = torch.cuda.current_stream(A.device) if stream is None else stream
+        neumann_plan_matmul(self.handle, A.data_ptr(), B.data_ptr(), C.data_ptr(), s.cuda_stream)
+        return C
+
+    def status(self) -> int:
+        return neumann_last_status(self.handle)
+
+    def timing(self) -> list:
+        return neumann_plan_timing(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            neumann_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchedPlan:
+    """Batched evaluation of independent matrices with n_i <= max_n."""
+
+    def __init__(self, count: int, max_n: int, k: int, radix: int, dtype="fp32", flags: int = 0):
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.flags = flags
+        self.handle = neumann_plan_create_batched(count, max_n, k, radix, self.dtype, flags)
+
+    def __call__(self, As, outs=None, stream=None):
+        import torch
+
+        dt = _torch_dtype(self.dtype, self.flags)
+        outs = [torch.empty_like(a) for a in As] if outs is None else outs
+        for a in As:
+            if a.dtype != dt or not a.is_contiguous():
+                raise ValueError(f"inputs must be contiguous {dt}")
+        s = torch.cuda.current_stream(As[0].device) if stream is None else stream
+        neumann_eval_batched(self.handle, [a.shape[0] for a in As], [a.data_ptr() for a in As],
+                             [o.data_ptr() for o in outs], s.cuda_stream)
+        return outs
+
+    def status(self) -> int:
+        return neumann_last_status(self.handle)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                neumann_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def evaluate(A, k: int, radix: int, dtype="fp64", flags: int = 0):
+    """S_k(A) for a CUDA tensor A (one-shot plan)."""
+    p = Plan(A.shape[0], k, radix, dtype, flags)
+    S = p(A)
+    return S

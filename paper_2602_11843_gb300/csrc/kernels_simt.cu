@@ -1,0 +1,144 @@
+// CUDA-core GEMMs for the plain FP64 and FP32 paths, with the fused epilogue.
+//
+// Blackwell tensor cores take no FP32 operands, and GB300's FP64 rate is the
+// same on the tensor and CUDA cores, so these products run as register-tiled
+// SIMT GEMMs: a 128 x 128 tile per 256-thread CTA, 8 x 8 outputs per thread,
+// K staged through double-buffered shared memory 8 at a time. All workspace
+// matrices are padded to a multiple of 256 in both dimensions and every
+// epilogue rewrites the padding with zeros, so the main loop has no bounds
+// checks.
+#include "epilogue.cuh"
+
+namespace neumann {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 8, TPB = 256;
+
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  double2 t0 = reinterpret_cast<const double2*>(p)[0];
+  double2 t1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B,
+                                                        int64_t ld, int ktiles,
+                                                        const __grid_constant__ EpiParams P) {
+  __shared__ __align__(16) T As[2][BK][BM + 4];
+  __shared__ __align__(16) T Bs[2][BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int a_row = tid >> 1, a_col = (tid & 1) * 4;   // A tile: 128 rows x 8
+  const int b_row = tid >> 5, b_col = (tid & 31) * 4;  // B tile: 8 rows x 128
+  const T* Ap = A + (int64_t)(m0 + a_row) * ld + a_col;
+  const T* Bp = B + (int64_t)b_row * ld + n0 + b_col;
+
+  T ra[4], rb[4];
+  load4(Ap, ra);
+  load4(Bp, rb);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    As[0][a_col + j][a_row] = ra[j];
+    Bs[0][b_row][b_col + j] = rb[j];
+  }
+  __syncthreads();
+
+  T acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+
+  for (int kt = 0; kt < ktiles; ++kt) {
+    const int cur = kt & 1;
+    const bool more = kt + 1 < ktiles;
+    if (more) {
+      load4(Ap + (int64_t)(kt + 1) * BK, ra);
+      load4(Bp + (int64_t)(kt + 1) * BK * ld, rb);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[8], b[8];
+      T t[4];
+      load4(&As[cur][kk][ty * 4], t);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = t[q];
+      load4(&As[cur][kk][64 + ty * 4], t);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[4 + q] = t[q];
+      load4(&Bs[cur][kk][tx * 4], t);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = t[q];
+      load4(&Bs[cur][kk][64 + tx * 4], t);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[4 + q] = t[q];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        As[cur ^ 1][a_col + j][a_row] = ra[j];
+        Bs[cur ^ 1][b_row][b_col + j] = rb[j];
+      }
+    }
+    __syncthreads();
+  }
+
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      bad |= epi_element<T>(P, r, c, acc[i][j]);
+    }
+  }
+  epi_flag(P, bad);
+}
+
+__global__ void __launch_bounds__(256) ewise_kernel(const __grid_constant__ EpiParams P) {
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int r = blockIdx.y * 8 + threadIdx.y;
+  bool bad = false;
+  if (r < P.npad && c < P.npad) bad = epi_element<float>(P, r, c, 0.f);
+  epi_flag(P, bad);
+}
+
+template <typename T>
+cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const EpiParams& P, cudaStream_t s) {
+  if (npad % BM != 0 || npad % BN != 0 || ld < npad) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)(npad / BN), (unsigned)(npad / BM));
+  simt_gemm_kernel<T><<<grid, TPB, 0, s>>>(A, B, ld, (int)(npad / BK), P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad, const EpiParams& P,
+                                 cudaStream_t s) {
+  return launch_simt<double>(A, B, ld, npad, P, s);
+}
+
+cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad, const EpiParams& P,
+                                 cudaStream_t s) {
+  return launch_simt<float>(A, B, ld, npad, P, s);
+}
+
+cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s) {
+  if (P.npad <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((P.npad + 31) / 32), (unsigned)((P.npad + 7) / 8));
+  ewise_kernel<<<grid, dim3(32, 8), 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace neumann

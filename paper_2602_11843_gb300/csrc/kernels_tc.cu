@@ -1,0 +1,334 @@
+// tcgen05 tensor-core product for the split-BF16 path.
+//
+// Each operand x is stored as a pair hi = RN_bf16(x), lo = RN_bf16(x - hi), so
+// x = hi + lo to about 2^-17 relative. A product A B is formed as
+//   Ahi Bhi + Ahi Blo + Alo Bhi
+// (the lo*lo term, ~2^-18 relative, is dropped), all three issued as
+// tcgen05.mma kind::f16 instructions into one FP32 accumulator in tensor
+// memory. One CTA computes a 128 x 256 output tile:
+//   warp 0 lane 0  TMA producer: four tiles per stage (Ahi, Alo, Bhi, Blo),
+//                  K = 32 per stage (64-byte rows, 64B swizzle), 4 stages
+//   warp 1 lane 0  MMA issuer: 2 K-slices x 3 products per stage, then a
+//                  tcgen05.commit that frees the stage
+//   warps 0-3      epilogue: tcgen05.ld of the 128 x 256 accumulator (each warp
+//                  owns 32 TMEM lanes = 32 rows) and the fused epilogue.
+// A is read row-major (K-major); B is read from its transpose (row j of the
+// stored array is column j of B), which makes it K-major too.
+//
+// Every mbarrier wait is bounded (kTimeoutNs): on expiry the kernel sets
+// NEUMANN_STATUS_TIMEOUT, stops issuing, drains what it issued and frees its
+// tensor memory before it returns.
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "epilogue.cuh"
+
+namespace neumann {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 32;  // bf16 elements per stage row = 64 bytes
+constexpr int STAGES = 4;
+constexpr int THREADS = 128;
+constexpr uint32_t A_TILE = BM * BK * 2;  // 8 KiB
+constexpr uint32_t B_TILE = BN * BK * 2;  // 16 KiB
+constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s; one CTA normally takes < 1 ms
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (gtimer() - t0 > kTimeoutNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major operand tile in shared memory with the 64-byte swizzle: rows of
+// 64 bytes, 8-row atoms of 512 bytes stacked along M/N (stride byte offset
+// 512), version 1 at bit 46, layout type 4 (SWIZZLE_64B) at bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int* tm, int* tn) {
+  constexpr int G = 8;  // row tiles per group: neighbouring CTAs share B column panels in L2
+  const int per_group = G * tiles_n;
+  const int g = bid / per_group;
+  const int first = g * G;
+  const int gs = min(tiles_m - first, G);
+  const int in = bid - g * per_group;
+  *tm = first + in % gs;
+  *tn = in / gs;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
+                         const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
+                         int ktiles, int tiles_m, int tiles_n, const __grid_constant__ EpiParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tm, tn;
+  raster(blockIdx.x, tiles_m, tiles_n, &tm, &tn);
+  const uint32_t smem_base = smem_u32(smem);
+  const uint32_t bar_base = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar_base + 8u * s; };
+  auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
+  const uint32_t acc_bar = bar_base + 8u * (2 * STAGES);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(acc_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_ahi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_alo)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_bhi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_blo)) : "memory");
+    int issued = 0;
+    for (int kb = 0; kb < ktiles; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (kb >= STAGES) {
+        if (!mbar_wait(empty_bar(s), ph ^ 1u) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+      const uint32_t st = smem_base + s * STAGE_BYTES;
+      mbar_expect_tx(full_bar(s), STAGE_BYTES);
+      tma_load_2d(st, &tm_ahi, full_bar(s), kb * BK, tm * BM);
+      tma_load_2d(st + A_TILE, &tm_alo, full_bar(s), kb * BK, tm * BM);
+      tma_load_2d(st + 2 * A_TILE, &tm_bhi, full_bar(s), kb * BK, tn * BN);
+      tma_load_2d(st + 2 * A_TILE + B_TILE, &tm_blo, full_bar(s), kb * BK, tn * BN);
+      ++issued;
+    }
+    if (*abort_flag) {
+      // drain: wait (bounded) for the last load issued into each stage
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        mbar_wait(full_bar(kb % STAGES), (uint32_t)(kb / STAGES) & 1u);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    for (int kb = 0; kb < ktiles; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(full_bar(s), ph) || *abort_flag) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = smem_base + s * STAGE_BYTES;
+#pragma unroll
+      for (int j = 0; j < BK / 16; ++j) {
+        const uint64_t a_hi = smem_desc(st + 32u * j);
+        const uint64_t a_lo = smem_desc(st + A_TILE + 32u * j);
+        const uint64_t b_hi = smem_desc(st + 2 * A_TILE + 32u * j);
+        const uint64_t b_lo = smem_desc(st + 2 * A_TILE + B_TILE + 32u * j);
+        umma_f16(tmem, a_hi, b_hi, (kb | j) != 0);
+        umma_f16(tmem, a_hi, b_lo, 1u);
+        umma_f16(tmem, a_lo, b_hi, 1u);
+      }
+      umma_commit(empty_bar(s));
+    }
+    umma_commit(acc_bar);  // arrives once every MMA issued above has completed
+  }
+
+  // ---------------- epilogue ----------------
+  __syncwarp();
+  bool ok = mbar_wait(acc_bar, 0);
+  __syncwarp();
+  tc_fence_after();
+  if (!ok) *abort_flag = 1;
+  __syncwarp();
+  const bool aborted = __any_sync(0xffffffffu, *abort_flag != 0) != 0;
+  bool bad = false;
+  if (!aborted) {
+    const int r = tm * BM + warp * 32 + lane;
+#pragma unroll 1
+    for (int chunk = 0; chunk < BN / 32; ++chunk) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
+      const int c0 = tn * BN + chunk * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) bad |= epi_element<float>(P, r, c0 + j, __uint_as_float(v[j]));
+    }
+  }
+  epi_flag(P, bad);
+  if (threadIdx.x == 0 && *abort_flag && P.status) atomicOr(P.status, 2u);
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)npad};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld) {
+  if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0) return false;
+  return make_map(&m->a_hi, a_hi, npad, ld, BM) && make_map(&m->a_lo, a_lo, npad, ld, BM) &&
+         make_map(&m->b_hi, bt_hi, npad, ld, BN) && make_map(&m->b_lo, bt_lo, npad, ld, BN);
+}
+
+cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s) {
+  if (npad % BN != 0) return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
+  tc_split_gemm_kernel<<<tiles_m * tiles_n, THREADS, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
+                                                                     (int)(npad / BK), tiles_m, tiles_n, P);
+  return cudaGetLastError();
+}
+
+}  // namespace neumann

@@ -1,0 +1,971 @@
+// Plan construction (the per-level scheduler), workspace layout, execution,
+// and the C ABI declared in include/neumann.h.
+//
+// Every scheme is compiled at plan time into a list of operations, each a
+// product (GEMM) or an element-wise pass, both ending in the fused epilogue.
+// A radix level with kernel f works on the residual R (R_0 = A) and the
+// partial sum Y (Y_0 = I), Sec. 5.3 eq. generalradix:
+//   kernel     G = f(R) - I            mu_m products (Thm 3.1; Sec. 4.1; Sec. 2.3)
+//   concat     Y <- Y + Y G            1 product; at level 1 Y = I + G, no product
+//   residual   R <- R + R G - G        1 product; skipped after the last level
+// The residual line is I - (I - R) f(R) (proof of Lemma 5.7), which for an
+// exact kernel T_m is the next power R^m (telescoping, Sec. 2.2). With
+// NEUMANN_FLAG_RESIDUAL_PAPER it is formed as I - (I - A) Y instead (eq.
+// generalradix). Storing G = f(R) - I rather than f(R) keeps the identity out
+// of the products and lets the residual combine small quantities.
+#include <math.h>
+#include <string.h>
+
+#include <map>
+#include <utility>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "neumann.h"
+
+using namespace neumann;
+
+namespace {
+
+enum Rep : uint32_t { REP_W = 1, REP_F64 = 2, REP_OPA = 4, REP_OPB = 8 };
+constexpr uint32_t REP_ALL = REP_W | REP_F64 | REP_OPA | REP_OPB;
+
+// Workspace matrices ("slots"). R and Y ping-pong: a product that reads one
+// of them as an operand writes the other.
+enum : int { SL_R0, SL_R1, SL_Y0, SL_Y1, SL_LF0, SL_LF1, SL_RF0, SL_RF1, SL_P1, SL_P2, SL_C, SL_G, SL_A0, SL_N };
+constexpr int SL_NONE = -1, SL_USER_A = -2, SL_USER_B = -3, SL_USER_S = -4;
+
+struct InRef {
+  int slot;
+  uint32_t rep;  // REP_W or REP_F64
+};
+
+struct OutSpec {
+  int slot;
+  uint32_t reps;
+  double acc, id;
+  double in[kMaxIn];
+};
+
+enum OpKind { OP_GEMM, OP_EWISE };
+
+struct Op {
+  OpKind kind;
+  int a, b;  // GEMM operands (a read as left operand, b as right operand)
+  int nin;
+  InRef in[kMaxIn];
+  int nout;
+  OutSpec out[kMaxOut];
+};
+
+enum Path { PATH_F64, PATH_F32, PATH_TC };
+
+constexpr int kMaxTimedProducts = 1 << 16;
+
+struct SlotBufs {
+  size_t w, f64, a_hi, a_lo, b_hi, b_lo;
+};
+constexpr size_t NOBUF = (size_t)-1;
+
+Op mk_gemm(int a, int b) {
+  Op op;
+  memset(&op, 0, sizeof(op));
+  op.kind = OP_GEMM;
+  op.a = a;
+  op.b = b;
+  return op;
+}
+
+Op mk_ewise() {
+  Op op;
+  memset(&op, 0, sizeof(op));
+  op.kind = OP_EWISE;
+  op.a = op.b = SL_NONE;
+  return op;
+}
+
+void add_in(Op& op, int slot, uint32_t rep) { op.in[op.nin++] = InRef{slot, rep}; }
+
+OutSpec& add_out(Op& op, int slot, uint32_t reps, double acc, double id) {
+  OutSpec& o = op.out[op.nout++];
+  memset(&o, 0, sizeof(o));
+  o.slot = slot;
+  o.reps = reps;
+  o.acc = acc;
+  o.id = id;
+  return o;
+}
+
+int mu_of(int m) {
+  switch (m) {
+    case 2: return 0;
+    case 3: return 1;
+    case 5: return 2;
+    case 9: return 3;
+    case 15: return 4;
+  }
+  return -1;
+}
+
+bool pure_power(int64_t k, int m, std::vector<int>* levels) {
+  levels->clear();
+  while (k > 1) {
+    if (k % m) return false;
+    k /= m;
+    levels->push_back(m);
+  }
+  return true;
+}
+
+}  // namespace
+
+struct neumann_plan_s {
+  int64_t n = 0, k = 0, npad = 0;
+  int radix = 0, dtype = 0;
+  uint32_t flags = 0;
+  Path path = PATH_F64;
+  int dt_io = DT_F64;
+  std::vector<int> levels;
+  int64_t formula = 0;
+  std::vector<Op> ops, mm_ops;
+  uint32_t reps[SL_N];
+  SlotBufs bufs[SL_N];
+  size_t ws_bytes = 0;
+  char* ws = nullptr;
+  bool ws_owned = false;
+  std::vector<TcMaps> maps, mm_maps;
+  bool maps_ready = false;
+  double c15[28];
+  cudaStream_t last_stream = nullptr;
+  std::vector<cudaEvent_t> events;
+  int timed = 0;
+  // batched
+  bool batched = false;
+  int count = 0;
+  int64_t max_n = 0;
+  std::map<int64_t, neumann_plan_s*> sub;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- scheduler
+
+struct Sched {
+  neumann_plan_s* p;
+  bool paper;
+
+  std::vector<Op>& ops() { return p->ops; }
+
+  // Kernel ops for G = f(R) - I. The last product also writes G (with greps)
+  // and, when ytarget != SL_NONE, the first partial sum Y = I + G.
+  void kernel(int m, int R, uint32_t greps, int ytarget, uint32_t yreps) {
+    auto tail = [&](Op& op, double acc, std::initializer_list<double> ins) {
+      // G = sum ins * inputs + acc * product; Y = I + G
+      if (greps) {
+        OutSpec& g = add_out(op, SL_G, greps, acc, 0.0);
+        int i = 0;
+        for (double c : ins) g.in[i++] = c;
+      }
+      if (ytarget != SL_NONE) {
+        OutSpec& y = add_out(op, ytarget, yreps, acc, 1.0);
+        int i = 0;
+        for (double c : ins) y.in[i++] = c;
+      }
+    };
+    if (m == 3) {  // T_3 = I + B + B^2 (Sec. 2.1): G = B + U
+      Op op = mk_gemm(R, R);
+      add_in(op, R, REP_W);
+      tail(op, 1.0, {1.0});
+      ops().push_back(op);
+    } else if (m == 5) {  // quinary (Sec. 2.3): U = B^2, V = U (B + U), G = B + U + V
+      Op op1 = mk_gemm(R, R);
+      add_in(op1, R, REP_W);
+      add_out(op1, SL_P1, REP_W | REP_OPA, 1.0, 0.0);
+      add_out(op1, SL_RF0, REP_OPB, 1.0, 0.0).in[0] = 1.0;
+      ops().push_back(op1);
+      Op op2 = mk_gemm(SL_P1, SL_RF0);
+      add_in(op2, R, REP_W);
+      add_in(op2, SL_P1, REP_W);
+      tail(op2, 1.0, {1.0, 1.0});
+      ops().push_back(op2);
+    } else if (m == 9) {  // Thm 3.1
+      // MM1: U = B B; emits U (value and left operand) and X = B + 2U (right operand)
+      Op op1 = mk_gemm(R, R);
+      add_in(op1, R, REP_W);
+      add_out(op1, SL_P1, REP_W | REP_OPA, 1.0, 0.0);
+      add_out(op1, SL_RF0, REP_OPB, 2.0, 0.0).in[0] = 1.0;
+      ops().push_back(op1);
+      // MM2: V = U X; emits P = 3/20 B + 2U + V, Q = 11/40 B - 1/8 U + 1/4 V,
+      //      C = B + 767/800 U + 15/32 V
+      Op op2 = mk_gemm(SL_P1, SL_RF0);
+      add_in(op2, R, REP_W);
+      add_in(op2, SL_P1, REP_W);
+      {
+        OutSpec& P = add_out(op2, SL_LF1, REP_OPA, 1.0, 0.0);
+        P.in[0] = 3.0 / 20.0;
+        P.in[1] = 2.0;
+        OutSpec& Q = add_out(op2, SL_RF1, REP_OPB, 0.25, 0.0);
+        Q.in[0] = 11.0 / 40.0;
+        Q.in[1] = -0.125;
+        OutSpec& C = add_out(op2, SL_C, REP_W, 15.0 / 32.0, 0.0);
+        C.in[0] = 1.0;
+        C.in[1] = 767.0 / 800.0;
+      }
+      ops().push_back(op2);
+      // MM3: W = P Q; G = W + C (T_9 = I + G)
+      Op op3 = mk_gemm(SL_LF1, SL_RF1);
+      add_in(op3, SL_C, REP_W);
+      tail(op3, 1.0, {1.0});
+      ops().push_back(op3);
+    } else if (m == 15) {  // Sec. 4.1, eq. factors / radix15kernel
+      const double* x = p->c15;
+      const double *l2 = x, *r2 = x + 3, *l3 = x + 6, *r3 = x + 10, *l4 = x + 14, *r4 = x + 19, *g = x + 24;
+      // P1 = B B; L2, R2 over (I, B, P1)
+      Op op1 = mk_gemm(R, R);
+      add_in(op1, R, REP_W);
+      add_out(op1, SL_P1, REP_W, 1.0, 0.0);
+      add_out(op1, SL_LF0, REP_OPA, l2[2], l2[0]).in[0] = l2[1];
+      add_out(op1, SL_RF0, REP_OPB, r2[2], r2[0]).in[0] = r2[1];
+      ops().push_back(op1);
+      // P2 = L2 R2; L3, R3 over (I, B, P1, P2); C = g1 B + g2 P1 + g3 P2
+      Op op2 = mk_gemm(SL_LF0, SL_RF0);
+      add_in(op2, R, REP_W);
+      add_in(op2, SL_P1, REP_W);
+      add_out(op2, SL_P2, REP_W, 1.0, 0.0);
+      {
+        OutSpec& L = add_out(op2, SL_LF1, REP_OPA, l3[3], l3[0]);
+        L.in[0] = l3[1];
+        L.in[1] = l3[2];
+        OutSpec& Rr = add_out(op2, SL_RF1, REP_OPB, r3[3], r3[0]);
+        Rr.in[0] = r3[1];
+        Rr.in[1] = r3[2];
+        OutSpec& C = add_out(op2, SL_C, REP_W, g[2], 0.0);
+        C.in[0] = g[0];
+        C.in[1] = g[1];
+      }
+      ops().push_back(op2);
+      // P3 = L3 R3; L4, R4 over (I, B, P1, P2, P3); C += g4 P3
+      Op op3 = mk_gemm(SL_LF1, SL_RF1);
+      add_in(op3, R, REP_W);
+      add_in(op3, SL_P1, REP_W);
+      add_in(op3, SL_P2, REP_W);
+      add_in(op3, SL_C, REP_W);
+      {
+        OutSpec& L = add_out(op3, SL_LF0, REP_OPA, l4[4], l4[0]);
+        L.in[0] = l4[1];
+        L.in[1] = l4[2];
+        L.in[2] = l4[3];
+        OutSpec& Rr = add_out(op3, SL_RF0, REP_OPB, r4[4], r4[0]);
+        Rr.in[0] = r4[1];
+        Rr.in[1] = r4[2];
+        Rr.in[2] = r4[3];
+        OutSpec& C = add_out(op3, SL_C, REP_W, g[3], 0.0);
+        C.in[3] = 1.0;
+      }
+      ops().push_back(op3);
+      // P4 = L4 R4; G = C + P4 (T~15 = I + G)
+      Op op4 = mk_gemm(SL_LF0, SL_RF0);
+      add_in(op4, SL_C, REP_W);
+      tail(op4, 1.0, {1.0});
+      ops().push_back(op4);
+    }
+  }
+
+  void levels() {
+    const std::vector<int>& lv = p->levels;
+    const int L = (int)lv.size();
+    int R = SL_R0, Rn = SL_R1, Y = SL_Y0, Yn = SL_Y1;
+    {  // R_0 = A in every representation; A kept as left operand for the paper-form residual
+      Op op = mk_ewise();
+      add_in(op, SL_USER_A, 0);
+      add_out(op, R, REP_ALL, 0.0, 0.0).in[0] = 1.0;
+      if (paper) add_out(op, SL_A0, REP_OPA, 0.0, 0.0).in[0] = 1.0;
+      ops().push_back(op);
+    }
+    bool y_is_I = true;
+    const uint32_t yreps = REP_F64 | REP_OPA | (paper ? REP_OPB : 0u);
+    for (int l = 0; l < L; ++l) {
+      const int m = lv[l];
+      const bool last = l == L - 1;
+      const bool need_res = !last;
+      const int ytarget = last ? SL_USER_S : Yn;
+      const uint32_t yr = last ? 0u : yreps;
+      int G = SL_G;
+      if (m == 2) {
+        G = R;  // f = 1 + z: G = R, no product (Sec. 5.5, Hensel)
+      } else {
+        uint32_t greps = 0;
+        if (!y_is_I) greps |= REP_OPB;
+        if (need_res && !paper) greps |= REP_OPB | REP_W;
+        kernel(m, R, greps, y_is_I ? ytarget : SL_NONE, yr);
+      }
+      const bool fuse_first_y = y_is_I && m == 2 && need_res && !paper;
+      if (!y_is_I) {  // concatenation Y <- Y + Y G
+        Op op = mk_gemm(Y, G);
+        add_in(op, Y, REP_F64);
+        add_out(op, ytarget, yr, 1.0, 0.0).in[0] = 1.0;
+        ops().push_back(op);
+      } else if (m == 2 && !fuse_first_y) {  // Y_1 = I + R_0, element-wise
+        Op op = mk_ewise();
+        add_in(op, R, REP_F64);
+        add_out(op, ytarget, yr, 0.0, 1.0).in[0] = 1.0;
+        ops().push_back(op);
+      }
+      if (need_res) {
+        if (paper) {  // R' = I - (I - A) Y' = I - Y' + A Y'
+          Op op = mk_gemm(SL_A0, ytarget);
+          add_in(op, ytarget, REP_F64);
+          add_out(op, Rn, REP_ALL, 1.0, 1.0).in[0] = -1.0;
+          ops().push_back(op);
+        } else if (m == 2) {  // R' = R R
+          Op op = mk_gemm(R, R);
+          add_out(op, Rn, REP_ALL, 1.0, 0.0);
+          if (fuse_first_y) {
+            add_in(op, R, REP_F64);
+            add_out(op, ytarget, yr, 0.0, 1.0).in[0] = 1.0;
+          }
+          ops().push_back(op);
+        } else {  // R' = R + R G - G
+          Op op = mk_gemm(R, G);
+          add_in(op, R, REP_F64);
+          add_in(op, G, REP_W);
+          OutSpec& o = add_out(op, Rn, REP_ALL, 1.0, 0.0);
+          o.in[0] = 1.0;
+          o.in[1] = -1.0;
+          ops().push_back(op);
+        }
+        int t = R;
+        R = Rn;
+        Rn = t;
+      }
+      if (!last) {
+        int t = Y;
+        Y = Yn;
+        Yn = t;
+      }
+      y_is_I = false;
+    }
+  }
+
+  // Horner-free naive chain (Sec. 2.1): S_2 = I + A, S_{i+1} = I + A S_i.
+  void naive() {
+    const int64_t k = p->k;
+    if (k == 2) {
+      Op op = mk_ewise();
+      add_in(op, SL_USER_A, 0);
+      add_out(op, SL_USER_S, 0, 0.0, 1.0).in[0] = 1.0;
+      ops().push_back(op);
+      return;
+    }
+    Op op = mk_ewise();
+    add_in(op, SL_USER_A, 0);
+    add_out(op, SL_R0, REP_OPA, 0.0, 0.0).in[0] = 1.0;
+    add_out(op, SL_Y0, REP_OPB, 0.0, 1.0).in[0] = 1.0;
+    ops().push_back(op);
+    int cur = SL_Y0, nxt = SL_Y1;
+    for (int64_t i = 3; i <= k; ++i) {
+      Op g = mk_gemm(SL_R0, cur);
+      add_out(g, i == k ? SL_USER_S : nxt, i == k ? 0u : REP_OPB, 1.0, 1.0);
+      ops().push_back(g);
+      int t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+
+  // Binary digits of k, most significant first (any k): doubling
+  // S_{2n} = S_n + S_n A^n, A^{2n} = A^n A^n; digit 1: S_{n+1} = S_n + A^n, A^{n+1} = A^n A.
+  void binary_digits() {
+    const int64_t k = p->k;
+    int nb = 0;
+    while ((k >> (nb + 1)) != 0) ++nb;  // digits after the leading one
+    {
+      Op op = mk_ewise();
+      add_in(op, SL_USER_A, 0);
+      add_out(op, SL_R0, REP_ALL, 0.0, 0.0).in[0] = 1.0;
+      add_out(op, SL_A0, REP_OPB, 0.0, 0.0).in[0] = 1.0;
+      ops().push_back(op);
+    }
+    int P = SL_R0, Pn = SL_R1, S = SL_Y0, Sn = SL_Y1;
+    bool s_is_I = true;
+    const uint32_t sreps = REP_F64 | REP_OPA;
+    size_t last_op = 0;
+    int last_out = 0;
+    for (int i = nb - 1; i >= 0; --i) {
+      const bool b = (k >> i) & 1;
+      const bool last = i == 0;
+      if (s_is_I) {
+        Op op = mk_ewise();
+        add_in(op, P, REP_F64);
+        add_out(op, Sn, sreps, 0.0, 1.0).in[0] = 1.0;
+        last_op = ops().size();
+        last_out = 0;
+        ops().push_back(op);
+      } else {
+        Op op = mk_gemm(S, P);
+        add_in(op, S, REP_F64);
+        add_out(op, Sn, sreps, 1.0, 0.0).in[0] = 1.0;
+        last_op = ops().size();
+        last_out = 0;
+        ops().push_back(op);
+      }
+      std::swap(S, Sn);
+      s_is_I = false;
+      if (!last || b) {
+        Op op = mk_gemm(P, P);
+        add_out(op, Pn, REP_ALL, 1.0, 0.0);
+        if (b) {
+          add_in(op, S, REP_F64);
+          add_out(op, Sn, sreps, 1.0, 0.0).in[0] = 1.0;
+          last_op = ops().size();
+          last_out = 1;
+        }
+        ops().push_back(op);
+        std::swap(P, Pn);
+        if (b) std::swap(S, Sn);
+      }
+      if (b && !last) {
+        Op op = mk_gemm(P, SL_A0);
+        add_out(op, Pn, REP_ALL, 1.0, 0.0);
+        ops().push_back(op);
+        std::swap(P, Pn);
+      }
+    }
+    OutSpec& o = ops()[last_op].out[last_out];
+    o.slot = SL_USER_S;
+    o.reps = 0;
+  }
+
+  void matmul() {
+    std::vector<Op>& mm = p->mm_ops;
+    Op a = mk_ewise();
+    add_in(a, SL_USER_A, 0);
+    add_out(a, SL_R0, REP_OPA, 0.0, 0.0).in[0] = 1.0;
+    mm.push_back(a);
+    Op b = mk_ewise();
+    add_in(b, SL_USER_B, 0);
+    add_out(b, SL_Y0, REP_OPB, 0.0, 0.0).in[0] = 1.0;
+    mm.push_back(b);
+    Op g = mk_gemm(SL_R0, SL_Y0);
+    add_out(g, SL_USER_S, 0, 1.0, 0.0);
+    mm.push_back(g);
+  }
+};
+
+// ---------------------------------------------------------------- layout
+
+void note_reps(neumann_plan_s* p, const std::vector<Op>& ops) {
+  for (const Op& op : ops) {
+    if (op.kind == OP_GEMM) {
+      p->reps[op.a] |= REP_OPA;
+      p->reps[op.b] |= REP_OPB;
+    }
+    for (int i = 0; i < op.nin; ++i)
+      if (op.in[i].slot >= 0) p->reps[op.in[i].slot] |= op.in[i].rep;
+    for (int j = 0; j < op.nout; ++j)
+      if (op.out[j].slot >= 0) p->reps[op.out[j].slot] |= op.out[j].reps;
+  }
+}
+
+void layout(neumann_plan_s* p) {
+  const size_t nn = (size_t)p->npad * (size_t)p->npad;
+  size_t off = 256;  // device status word(s)
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  for (int s = 0; s < SL_N; ++s) {
+    SlotBufs& b = p->bufs[s];
+    b.w = b.f64 = b.a_hi = b.a_lo = b.b_hi = b.b_lo = NOBUF;
+    const uint32_t r = p->reps[s];
+    if (!r) continue;
+    if (p->path == PATH_F64) {
+      b.w = take(nn * 8);
+    } else if (p->path == PATH_F32) {
+      if (r & (REP_W | REP_OPA | REP_OPB)) b.w = take(nn * 4);
+      if (r & REP_F64) b.f64 = take(nn * 8);
+    } else {
+      if (r & REP_W) b.w = take(nn * 4);
+      if (r & REP_F64) b.f64 = take(nn * 8);
+      if (r & REP_OPA) {
+        b.a_hi = take(nn * 2);
+        b.a_lo = take(nn * 2);
+      }
+      if (r & REP_OPB) {
+        b.b_hi = take(nn * 2);
+        b.b_lo = take(nn * 2);
+      }
+    }
+  }
+  p->ws_bytes = off;
+}
+
+int build(neumann_plan_s* p) {
+  Sched sc{p, (p->flags & NEUMANN_FLAG_RESIDUAL_PAPER) != 0};
+  p->ops.clear();
+  p->mm_ops.clear();
+  if (p->k == 1) {
+    Op op = mk_ewise();
+    add_out(op, SL_USER_S, 0, 0.0, 1.0);
+    p->ops.push_back(op);
+  } else if (p->radix == 1) {
+    sc.naive();
+  } else if (p->radix == 2 && (p->k & (p->k - 1)) != 0) {
+    sc.binary_digits();
+  } else {
+    sc.levels();
+  }
+  sc.matmul();
+  memset(p->reps, 0, sizeof(p->reps));
+  note_reps(p, p->ops);
+  note_reps(p, p->mm_ops);
+  layout(p);
+  return NEUMANN_OK;
+}
+
+int validate_and_levels(neumann_plan_s* p) {
+  const int64_t k = p->k;
+  p->levels.clear();
+  switch (p->radix) {
+    case 1:
+      p->formula = k - 1;
+      return NEUMANN_OK;
+    case 2: {
+      const bool pow2 = (k & (k - 1)) == 0;
+      if (!pow2 && !(p->flags & NEUMANN_FLAG_EXACT_K)) return NEUMANN_EINVAL;
+      int c = 0;
+      while ((int64_t(1) << c) < k) ++c;
+      p->formula = 2 * c;  // Sec. 6: 2 ceil(log2 k)
+      if (pow2) pure_power(k, 2, &p->levels);
+      return NEUMANN_OK;
+    }
+    case 3:
+    case 5:
+    case 9:
+    case 15:
+      if (!pure_power(k, p->radix, &p->levels)) return NEUMANN_EINVAL;
+      break;
+    case 0: {
+      int64_t q = k;
+      for (int m : {9, 5, 3, 2}) {
+        while (q % m == 0) {
+          p->levels.push_back(m);
+          q /= m;
+        }
+      }
+      if (q != 1) return NEUMANN_EINVAL;
+      break;
+    }
+    default:
+      return NEUMANN_EINVAL;
+  }
+  if ((int)p->levels.size() > NEUMANN_MAX_LEVELS) return NEUMANN_EINVAL;
+  p->formula = 0;
+  for (int m : p->levels) p->formula += mu_of(m) + 2;  // Sec. 2.2: C(m) = mu_m + 2
+  return NEUMANN_OK;
+}
+
+int init_plan(neumann_plan_s* p, int64_t n, int64_t k, int radix, int dtype, uint32_t flags) {
+  if (n < 1 || k < 1 || n > (int64_t(1) << 20)) return NEUMANN_EINVAL;
+  if (dtype < NEUMANN_FP64 || dtype > NEUMANN_SPLIT_FP16) return NEUMANN_EINVAL;
+  if (dtype == NEUMANN_SPLIT_FP16) return NEUMANN_ENOTSUP;
+  p->n = n;
+  p->k = k;
+  p->radix = radix;
+  p->dtype = dtype;
+  p->flags = flags;
+  p->npad = (n + 255) / 256 * 256;
+  p->path = dtype == NEUMANN_FP64 ? PATH_F64 : dtype == NEUMANN_FP32 ? PATH_F32 : PATH_TC;
+  p->dt_io = (dtype == NEUMANN_FP32 || (p->path == PATH_TC && (flags & NEUMANN_FLAG_IO_FP32))) ? DT_F32 : DT_F64;
+  int rc = validate_and_levels(p);
+  if (rc) return rc;
+  if (radix == 15 || radix == 0) {
+    double e, s15, s16;
+    if (!radix15_coefficients((flags & NEUMANN_FLAG_PRINTED_COEFFS) ? 1 : 0, p->c15, &e, &s15, &s16))
+      return NEUMANN_ENOTSUP;
+  }
+  return build(p);
+}
+
+// ---------------------------------------------------------------- execution
+
+size_t elem_bytes(int dt) { return dt == DT_F64 ? 8 : 4; }
+
+struct UserPtrs {
+  const void* A;
+  int64_t lda;
+  const void* B;
+  void* S;
+  int64_t lds;
+};
+
+EpiIn resolve_in(const neumann_plan_s* p, const InRef& r, const UserPtrs& u) {
+  EpiIn e;
+  if (r.slot == SL_USER_A) {
+    e.p = u.A;
+    e.ld = u.lda;
+    e.dt = p->dt_io;
+  } else if (r.slot == SL_USER_B) {
+    e.p = u.B;
+    e.ld = p->n;
+    e.dt = p->dt_io;
+  } else {
+    const SlotBufs& b = p->bufs[r.slot];
+    e.ld = p->npad;
+    if (p->path == PATH_F64) {
+      e.p = p->ws + b.w;
+      e.dt = DT_F64;
+    } else if (r.rep == REP_F64) {
+      e.p = p->ws + b.f64;
+      e.dt = DT_F64;
+    } else {
+      e.p = p->ws + b.w;
+      e.dt = DT_F32;
+    }
+  }
+  return e;
+}
+
+EpiOut resolve_out(const neumann_plan_s* p, const OutSpec& s, const EpiIn* ins, int nin, const UserPtrs& u) {
+  EpiOut o;
+  memset(&o, 0, sizeof(o));
+  o.acc_d = s.acc;
+  o.id_d = s.id;
+  o.acc_f = (float)s.acc;
+  o.id_f = (float)s.id;
+  for (int i = 0; i < kMaxIn; ++i) {
+    o.in_d[i] = s.in[i];
+    o.in_f[i] = (float)s.in[i];
+  }
+  auto dst = [&](void* ptr, int64_t ld, int dt, int pad) { o.dst[o.ndst++] = EpiDst{ptr, ld, dt, pad}; };
+  auto split = [&](size_t hi, size_t lo, int tr) {
+    o.split[o.nsplit++] = EpiSplit{p->ws + hi, p->ws + lo, p->npad, tr};
+  };
+  if (s.slot == SL_USER_S) {
+    dst(u.S, u.lds, p->dt_io, 0);
+  } else {
+    const SlotBufs& b = p->bufs[s.slot];
+    if (p->path == PATH_F64) {
+      dst(p->ws + b.w, p->npad, DT_F64, 1);
+    } else if (p->path == PATH_F32) {
+      if (s.reps & (REP_W | REP_OPA | REP_OPB)) dst(p->ws + b.w, p->npad, DT_F32, 1);
+      if (s.reps & REP_F64) dst(p->ws + b.f64, p->npad, DT_F64, 1);
+    } else {
+      if (s.reps & REP_W) dst(p->ws + b.w, p->npad, DT_F32, 1);
+      if (s.reps & REP_F64) dst(p->ws + b.f64, p->npad, DT_F64, 1);
+      if (s.reps & REP_OPA) split(b.a_hi, b.a_lo, 0);
+      if (s.reps & REP_OPB) split(b.b_hi, b.b_lo, 1);
+    }
+  }
+  bool f64 = p->path == PATH_F64;
+  for (int d = 0; d < o.ndst; ++d) f64 |= o.dst[d].dt == DT_F64;
+  for (int i = 0; i < nin; ++i) f64 |= (s.in[i] != 0.0 && ins[i].dt == DT_F64);
+  o.f64 = f64;
+  return o;
+}
+
+void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiParams* P) {
+  memset(P, 0, sizeof(*P));
+  P->n = (int)p->n;
+  P->npad = (int)p->npad;
+  P->status = reinterpret_cast<unsigned*>(p->ws);
+  P->nin = op.nin;
+  for (int i = 0; i < op.nin; ++i) P->in[i] = resolve_in(p, op.in[i], u);
+  P->nout = op.nout;
+  for (int j = 0; j < op.nout; ++j) P->out[j] = resolve_out(p, op.out[j], P->in, op.nin, u);
+}
+
+bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMaps>* maps) {
+  maps->assign(ops.size(), TcMaps());
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const Op& op = ops[i];
+    if (op.kind != OP_GEMM) continue;
+    const SlotBufs& a = p->bufs[op.a];
+    const SlotBufs& b = p->bufs[op.b];
+    if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + b.b_hi, p->ws + b.b_lo, p->npad,
+                      p->npad))
+      return false;
+  }
+  return true;
+}
+
+int attach(neumann_plan_s* p, void* ws) {
+  p->ws = reinterpret_cast<char*>(ws);
+  p->maps_ready = false;
+  if (p->path == PATH_TC) {
+    if (!build_maps(p, p->ops, &p->maps) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
+  }
+  p->maps_ready = true;
+  return NEUMANN_OK;
+}
+
+int ensure_workspace(neumann_plan_s* p, cudaStream_t s) {
+  if (p->ws) return NEUMANN_OK;
+  void* ws = nullptr;
+  if (cudaMalloc(&ws, p->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return NEUMANN_ENOMEM;
+  }
+  if (cudaMemsetAsync(ws, 0, 256, s) != cudaSuccess) {
+    cudaFree(ws);
+    return NEUMANN_ECUDA;
+  }
+  p->ws_owned = true;
+  int rc = attach(p, ws);
+  if (rc) {
+    cudaFree(ws);
+    p->ws = nullptr;
+    p->ws_owned = false;
+  }
+  return rc;
+}
+
+int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcMaps>& maps, const UserPtrs& u,
+            cudaStream_t s, bool timing) {
+  EpiParams P;
+  int gi = p->timed;  // timing accumulates over evaluations until neumann_plan_timing reads it
+  if (timing) {
+    int ng = 0;
+    for (const Op& op : ops) ng += op.kind == OP_GEMM;
+    if (p->timed + ng > kMaxTimedProducts) return NEUMANN_EINVAL;
+    while ((int)p->events.size() < 2 * (p->timed + ng)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return NEUMANN_ECUDA;
+      p->events.push_back(e);
+    }
+  }
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const Op& op = ops[i];
+    make_params(p, op, u, &P);
+    cudaError_t err;
+    if (op.kind == OP_EWISE) {
+      err = launch_ewise(P, s);
+    } else {
+      if (timing) cudaEventRecord(p->events[2 * gi], s);
+      if (p->path == PATH_F64) {
+        err = launch_simt_gemm_f64(reinterpret_cast<const double*>(p->ws + p->bufs[op.a].w),
+                                   reinterpret_cast<const double*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, P, s);
+      } else if (p->path == PATH_F32) {
+        err = launch_simt_gemm_f32(reinterpret_cast<const float*>(p->ws + p->bufs[op.a].w),
+                                   reinterpret_cast<const float*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, P, s);
+      } else {
+        err = launch_tc_gemm(maps[i], p->npad, P, s);
+      }
+      if (timing) cudaEventRecord(p->events[2 * gi + 1], s);
+      ++gi;
+    }
+    if (err != cudaSuccess) return NEUMANN_ECUDA;
+  }
+  if (timing) p->timed = gi;
+  return NEUMANN_OK;
+}
+
+bool overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const char* x = reinterpret_cast<const char*>(a);
+  const char* y = reinterpret_cast<const char*>(b);
+  return x < y + bbytes && y < x + abytes;
+}
+
+int eval_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t lds, cudaStream_t s) {
+  if (!A || !S || lda < p->n || lds < p->n) return NEUMANN_EINVAL;
+  const size_t es = elem_bytes(p->dt_io);
+  const size_t ab = ((size_t)(p->n - 1) * (size_t)lda + (size_t)p->n) * es;
+  const size_t sb = ((size_t)(p->n - 1) * (size_t)lds + (size_t)p->n) * es;
+  if (overlap(A, ab, S, sb)) return NEUMANN_EINVAL;
+  int rc = ensure_workspace(p, s);
+  if (rc) return rc;
+  p->last_stream = s;
+  UserPtrs u{A, lda, nullptr, S, lds};
+  return run_ops(p, p->ops, p->maps, u, s, (p->flags & NEUMANN_FLAG_TIMING) != 0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int neumann_plan_create(neumann_plan_t* out, int64_t n, int64_t k, int radix, int dtype, uint32_t flags) {
+  if (!out) return NEUMANN_EINVAL;
+  *out = nullptr;
+  neumann_plan_s* p = new (std::nothrow) neumann_plan_s();
+  if (!p) return NEUMANN_ENOMEM;
+  int rc;
+  try {
+    rc = init_plan(p, n, k, radix, dtype, flags);
+  } catch (...) {
+    rc = NEUMANN_ENOMEM;
+  }
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return NEUMANN_OK;
+}
+
+int neumann_plan_info(neumann_plan_t p, neumann_plan_info_t* info) {
+  if (!p || !info) return NEUMANN_EINVAL;
+  memset(info, 0, sizeof(*info));
+  info->n = p->batched ? p->max_n : p->n;
+  info->k = p->k;
+  info->radix = p->radix;
+  info->dtype = p->dtype;
+  info->flags = p->flags;
+  info->levels = (int)p->levels.size();
+  for (size_t i = 0; i < p->levels.size() && i < NEUMANN_MAX_LEVELS; ++i) info->level_radix[i] = p->levels[i];
+  info->products_formula = p->formula;
+  int64_t g = 0;
+  for (const Op& op : p->ops) g += op.kind == OP_GEMM;
+  info->products_executed = g;
+  info->launches = (int64_t)p->ops.size();
+  info->workspace_bytes = p->ws_bytes;
+  info->padded_n = p->npad;
+  return NEUMANN_OK;
+}
+
+int neumann_plan_set_workspace(neumann_plan_t p, void* ws, size_t bytes) {
+  if (!p || !ws || bytes < p->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255)) return NEUMANN_EINVAL;
+  if (p->ws_owned) {
+    cudaFree(p->ws);
+    p->ws_owned = false;
+  }
+  if (cudaMemset(ws, 0, 256) != cudaSuccess) return NEUMANN_ECUDA;
+  int rc = attach(p, ws);
+  if (rc) return rc;
+  for (auto& kv : p->sub) {
+    rc = neumann_plan_set_workspace(kv.second, ws, bytes);
+    if (rc) return rc;
+  }
+  return NEUMANN_OK;
+}
+
+int neumann_eval(neumann_plan_t p, const void* A, int64_t lda, void* S, int64_t lds, void* stream) {
+  if (!p || p->batched) return NEUMANN_EINVAL;
+  try {
+    return eval_one(p, A, lda, S, lds, reinterpret_cast<cudaStream_t>(stream));
+  } catch (...) {
+    return NEUMANN_ENOMEM;
+  }
+}
+
+int neumann_plan_matmul(neumann_plan_t p, const void* A, const void* B, void* C, void* stream) {
+  if (!p || p->batched || !A || !B || !C) return NEUMANN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)p->n * (size_t)p->n * elem_bytes(p->dt_io);
+  if (overlap(A, bytes, C, bytes) || overlap(B, bytes, C, bytes)) return NEUMANN_EINVAL;
+  int rc = ensure_workspace(p, s);
+  if (rc) return rc;
+  p->last_stream = s;
+  UserPtrs u{A, p->n, B, C, p->n};
+  return run_ops(p, p->mm_ops, p->mm_maps, u, s, false);
+}
+
+int neumann_plan_create_batched(neumann_plan_t* out, int count, int64_t max_n, int64_t k, int radix, int dtype,
+                                uint32_t flags) {
+  if (!out) return NEUMANN_EINVAL;
+  *out = nullptr;
+  if (count < 0) return NEUMANN_EINVAL;
+  neumann_plan_t p = nullptr;
+  int rc = neumann_plan_create(&p, max_n, k, radix, dtype, flags);
+  if (rc) return rc;
+  p->batched = true;
+  p->count = count;
+  p->max_n = max_n;
+  *out = p;
+  return NEUMANN_OK;
+}
+
+int neumann_eval_batched(neumann_plan_t p, int count, const int64_t* n, const void* const* A, void* const* S,
+                         void* stream) {
+  if (!p || !p->batched || count < 0 || count > p->count) return NEUMANN_EINVAL;
+  if (count == 0) return NEUMANN_OK;
+  if (!n || !A || !S) return NEUMANN_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || n[i] > p->max_n || !A[i] || !S[i]) return NEUMANN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  try {
+    int rc = ensure_workspace(p, s);
+    if (rc) return rc;
+    p->last_stream = s;
+    for (int i = 0; i < count; ++i) {
+      neumann_plan_s*& sp = p->sub[n[i]];
+      if (!sp) {
+        rc = neumann_plan_create(&sp, n[i], p->k, p->radix, p->dtype, p->flags & ~NEUMANN_FLAG_TIMING);
+        if (rc) {
+          p->sub.erase(n[i]);
+          return rc;
+        }
+        rc = attach(sp, p->ws);  // a smaller order needs no more workspace than max_n
+        if (rc) return rc;
+      }
+      rc = eval_one(sp, A[i], n[i], S[i], n[i], s);
+      if (rc) return rc;
+    }
+  } catch (...) {
+    return NEUMANN_ENOMEM;
+  }
+  return NEUMANN_OK;
+}
+
+int neumann_last_status(neumann_plan_t p, unsigned* status) {
+  if (!p || !status) return NEUMANN_EINVAL;
+  *status = 0;
+  if (!p->ws) return NEUMANN_OK;
+  if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return NEUMANN_ECUDA;
+  unsigned v = 0;
+  if (cudaMemcpy(&v, p->ws, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return NEUMANN_ECUDA;
+  if (v && cudaMemset(p->ws, 0, sizeof(v)) != cudaSuccess) return NEUMANN_ECUDA;
+  *status = v;
+  return NEUMANN_OK;
+}
+
+int neumann_plan_timing(neumann_plan_t p, float* ms, int cap, int* count) {
+  if (!p || !count || !(p->flags & NEUMANN_FLAG_TIMING)) return NEUMANN_EINVAL;
+  *count = p->timed;
+  if (p->timed == 0) return NEUMANN_OK;
+  if (cudaEventSynchronize(p->events[2 * p->timed - 1]) != cudaSuccess) return NEUMANN_ECUDA;
+  for (int i = 0; i < p->timed && i < cap && ms; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->events[2 * i], p->events[2 * i + 1]) != cudaSuccess) return NEUMANN_ECUDA;
+    ms[i] = t;
+  }
+  p->timed = 0;
+  return NEUMANN_OK;
+}
+
+int neumann_radix15_coefficients(int set, double* coef28, double* prefix_error, double* spill15, double* spill16) {
+  if ((set != 0 && set != 1) || !coef28) return NEUMANN_EINVAL;
+  double e = 0, a = 0, b = 0;
+  bool ok = radix15_coefficients(set, coef28, &e, &a, &b);
+  if (prefix_error) *prefix_error = e;
+  if (spill15) *spill15 = a;
+  if (spill16) *spill16 = b;
+  return ok ? NEUMANN_OK : NEUMANN_ENOTSUP;
+}
+
+void neumann_plan_destroy(neumann_plan_t p) {
+  if (!p) return;
+  for (auto& kv : p->sub) {
+    kv.second->ws = nullptr;  // shares the parent's workspace
+    neumann_plan_destroy(kv.second);
+  }
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->ws_owned) cudaFree(p->ws);
+  delete p;
+}
+
+const char* neumann_error_string(int code) {
+  switch (code) {
+    case NEUMANN_OK: return "ok";
+    case NEUMANN_EINVAL: return "invalid argument";
+    case NEUMANN_ENOMEM: return "out of memory";
+    case NEUMANN_ECUDA: return "CUDA error";
+    case NEUMANN_ENOTSUP: return "not supported";
+  }
+  return "unknown error";
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol include/neumann.h declares, validates arguments and plans the paper's
+product counts."""
+
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+nm = pytest.importorskip("paper_2602_11843_gb300", reason="library not built")
+from paper_2602_11843_gb300 import _capi as C  # noqa: E402
+
+from oracle import counts as CT  # noqa: E402
+from oracle import radix15 as R15  # noqa: E402
+
+
+def test_exports_every_declared_symbol():
+    import ctypes
+
+    hdr = open(os.path.join(ROOT, "include", "neumann.h")).read()
+    names = re.findall(r"^\s*(?:int|void|const char\*)\s+(neumann_\w+)\s*\(", hdr, re.M)
+    assert len(names) >= 12
+    lib = ctypes.CDLL(C.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("n,k,radix,dtype,flags", [
+    (0, 81, 9, C.FP64, 0), (10, 0, 9, C.FP64, 0), (10, 80, 9, C.FP64, 0), (10, 100, 15, C.FP64, 0),
+    (10, 12, 2, C.FP64, 0), (10, 7 * 9, 0, C.FP64, 0), (10, 81, 7, C.FP64, 0), (10, 81, 9, 9, 0),
+])
+def test_invalid_arguments(n, k, radix, dtype, flags):
+    with pytest.raises(C.NeumannError) as e:
+        C.neumann_plan_create(n, k, radix, dtype, flags)
+    assert e.value.code == C.EINVAL
+
+
+def test_fp16_not_supported_yet():
+    with pytest.raises(C.NeumannError) as e:
+        C.neumann_plan_create(64, 81, 9, C.SPLIT_FP16, 0)
+    assert e.value.code == C.ENOTSUP
+
+
+def _info(n, k, radix, dtype=C.FP64, flags=0):
+    h = C.neumann_plan_create(n, k, radix, dtype, flags)
+    try:
+        return C.neumann_plan_info(h)
+    finally:
+        C.neumann_plan_destroy(h)
+
+
+@pytest.mark.parametrize("k,radix", [(81, 9), (729, 9), (6561, 9), (225, 15), (3375, 15), (125, 5), (625, 5),
+                                     (27, 3), (128, 2), (1024, 2), (4096, 2)])
+def test_product_counts_match_paper(k, radix):
+    """products_formula = the paper's count (Table tab:results, Sec. 2.2 cost model,
+    Sec. 6 binary); products_executed = formula - 2 (no product with S_1 = I, no unused power)."""
+    info = _info(64, k, radix)
+    formula = CT.binary_formula(k) if radix == 2 else CT.radix_formula(k, radix)
+    assert info["products_formula"] == formula
+    assert info["products_executed"] == formula - 2
+    assert info["levels"] == [radix] * len(info["levels"])
+
+
+def test_naive_and_exact_binary_counts():
+    assert _info(32, 81, 1)["products_executed"] == 79
+    assert _info(32, 81, 1)["products_formula"] == 80
+    for k in (81, 100, 225, 729, 3375, 6561):
+        L, ones = k.bit_length(), bin(k).count("1")
+        assert _info(32, k, 2, flags=C.FLAG_EXACT_K)["products_executed"] == 2 * L + ones - 5
+
+
+def test_auto_levels():
+    info = _info(32, 2 * 3 * 5 * 9, 0)
+    assert sorted(info["levels"]) == [2, 3, 5, 9]
+    assert info["products_formula"] == 2 + 3 + 4 + 5
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_trivial_k_has_no_products(k):
+    for radix in (1, 2, 9):
+        if radix == 9 and k == 2:
+            continue
+        assert _info(16, k, radix)["products_executed"] == 0
+
+
+def test_workspace_layout_padded():
+    info = _info(300, 81, 9, C.SPLIT_BF16)
+    assert info["padded_n"] == 512
+    assert info["workspace_bytes"] % 256 == 0 and info["workspace_bytes"] > 512 * 512 * 8
+
+
+def test_library_radix15_coefficients_match_oracle():
+    """The library refines the App. B values on the host in double precision;
+    the oracle refines them in multi-precision. Same reading, same solution."""
+    coef, err, s15, s16 = C.neumann_radix15_coefficients(0)
+    ref = R15.flatten(R15.load_refined(float))
+    assert max(abs(a - b) for a, b in zip(coef, ref)) < 1e-13
+    assert err < 1e-14
+    assert abs(s15 - 0.18520417118533553) < 1e-12 and abs(s16 - 0.4583601331249466) < 1e-12
+    pcoef, perr, _, _ = C.neumann_radix15_coefficients(1)
+    assert pcoef == R15.flatten(R15.printed(float))
+    assert 2e-3 < perr < 4e-3
+
+
+def test_batched_plan_and_empty_batch():
+    h = C.neumann_plan_create_batched(4, 256, 81, 9, C.FP32, 0)
+    try:
+        C.neumann_eval_batched(h, [], [], [])  # empty batch is a no-op
+        with pytest.raises(C.NeumannError):
+            C.neumann_eval_batched(h, [300], [1], [2])  # n above max_n
+    finally:
+        C.neumann_plan_destroy(h)

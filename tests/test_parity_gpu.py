@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (relative Frobenius error against the oracle result of the same
+scheme: S_k for exact schemes, Lemma 5.7's closed form for radix 15):
+  FP64        1e-12
+  FP32        1e-5
+  split-BF16  TOL_BF16[rho]; each operand is kept to ~2^-17 relative, so a
+              product carries ~1e-5 relative error, amplified by ||S|| <= 1/(1-rho)
+              across levels.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import closed_form as CF
+from oracle import evaluate as EV
+from workloads import generators as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL_BF16 = {0.5: 2e-4, 0.9: 1e-3, 0.97: 3e-3}
+
+
+def _nm():
+    import paper_2602_11843_gb300 as nm
+
+    return nm
+
+
+def _tol(dtype, rho):
+    return TOL[dtype] if dtype in TOL else TOL_BF16[rho]
+
+
+def _run(A_np, k, radix, dtype, flags=0):
+    nm = _nm()
+    n = A_np.shape[0]
+    p = nm.Plan(n, k, radix, dtype, flags)
+    A = torch.tensor(A_np, dtype=p.io_dtype, device="cuda")
+    S = p(A)
+    torch.cuda.synchronize()
+    st = p.status()
+    return S.double().cpu().numpy(), st, p
+
+
+# ---------------------------------------------------------------- products
+
+@pytest.mark.parametrize("dtype,tol", [("fp64", 1e-14), ("fp32", 2e-6), ("split_bf16", 2e-5)])
+@pytest.mark.parametrize("n", [1, 17, 200, 256, 300, 513])
+def test_matmul_against_fp64_reference(dtype, tol, n):
+    """C = A B of each arithmetic against an FP64 product (torch on the CPU)."""
+    nm = _nm()
+    rng = np.random.default_rng(n)
+    A_np, B_np = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    p = nm.Plan(n, 2, 2, dtype)
+    A = torch.tensor(A_np, dtype=p.io_dtype, device="cuda")
+    B = torch.tensor(B_np, dtype=p.io_dtype, device="cuda")
+    C = p.matmul(A, B)
+    torch.cuda.synchronize()
+    ref = (A.double().cpu() @ B.double().cpu()).numpy()
+    assert p.status() == 0
+    assert CF.rel_fro(C.double().cpu().numpy(), ref) < tol
+
+
+# ---------------------------------------------------------------- schemes, small n
+
+SCHEMES = [(1, 81, 0), (2, 64, 0), (2, 81, 1), (3, 27, 0), (5, 125, 0), (9, 81, 0), (9, 729, 0),
+           (15, 225, 0), (15, 3375, 0), (0, 360, 0)]
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+@pytest.mark.parametrize("radix,k,exact", SCHEMES)
+@pytest.mark.parametrize("n", [200, 300])
+def test_scheme_parity_planted(dtype, radix, k, exact, n):
+    nm = _nm()
+    rho = 0.9
+    pl = G.planted_symmetric(n, rho, 100 + n)
+    ref = EV.planted_reference(pl["V"], pl["lam"], k, 15 if radix == 15 else 1)
+    S, st, p = _run(pl["A"], k, radix, dtype, nm.FLAG_EXACT_K if exact else 0)
+    assert st == 0
+    assert CF.rel_fro(S, ref) < _tol(dtype, rho)
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+@pytest.mark.parametrize("radix,k,exact", [(1, 81, 0), (2, 128, 0), (2, 81, 1), (9, 81, 0), (15, 225, 0)])
+def test_scheme_parity_nonsymmetric(dtype, radix, k, exact):
+    """Nonsymmetric Gaussian input (||A||_2 = 0.5) against the oracle's matrix schemes."""
+    nm = _nm()
+    g = G.gaussian_scaled(300, 0.5, 7)
+    ref, _ = EV.evaluate(g["A"], k, radix)
+    S, st, _ = _run(g["A"], k, radix, dtype, nm.FLAG_EXACT_K if exact else 0)
+    assert st == 0
+    assert CF.rel_fro(S, ref) < _tol(dtype, 0.5)
+
+
+@pytest.mark.parametrize("n,k,radix", [(1, 81, 9), (1, 5, 1), (17, 1, 9), (17, 2, 1), (17, 2, 2), (17, 9, 9),
+                                       (33, 15, 15), (5, 7, 2)])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+def test_edge_cases(n, k, radix, dtype):
+    nm = _nm()
+    g = G.gaussian_scaled(n, 0.5, 11)
+    ref, _ = EV.evaluate(g["A"], k, radix)
+    S, st, _ = _run(g["A"], k, radix, dtype, nm.FLAG_EXACT_K if radix == 2 else 0)
+    assert st == 0
+    assert CF.rel_fro(S, ref) < _tol(dtype, 0.5)
+
+
+def test_residual_paper_form_and_printed_coefficients():
+    nm = _nm()
+    pl = G.planted_symmetric(256, 0.9, 5)
+    ref = EV.planted_reference(pl["V"], pl["lam"], 225, 15)
+    S, st, _ = _run(pl["A"], 225, 15, "fp64", nm.FLAG_RESIDUAL_PAPER)
+    assert st == 0 and CF.rel_fro(S, ref) < 1e-12
+    refp = EV.planted_reference(pl["V"], pl["lam"], 225, 15, coef15="printed")
+    S, st, _ = _run(pl["A"], 225, 15, "fp64", nm.FLAG_PRINTED_COEFFS)
+    assert st == 0 and CF.rel_fro(S, refp) < 1e-12
+
+
+def test_leading_dimensions_and_io_fp32():
+    nm = _nm()
+    g = G.gaussian_scaled(100, 0.5, 3)
+    ref, _ = EV.evaluate(g["A"], 81, 9)
+    p = nm.Plan(100, 81, 9, "fp64")
+    big = torch.zeros((100, 160), dtype=torch.float64, device="cuda")
+    big[:, :100] = torch.tensor(g["A"], device="cuda")
+    out = torch.full((100, 130), 7.0, dtype=torch.float64, device="cuda")
+    nm.neumann_eval(p.handle, big.data_ptr(), 160, out.data_ptr(), 130, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert CF.rel_fro(out[:, :100].cpu().numpy(), ref) < 1e-12
+    assert bool((out[:, 100:] == 7.0).all())  # nothing written past n
+    S, st, _ = _run(g["A"], 81, 9, "split_bf16", nm.FLAG_IO_FP32)
+    assert st == 0 and CF.rel_fro(S, ref) < 2e-4
+
+
+def test_nonfinite_status_for_divergent_input():
+    """Undamped Jacobi splitting has rho(A) > 1; S_k overflows and the epilogue
+    reports NEUMANN_STATUS_NONFINITE instead of trapping."""
+    nm = _nm()
+    m = G.jacobi_batch(1, 4, sizes=(64,), damped=False)[0]
+    for dtype in ("fp32", "split_bf16"):
+        S, st, _ = _run(m["A"], 15 ** 3, 15, dtype)
+        assert st & nm.STATUS_NONFINITE
+
+
+def test_timing_flag_reports_every_product():
+    nm = _nm()
+    pl = G.planted_symmetric(512, 0.9, 9)
+    _, st, p = _run(pl["A"], 225, 15, "split_bf16", nm.FLAG_TIMING)
+    t = p.timing()
+    assert len(t) == p.info["products_executed"] == 10 and all(x > 0 for x in t)
+
+
+def test_batched_matches_oracle():
+    nm = _nm()
+    mats = G.jacobi_batch(24, 4001)
+    for dtype in ("fp32", "split_bf16"):
+        bp = nm.BatchedPlan(len(mats), 256, 81, 9, dtype)
+        dt = torch.float32 if dtype == "fp32" else torch.float64
+        As = [torch.tensor(m["A"], dtype=dt, device="cuda") for m in mats]
+        outs = bp(As)
+        torch.cuda.synchronize()
+        assert bp.status() == 0
+        for m, o in zip(mats, outs):
+            ref, _ = EV.evaluate(m["A"], 81, 9)
+            assert CF.rel_fro(o.double().cpu().numpy(), ref) < (1e-5 if dtype == "fp32" else 2e-3)
+
+
+# ---------------------------------------------------------------- full-size workloads
+
+def test_cfg1_full():
+    """n = 256, k = 81, ||A||_2 = 0.5: naive, squaring to 2^7, exact-k binary and radix 9, FP64."""
+    nm = _nm()
+    g = G.config_inputs(1)
+    for radix, k, fl in ((1, 81, 0), (2, 128, 0), (2, 81, nm.FLAG_EXACT_K), (9, 81, 0)):
+        ref, _ = EV.evaluate(g["A"], k, radix)
+        S, st, _ = _run(g["A"], k, radix, "fp64", fl)
+        assert st == 0 and CF.rel_fro(S, ref) < 1e-12
+        # (I - A) S_k = I - A^k
+        I = np.eye(256)
+        lhs = (I - g["A"]) @ S
+        rhs = I - np.linalg.matrix_power(g["A"], k)
+        assert np.linalg.norm(lhs - rhs) < 1e-12 * np.linalg.norm(rhs)
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+@pytest.mark.parametrize("radix,k", [(9, 729), (15, 225)])
+def test_cfg2_full(dtype, radix, k):
+    pl = G.config_inputs(2)
+    ref = EV.planted_reference(pl["V"], pl["lam"], k, radix)
+    S, st, _ = _run(pl["A"], k, radix, dtype)
+    assert st == 0 and CF.rel_fro(S, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("radix,k", [(15, 3375), (9, 6561)])
+def test_cfg3_full_split_bf16(radix, k):
+    pl = G.config_inputs(3)
+    ref = EV.planted_reference(pl["V"], pl["lam"], k, radix)
+    S, st, _ = _run(pl["A"], k, radix, "split_bf16")
+    assert st == 0
+    err = CF.rel_fro(S, ref)
+    print(f"cfg3 radix {radix} k {k} split-bf16 rel err {err:.3e}")
+    assert err < TOL_BF16[0.97]
