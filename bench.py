@@ -314,8 +314,8 @@ def run_ours(args, wl):
         flops = 2.0 * n ** 3
         # CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes (x 2 flop) at the
         # maximum SM clock; FP64 at 1/64 of the FP32 rate
-        clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        fp32_peak = 152 * 128 * 2 * clk / 1e12
+        sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        fp32_peak = 152 * 128 * 2 * sm_hz / 1e12
         peak = fp32_peak if wl["dtype"] == "fp32" else fp32_peak / 64
         roof = {"bound": "alu", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "kernel": "simt_gemm_kernel",

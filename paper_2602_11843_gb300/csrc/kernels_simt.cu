@@ -49,11 +49,16 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
   }
   __syncthreads();
 
-  T acc[8][8];
+  // FP32: two-level accumulation. Products are summed into `part` for 64
+  // consecutive k and then added to `acc`, so each rounding error grows with
+  // sqrt(64) + sqrt(K/64) instead of sqrt(K) (K = 4096: 16 vs 64 units).
+  constexpr bool kTwoLevel = sizeof(T) == 4;
+  constexpr int kFlush = 64 / BK;  // k tiles per partial sum
+  T acc[8][8], part[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < 8; ++j) acc[i][j] = part[i][j] = T(0);
 
   for (int kt = 0; kt < ktiles; ++kt) {
     const int cur = kt & 1;
@@ -81,7 +86,21 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) {
+          if (kTwoLevel)
+            part[i][j] = fma(a[i], b[j], part[i][j]);
+          else
+            acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+    }
+    if (kTwoLevel && ((kt + 1) % kFlush == 0 || !more)) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          acc[i][j] += part[i][j];
+          part[i][j] = T(0);
+        }
     }
     if (more) {
 #pragma unroll
@@ -98,9 +117,9 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
   for (int i = 0; i < 8; ++i) {
     const int r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
-      bad |= epi_element<T>(P, r, c, acc[i][j]);
+    for (int h = 0; h < 2; ++h) {
+      const T(&a4)[4] = *reinterpret_cast<const T(*)[4]>(&acc[i][4 * h]);
+      bad |= epi_row<4, T>(P, r, n0 + h * 64 + tx * 4, a4);
     }
   }
   epi_flag(P, bad);

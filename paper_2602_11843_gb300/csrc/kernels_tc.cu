@@ -5,13 +5,18 @@
 //   Ahi Bhi + Ahi Blo + Alo Bhi
 // (the lo*lo term, ~2^-18 relative, is dropped), all three issued as
 // tcgen05.mma kind::f16 instructions into one FP32 accumulator in tensor
-// memory. One CTA computes a 128 x 256 output tile:
+// memory.
+//
+// The kernel is persistent and warp-specialised: one CTA per SM walks the
+// 128 x 256 output tiles (tile = blockIdx.x + i * gridDim.x, grouped raster):
 //   warp 0 lane 0  TMA producer: four tiles per stage (Ahi, Alo, Bhi, Blo),
 //                  K = 32 per stage (64-byte rows, 64B swizzle), 4 stages
-//   warp 1 lane 0  MMA issuer: 2 K-slices x 3 products per stage, then a
-//                  tcgen05.commit that frees the stage
-//   warps 0-3      epilogue: tcgen05.ld of the 128 x 256 accumulator (each warp
-//                  owns 32 TMEM lanes = 32 rows) and the fused epilogue.
+//   warp 1         allocates tensor memory; lane 0 issues the MMAs: 2 K-slices
+//                  x 3 products per stage, tcgen05.commit frees the stage
+//   warps 2-5      epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//                  lanes 32 (w % 4) .. +31 = 32 rows) and the fused epilogue
+// Two 128 x 256 FP32 accumulators (all 512 TMEM columns) alternate between
+// tiles, so the epilogue of one tile runs while the next tile's MMAs issue.
 // A is read row-major (K-major); B is read from its transpose (row j of the
 // stored array is column j of B), which makes it K-major too.
 //
@@ -32,13 +37,14 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 32;  // bf16 elements per stage row = 64 bytes
 constexpr int STAGES = 4;
-constexpr int THREADS = 128;
+constexpr int THREADS = 192;
 constexpr uint32_t A_TILE = BM * BK * 2;  // 8 KiB
 constexpr uint32_t B_TILE = BN * BK * 2;  // 16 KiB
 constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 256;
-constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s; one CTA normally takes < 1 ms
+constexpr uint32_t ACC_COLS = BN;              // one FP32 accumulator: 128 lanes x 256 columns
+constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // double-buffered
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s; a whole launch normally takes < 20 ms
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
@@ -152,36 +158,45 @@ __device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int* t
   *tn = in / gs;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
                          int ktiles, int tiles_m, int tiles_n, const __grid_constant__ EpiParams P) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // barriers: full[S], empty[S], tfull[2], tempty[2], drain
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int tm, tn;
-  raster(blockIdx.x, tiles_m, tiles_n, &tm, &tn);
+  const int ntiles = tiles_m * tiles_n;
   const uint32_t smem_base = smem_u32(smem);
   const uint32_t bar_base = smem_u32(bars);
-  auto full_bar = [&](int s) { return bar_base + 8u * s; };
-  auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
-  const uint32_t acc_bar = bar_base + 8u * (2 * STAGES);
+  auto full_bar = [&](uint32_t s) { return bar_base + 8u * s; };
+  auto empty_bar = [&](uint32_t s) { return bar_base + 8u * (STAGES + s); };
+  auto tfull_bar = [&](uint32_t b) { return bar_base + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](uint32_t b) { return bar_base + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar_base + 8u * (2 * STAGES + 4);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    mbar_init(acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 4);  // lane 0 of each epilogue warp
+    }
+    mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(TMEM_COLS)
                  : "memory");
@@ -192,87 +207,128 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_ahi)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_alo)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_bhi)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_blo)) : "memory");
-    int issued = 0;
-    for (int kb = 0; kb < ktiles; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES) {
-        if (!mbar_wait(empty_bar(s), ph ^ 1u) || *abort_flag) {
-          *abort_flag = 1;
-          break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_ahi)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_alo)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_bhi)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_blo)) : "memory");
+      uint32_t kg = 0;  // stage loads issued so far
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int tm, tn;
+        raster(tile, tiles_m, tiles_n, &tm, &tn);
+        for (int kb = 0; kb < ktiles; ++kb) {
+          const uint32_t s = kg % STAGES;
+          const uint32_t ph = (kg / STAGES) & 1u;
+          if (kg >= STAGES && (!mbar_wait(empty_bar(s), ph ^ 1u) || *abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = smem_base + s * STAGE_BYTES;
+          mbar_expect_tx(full_bar(s), STAGE_BYTES);
+          tma_load_2d(st, &tm_ahi, full_bar(s), kb * BK, tm * BM);
+          tma_load_2d(st + A_TILE, &tm_alo, full_bar(s), kb * BK, tm * BM);
+          tma_load_2d(st + 2 * A_TILE, &tm_bhi, full_bar(s), kb * BK, tn * BN);
+          tma_load_2d(st + 2 * A_TILE + B_TILE, &tm_blo, full_bar(s), kb * BK, tn * BN);
+          ++kg;
         }
       }
-      const uint32_t st = smem_base + s * STAGE_BYTES;
-      mbar_expect_tx(full_bar(s), STAGE_BYTES);
-      tma_load_2d(st, &tm_ahi, full_bar(s), kb * BK, tm * BM);
-      tma_load_2d(st + A_TILE, &tm_alo, full_bar(s), kb * BK, tm * BM);
-      tma_load_2d(st + 2 * A_TILE, &tm_bhi, full_bar(s), kb * BK, tn * BN);
-      tma_load_2d(st + 2 * A_TILE + B_TILE, &tm_blo, full_bar(s), kb * BK, tn * BN);
-      ++issued;
+      if (!ok) {
+        *abort_flag = 1;
+        // drain: wait (bounded) for the last load issued into each stage
+        for (uint32_t q = (kg > STAGES ? kg - STAGES : 0); q < kg; ++q)
+          mbar_wait(full_bar(q % STAGES), (q / STAGES) & 1u);
+      }
     }
-    if (*abort_flag) {
-      // drain: wait (bounded) for the last load issued into each stage
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        mbar_wait(full_bar(kb % STAGES), (uint32_t)(kb / STAGES) & 1u);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      uint32_t kg = 0;
+      bool ok = true;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+        const uint32_t buf = it & 1;
+        const uint32_t use = (uint32_t)it >> 1;
+        if (it >= 2 && (!mbar_wait(tempty_bar(buf), (use - 1) & 1u) || *abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + buf * ACC_COLS;
+        for (int kb = 0; kb < ktiles; ++kb) {
+          const uint32_t s = kg % STAGES;
+          const uint32_t ph = (kg / STAGES) & 1u;
+          if (!mbar_wait(full_bar(s), ph) || *abort_flag) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_base + s * STAGE_BYTES;
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint64_t a_hi = smem_desc(st + 32u * j);
+            const uint64_t a_lo = smem_desc(st + A_TILE + 32u * j);
+            const uint64_t b_hi = smem_desc(st + 2 * A_TILE + 32u * j);
+            const uint64_t b_lo = smem_desc(st + 2 * A_TILE + B_TILE + 32u * j);
+            umma_f16(d, a_hi, b_hi, (kb | j) != 0);
+            umma_f16(d, a_hi, b_lo, 1u);
+            umma_f16(d, a_lo, b_hi, 1u);
+          }
+          umma_commit(empty_bar(s));
+          ++kg;
+        }
+        if (ok) umma_commit(tfull_bar(buf));  // accumulator `buf` holds the finished tile
+      }
+      if (!ok) *abort_flag = 1;
+      // no MMA may be in flight when the tensor memory is freed
+      umma_commit(drain_bar);
+      mbar_wait(drain_bar, 0);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    for (int kb = 0; kb < ktiles; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(full_bar(s), ph) || *abort_flag) {
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    bool bad = false;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const uint32_t buf = it & 1;
+      const uint32_t use = (uint32_t)it >> 1;
+      const bool got = mbar_wait(tfull_bar(buf), use & 1u);
+      if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t st = smem_base + s * STAGE_BYTES;
-#pragma unroll
-      for (int j = 0; j < BK / 16; ++j) {
-        const uint64_t a_hi = smem_desc(st + 32u * j);
-        const uint64_t a_lo = smem_desc(st + A_TILE + 32u * j);
-        const uint64_t b_hi = smem_desc(st + 2 * A_TILE + 32u * j);
-        const uint64_t b_lo = smem_desc(st + 2 * A_TILE + B_TILE + 32u * j);
-        umma_f16(tmem, a_hi, b_hi, (kb | j) != 0);
-        umma_f16(tmem, a_hi, b_lo, 1u);
-        umma_f16(tmem, a_lo, b_hi, 1u);
-      }
-      umma_commit(empty_bar(s));
-    }
-    umma_commit(acc_bar);  // arrives once every MMA issued above has completed
-  }
-
-  // ---------------- epilogue ----------------
-  __syncwarp();
-  bool ok = mbar_wait(acc_bar, 0);
-  __syncwarp();
-  tc_fence_after();
-  if (!ok) *abort_flag = 1;
-  __syncwarp();
-  const bool aborted = __any_sync(0xffffffffu, *abort_flag != 0) != 0;
-  bool bad = false;
-  if (!aborted) {
-    const int r = tm * BM + warp * 32 + lane;
+      int tm, tn;
+      raster(tile, tiles_m, tiles_n, &tm, &tn);
+      const int r = tm * BM + q * 32 + lane;
+      const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-    for (int chunk = 0; chunk < BN / 32; ++chunk) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
-      const int c0 = tn * BN + chunk * 32;
+      for (int chunk = 0; chunk < BN / 32; ++chunk) {
+        uint32_t v[32];
+        __syncwarp();
+        tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
+        const int c0 = tn * BN + chunk * 32;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) bad |= epi_element<float>(P, r, c0 + j, __uint_as_float(v[j]));
+        for (int sub = 0; sub < 4; ++sub) {
+          float a8[8];
+#pragma unroll
+          for (int w = 0; w < 8; ++w) a8[w] = __uint_as_float(v[sub * 8 + w]);
+          bad |= epi_row<8, float>(P, r, c0 + sub * 8, a8);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(buf));
     }
+    epi_flag(P, bad);
   }
-  epi_flag(P, bad);
-  if (threadIdx.x == 0 && *abort_flag && P.status) atomicOr(P.status, 2u);
 
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (threadIdx.x == 0 && *abort_flag && P.status) atomicOr(P.status, 2u);
+  if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
@@ -325,9 +381,16 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
                                     (int)SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
   const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
-  tc_split_gemm_kernel<<<tiles_m * tiles_n, THREADS, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
-                                                                     (int)(npad / BK), tiles_m, tiles_n, P);
+  const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
+  tc_split_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
+                                                         (int)(npad / BK), tiles_m, tiles_n, P);
   return cudaGetLastError();
 }
 
