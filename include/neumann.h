@@ -177,6 +177,30 @@ int neumann_plan_timing(neumann_plan_t plan, float* ms, int cap, int* count);
 int neumann_radix15_coefficients(int set, double* coef28, double* prefix_error, double* spill15,
                                  double* spill16);
 
+/* C <- A B without any device allocation. The paper has no counterpart to this
+ * call; it exists for callers that cannot call cudaMalloc/cudaFree where they
+ * need a product: code running under an allocator that owns all device memory
+ * (a framework's caching allocator, an allocation hook that must not re-enter
+ * the driver's allocator) and latency-critical loops that cannot take the
+ * device-wide synchronisation cudaFree implies. Such callers cannot give a plan
+ * a workspace, nor let neumann_plan_matmul allocate one.
+ * Arithmetic and kernels are those of neumann_plan_matmul on a
+ * NEUMANN_SPLIT_BF16 plan (hi/lo BF16 operands, three tensor-core products,
+ * FP32 accumulation); the hi/lo operand scratch is a fixed 8 MiB device array
+ * inside the library, present on every GPU that loads it until the process exits.
+ *   n      order, 1 <= n <= 1024; larger n returns NEUMANN_EINVAL
+ *   A, B   device, double, n x n row-major, leading dimensions lda, ldb >= n; read only
+ *   C      device, double, n x n row-major, leading dimension ldc >= n; must not
+ *          overlap A or B
+ * Stream-ordered. The first call on a device looks up the scratch array's
+ * device address (a runtime query, no allocation); make that first call before
+ * any stream capture. Every call on a device shares the array: calls whose work
+ * overlaps on the GPU (different streams, different host threads) race and must
+ * be serialised by the caller. Device status bits are not reported.
+ * Errors: NEUMANN_EINVAL, NEUMANN_ENOTSUP (device index >= 64), NEUMANN_ECUDA. */
+int neumann_matmul_noalloc(int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
+                           int64_t ldc, void* stream);
+
 /* Release a plan and the workspace it allocated (not a caller-set one). NULL is ignored. */
 void neumann_plan_destroy(neumann_plan_t plan);
 

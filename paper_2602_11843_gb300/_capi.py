@@ -67,6 +67,8 @@ def _load():
         "neumann_plan_timing": (c_int, [P, POINTER(c_float), c_int, POINTER(c_int)]),
         "neumann_radix15_coefficients": (c_int, [c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double),
                                                  POINTER(c_double)]),
+        "neumann_matmul_noalloc": (c_int, [c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
+                                           c_void_p]),
         "neumann_plan_destroy": (None, [P]),
         "neumann_error_string": (ctypes.c_char_p, [c_int]),
     }
@@ -152,6 +154,12 @@ def neumann_radix15_coefficients(coef_set: int = 0):
     _check(_lib.neumann_radix15_coefficients(coef_set, c, byref(e), byref(a), byref(b)),
            "neumann_radix15_coefficients")
     return list(c), e.value, a.value, b.value
+
+
+def neumann_matmul_noalloc(n: int, A: int, lda: int, B: int, ldb: int, C: int, ldc: int, stream: int = 0) -> None:
+    """C = A B (FP64 in/out, split-BF16 tensor-core arithmetic) with no device
+    allocation; the operand scratch is a fixed array inside the library, n <= 1024."""
+    _check(_lib.neumann_matmul_noalloc(n, A, lda, B, ldb, C, ldc, stream), "neumann_matmul_noalloc")
 
 
 def neumann_plan_destroy(plan: int) -> None:
