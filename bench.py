@@ -322,6 +322,11 @@ def run_ours(args, wl):
                 "peak_source": "derived: 152 SM x 128 lanes x 2 flop x max SM clock (FP64: /64)",
                 "work_per_launch": "2n^3 flops", "launches_timed": len(prod_ms)}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # mean device time of each product of an evaluation, in launch order
+    per = info["products_executed"]
+    if prod_ms and per and len(prod_ms) % per == 0:
+        reps = len(prod_ms) // per
+        roof["per_product_ms"] = [round(sum(prod_ms[i::per]) / reps, 4) for i in range(per)]
     roof["effective_tflops"] = 2.0 * n ** 3 / (mean_prod_ms / 1e3) / 1e12
 
     line = {

@@ -1,0 +1,46 @@
+"""Small, fixed workloads for profiling the library's kernels under ncu.
+
+  python -m paper_2602_11843_gb300.profile_case matmul N REPS   split-BF16 product C = A B
+  python -m paper_2602_11843_gb300.profile_case r15 N REPS      radix-15, k = 3375, split-BF16
+
+Inputs are drawn on the device (no host copies): A, B ~ N(0, 1) for the
+product; for r15 a symmetric A with spectral radius about 0.45. Prints the
+plan's device status at the end; exits non-zero if it is not 0.
+"""
+
+from __future__ import annotations
+
+import sys
+
+
+def main(argv):
+    import torch
+
+    import paper_2602_11843_gb300 as nm
+
+    mode, n, reps = argv[0], int(argv[1]), int(argv[2])
+    g = torch.Generator(device="cuda").manual_seed(0)
+    if mode == "matmul":
+        A = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+        p = nm.Plan(n, 2, 2, "split_bf16")
+        C = torch.empty_like(A)
+        for _ in range(reps):
+            p.matmul(A, B, out=C)
+    elif mode == "r15":
+        X = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+        A = (X + X.T) * (0.45 / (2.0 * n ** 0.5))
+        p = nm.Plan(n, 3375, 15, "split_bf16")
+        S = torch.empty_like(A)
+        for _ in range(reps):
+            p(A, out=S)
+    else:
+        raise SystemExit(f"unknown case {mode}")
+    torch.cuda.synchronize()
+    st = p.status()
+    print("profile_case", mode, n, reps, "status", st)
+    return 0 if st == 0 else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))
