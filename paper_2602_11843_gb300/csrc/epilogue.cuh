@@ -22,18 +22,13 @@ __device__ __forceinline__ void split_store(const EpiSplit& s, int r, int c, flo
 }
 
 __device__ __forceinline__ void split_store_d(const EpiSplit& s, int r, int c, double v) {
-  // hi = RN_bf16(v) through FP32: v -> f32 is exact to 2^-24 relative, far below
-  // the 2^-17 the hi+lo pair keeps.
-  float vf = (float)v;
-  __nv_bfloat16 hi = __float2bfloat16_rn(vf);
-  float rem = (float)(v - (double)__bfloat162float(hi));
-  __nv_bfloat16 lo = __float2bfloat16_rn(rem);
-  int64_t off = s.transposed ? (int64_t)c * s.ld + r : (int64_t)r * s.ld + c;
-  reinterpret_cast<__nv_bfloat16*>(s.hi)[off] = hi;
-  reinterpret_cast<__nv_bfloat16*>(s.lo)[off] = lo;
+  // The pair is formed from RN_fp32(v): FP32 keeps 24 bits, the hi+lo pair 16.
+  split_store(s, r, c, (float)v);
 }
 
-// Write 0 to every workspace destination of element (r, c), n <= r or c < npad.
+// Write 0 to every workspace destination of element (r, c), n <= r or c < npad
+// (transposed splits excepted when kSkipT).
+template <bool kSkipT = false>
 __device__ __forceinline__ void epi_padding(const EpiParams& P, int r, int c) {
 #pragma unroll 1
   for (int j = 0; j < P.nout; ++j) {
@@ -49,6 +44,7 @@ __device__ __forceinline__ void epi_padding(const EpiParams& P, int r, int c) {
     }
     for (int s = 0; s < o.nsplit; ++s) {
       const EpiSplit& sp = o.split[s];
+      if (kSkipT && sp.transposed) continue;
       int64_t off = sp.transposed ? (int64_t)c * sp.ld + r : (int64_t)r * sp.ld + c;
       reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = __float2bfloat16_rn(0.f);
       reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = __float2bfloat16_rn(0.f);
@@ -59,13 +55,17 @@ __device__ __forceinline__ void epi_padding(const EpiParams& P, int r, int c) {
 // Apply every output of the epilogue to element (r, c) with accumulator value
 // acc; r, c < npad. Inside the n x n block the outputs are formed; in the
 // padding only workspace buffers are written (with 0). Returns true on a
-// non-finite result. Not inlined: one copy serves every call site, and P is a
-// __grid_constant__ kernel parameter, so passing it by reference copies nothing.
-template <typename AccT>
-__device__ __noinline__ bool epi_element(const EpiParams& P, int r, int c, AccT acc) {
+// non-finite result.
+// kDeferT: outputs' transposed split stores are not written; the value they
+// would split (RN_fp32 of the output) is left in tv[j] for the caller to write
+// through a shared-memory transpose (0 in the padding).
+template <typename AccT, bool kDeferT>
+__device__ __forceinline__ bool epi_element_impl(const EpiParams& P, int r, int c, AccT acc, float* tv) {
   bool bad = false;
   if (r >= P.n || c >= P.n) {
-    epi_padding(P, r, c);
+    if (kDeferT)
+      for (int j = 0; j < kMaxOut; ++j) tv[j] = 0.f;
+    epi_padding<kDeferT>(P, r, c);
     return false;
   }
   float fin[kMaxIn];
@@ -89,11 +89,25 @@ __device__ __noinline__ bool epi_element(const EpiParams& P, int r, int c, AccT 
   for (int j = 0; j < P.nout; ++j) {
     const EpiOut& o = P.out[j];
     if (o.f64) {
-      double v = o.acc_d * (double)acc + (diag ? o.id_d : 0.0);
+      double v;
+      if (sizeof(AccT) == 8) {
+        v = o.acc_d * (double)acc + (diag ? o.id_d : 0.0);
 #pragma unroll
-      for (int i = 0; i < kMaxIn; ++i) {
-        if (i < P.nin && o.in_d[i] != 0.0)
-          v += o.in_d[i] * (P.in[i].dt == DT_F64 ? din[i] : (double)fin[i]);
+        for (int i = 0; i < kMaxIn; ++i) {
+          if (i < P.nin && o.in_d[i] != 0.0)
+            v += o.in_d[i] * (P.in[i].dt == DT_F64 ? din[i] : (double)fin[i]);
+        }
+      } else {
+        // FP32 terms summed in FP32 (they carry FP32 rounding already); the FP64
+        // inputs (a partial sum Y or residual R) are added in FP64, one DFMA each.
+        float vf = o.acc_f * (float)acc;
+#pragma unroll
+        for (int i = 0; i < kMaxIn; ++i)
+          if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) vf = fmaf(o.in_f[i], fin[i], vf);
+        v = (double)vf + (diag ? o.id_d : 0.0);
+#pragma unroll
+        for (int i = 0; i < kMaxIn; ++i)
+          if (i < P.nin && o.in_d[i] != 0.0 && P.in[i].dt == DT_F64) v = fma(o.in_d[i], din[i], v);
       }
       if (!isfinite(v)) bad = true;
       for (int d = 0; d < o.ndst; ++d) {
@@ -104,7 +118,12 @@ __device__ __noinline__ bool epi_element(const EpiParams& P, int r, int c, AccT 
         else
           reinterpret_cast<float*>(ds.p)[off] = (float)v;
       }
-      for (int s = 0; s < o.nsplit; ++s) split_store_d(o.split[s], r, c, v);
+      for (int s = 0; s < o.nsplit; ++s) {
+        if (kDeferT && o.split[s].transposed)
+          tv[j] = (float)v;
+        else
+          split_store_d(o.split[s], r, c, v);
+      }
     } else {
       float v = o.acc_f * (float)acc + (diag ? o.id_f : 0.f);
 #pragma unroll
@@ -121,10 +140,22 @@ __device__ __noinline__ bool epi_element(const EpiParams& P, int r, int c, AccT 
         else
           reinterpret_cast<float*>(ds.p)[off] = v;
       }
-      for (int s = 0; s < o.nsplit; ++s) split_store(o.split[s], r, c, v);
+      for (int s = 0; s < o.nsplit; ++s) {
+        if (kDeferT && o.split[s].transposed)
+          tv[j] = v;
+        else
+          split_store(o.split[s], r, c, v);
+      }
     }
   }
   return bad;
+}
+
+// One copy serves every call site of the GEMM kernels; P is a __grid_constant__
+// kernel parameter, so passing it by reference copies nothing.
+template <typename AccT>
+__device__ __noinline__ bool epi_element(const EpiParams& P, int r, int c, AccT acc) {
+  return epi_element_impl<AccT, false>(P, r, c, acc, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,10 +213,10 @@ __device__ __forceinline__ void st_row(const EpiOut& o, int r, int c0, const V (
     const EpiSplit& sp = o.split[s];
     __nv_bfloat16 hi[W], lo[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
+    for (int w = 0; w < W; ++w) {  // from RN_fp32(v): FP32 keeps 24 bits, the pair 16
       const float vf = (float)v[w];
       hi[w] = __float2bfloat16_rn(vf);
-      lo[w] = __float2bfloat16_rn((float)(v[w] - (V)__bfloat162float(hi[w])));
+      lo[w] = __float2bfloat16_rn(vf - __bfloat162float(hi[w]));
     }
     if (sp.transposed) {
 #pragma unroll
@@ -243,14 +274,37 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, int r, int c0, const
     const EpiOut& o = P.out[j];
     if (o.f64) {
       double v[W];
+      if (sizeof(AccT) == 8) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) v[w] = o.acc_d * (double)acc[w] + (r == c0 + w ? o.id_d : 0.0);
+        for (int w = 0; w < W; ++w) v[w] = o.acc_d * (double)acc[w] + (r == c0 + w ? o.id_d : 0.0);
 #pragma unroll
-      for (int i = 0; i < kMaxIn; ++i) {
-        if (i < P.nin && o.in_d[i] != 0.0) {
-          const bool f = P.in[i].dt == DT_F64;
+        for (int i = 0; i < kMaxIn; ++i) {
+          if (i < P.nin && o.in_d[i] != 0.0) {
+            const bool f = P.in[i].dt == DT_F64;
 #pragma unroll
-          for (int w = 0; w < W; ++w) v[w] += o.in_d[i] * (f ? din[i][w] : (double)fin[i][w]);
+            for (int w = 0; w < W; ++w) v[w] += o.in_d[i] * (f ? din[i][w] : (double)fin[i][w]);
+          }
+        }
+      } else {
+        // FP32 terms in FP32, then one DFMA per FP64 input (see epi_element)
+        float vf[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) vf[w] = o.acc_f * (float)acc[w];
+#pragma unroll
+        for (int i = 0; i < kMaxIn; ++i) {
+          if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) vf[w] = fmaf(o.in_f[i], fin[i][w], vf[w]);
+          }
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = (double)vf[w] + (r == c0 + w ? o.id_d : 0.0);
+#pragma unroll
+        for (int i = 0; i < kMaxIn; ++i) {
+          if (i < P.nin && o.in_d[i] != 0.0 && P.in[i].dt == DT_F64) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) v[w] = fma(o.in_d[i], din[i][w], v[w]);
+          }
         }
       }
 #pragma unroll

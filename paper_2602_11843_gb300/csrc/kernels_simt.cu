@@ -125,11 +125,39 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
   epi_flag(P, bad);
 }
 
+// Element-wise pass (acc = 0) over one 32 x 32 tile per 256-thread CTA.
+// Row-major stores are coalesced along the warp; transposed hi/lo stores go
+// through a shared-memory tile so that they are coalesced too.
 __global__ void __launch_bounds__(256) ewise_kernel(const __grid_constant__ EpiParams P) {
-  const int c = blockIdx.x * 32 + threadIdx.x;
-  const int r = blockIdx.y * 8 + threadIdx.y;
+  __shared__ float tile[kMaxOut][32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   bool bad = false;
-  if (r < P.npad && c < P.npad) bad = epi_element<float>(P, r, c, 0.f);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float tv[kMaxOut];
+    bad |= epi_element_impl<float, true>(P, r0 + ty + 8 * q, c0 + tx, 0.f, tv);
+#pragma unroll
+    for (int j = 0; j < kMaxOut; ++j) tile[j][ty + 8 * q][tx] = tv[j];
+  }
+  __syncthreads();
+  for (int j = 0; j < P.nout; ++j) {
+    const EpiOut& o = P.out[j];
+    for (int s = 0; s < o.nsplit; ++s) {
+      const EpiSplit& sp = o.split[s];
+      if (!sp.transposed) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // lane tx writes element (r0 + tx, c0 + ty + 8q) at row c, column r of the stored transpose
+        const float v = tile[j][tx][ty + 8 * q];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        const int64_t off = (int64_t)(c0 + ty + 8 * q) * sp.ld + (r0 + tx);
+        reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = hi;
+        reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = lo;
+      }
+    }
+  }
   epi_flag(P, bad);
 }
 
@@ -154,8 +182,8 @@ cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int
 }
 
 cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s) {
-  if (P.npad <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((P.npad + 31) / 32), (unsigned)((P.npad + 7) / 8));
+  if (P.npad <= 0 || P.npad % 32 != 0) return P.npad <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  dim3 grid((unsigned)(P.npad / 32), (unsigned)(P.npad / 32));
   ewise_kernel<<<grid, dim3(32, 8), 0, s>>>(P);
   return cudaGetLastError();
 }
