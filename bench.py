@@ -38,6 +38,12 @@ WORKLOADS = {
     "plain-r9-fp32-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
     "plain-r15-fp32-n4096-k225": dict(cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
     "plain-r9-fp64-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
+    # cfg 4: 4096 damped-Jacobi matrices, n uniform in {16, 32, ..., 256}; a step is one
+    # grouped evaluation of the whole batch
+    "batched-r9-bf16-4096-k81": dict(cfg=4, count=4096, k=81, radix=9, dtype="split_bf16", batched=True),
+    "batched-r15-bf16-4096-k225": dict(cfg=4, count=4096, k=225, radix=15, dtype="split_bf16", batched=True),
+    "batched-r9-fp32-4096-k81": dict(cfg=4, count=4096, k=81, radix=9, dtype="fp32", batched=True),
+    "batched-r15-fp32-4096-k225": dict(cfg=4, count=4096, k=225, radix=15, dtype="fp32", batched=True),
 }
 DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 
@@ -172,6 +178,33 @@ def run_reference(args, wl):
     from oracle import circuits as C
     from oracle import evaluate as EV
 
+    if wl.get("batched"):
+        from workloads import generators as G
+
+        mats = G.jacobi_batch(wl["count"], 1000 * wl["cfg"])
+        times = []
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            done = 0
+            for m in mats[it * 8 % len(mats):]:
+                EV.evaluate(m["A"], wl["k"], wl["radix"])
+                done += 1
+                if done >= 8:
+                    break
+            if it >= args.warmup:
+                times.append((time.perf_counter() - t0) / done)
+        value = 1.0 / statistics.median(times)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(mats) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "count": len(mats), "k": wl["k"], "radix": wl["radix"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "each step: 8 matrices of the batch, scaled to S_k/s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     inp = make_input(wl, 0)
     A = np.asarray(inp["A"], dtype=np.float64)
     ks = EV.kernels()
@@ -205,7 +238,168 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, wl):
+    """cfg 4: one grouped evaluation of the whole batch per step; compared with the
+    same batch evaluated one matrix (one plan, its own launches) at a time."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2602_11843_gb300 as nm
+    from workloads import generators as G
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    mats = G.jacobi_batch(wl["count"], 1000 * wl["cfg"] + rank)
+    ns = [m["n"] for m in mats]
+    bp = nm.BatchedPlan(len(mats), 256, wl["k"], wl["radix"], wl["dtype"], nm.FLAG_TIMING)
+    dt = torch.float32 if wl["dtype"] == "fp32" else torch.float64
+    # the batch lives in one contiguous buffer (A_i are views), so an end-to-end
+    # step moves it with one copy each way
+    offs = np.cumsum([0] + [n * n for n in ns])
+    A_all = torch.empty(int(offs[-1]), dtype=dt, device=dev)
+    S_all = torch.empty_like(A_all)
+    host = np.concatenate([m["A"].reshape(-1) for m in mats])
+    A_all.copy_(torch.from_numpy(host).to(dt))
+    As = [A_all[offs[i]:offs[i + 1]].view(n, n) for i, n in enumerate(ns)]
+    outs = [S_all[offs[i]:offs[i + 1]].view(n, n) for i, n in enumerate(ns)]
+    bp.bind(As, outs)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        bp.launch()
+    torch.cuda.synchronize()
+    nm.neumann_plan_timing(bp.handle, 1 << 16)
+    assert bp.status() == 0
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            bp.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    prod_ms = nm.neumann_plan_timing(bp.handle, 1 << 16)
+    status = bp.status()
+    value = len(mats) * args.steps * world / (ms_max / 1e3)
+    info = nm.neumann_plan_info(bp.handle)
+    # the same batch, one plan per matrix order and one evaluation (own launches) per matrix
+    plans = {}
+    for n in sorted(set(ns)):
+        plans[n] = nm.Plan(n, wl["k"], wl["radix"], wl["dtype"])
+    for a, o in zip(As, outs):
+        plans[a.shape[0]](a, out=o)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for a, o in zip(As, outs):
+        plans[a.shape[0]](a, out=o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_matrix_ms = e0.elapsed_time(e1)
+    # end to end: host inputs in, host results out, every step
+    A_host = A_all.cpu().pin_memory()
+    S_host = torch.empty_like(A_host).pin_memory()
+    h2d = A_host.numel() * A_host.element_size()
+
+    def e2e_step():
+        A_all.copy_(A_host, non_blocking=True)
+        bp.launch()
+        S_host.copy_(S_all, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = len(mats) * args.steps * world / (e0.elapsed_time(e1) / 1e3)
+    nm.neumann_plan_timing(bp.handle, 1 << 16)
+    peaks, peak_src = _peaks()
+    tc = wl["dtype"].startswith("split")
+    per = info["products_executed"]
+    flops_one = sum(2.0 * n ** 3 for n in ns)  # one product over the batch, 2 n^3 per matrix
+    mean_prod = statistics.mean(prod_ms) if prod_ms else float("nan")
+    if tc:
+        roof = {"bound": "tensor", "achieved": 3 * flops_one / (mean_prod / 1e3) / 1e12,
+                "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
+                "kernel": "tc_split_gemm_kernel (grouped)", "peak_source": f"bf16_tflops_sustained ({peak_src})",
+                "work_per_launch": "3 x sum 2 n_i^3 BF16 tensor flops"}
+    else:
+        sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        roof = {"bound": "alu", "achieved": flops_one / (mean_prod / 1e3) / 1e12,
+                "peak": 152 * 128 * 2 * sm_hz / 1e12, "unit": "TFLOP/s", "traffic": None,
+                "kernel": "simt_gemm_kernel (grouped)",
+                "peak_source": "derived: 152 SM x 128 lanes x 2 flop x max SM clock",
+                "work_per_launch": "sum 2 n_i^3 FP32 flops"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["effective_tflops"] = flops_one / (mean_prod / 1e3) / 1e12
+    roof["launches_timed"] = len(prod_ms)
+    if prod_ms and per and len(prod_ms) % per == 0:
+        reps = len(prod_ms) // per
+        roof["per_product_ms"] = [round(sum(prod_ms[i::per]) / reps, 4) for i in range(per)]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if tc else "f32",
+        "precision": "hi+lo BF16 operands, 3 products, FP32 accumulate, FP64 Y and R" if tc else
+                     "FP32 products, FP64 Y and R",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "count": len(mats), "n": "uniform in {16,...,256}", "k": wl["k"],
+                   "radix": wl["radix"], "scheme": wl["dtype"], "products_per_matrix": per,
+                   "launches_per_step": info["launches"] * ((len(mats) + 2047) // 2048),
+                   "l2": "inputs larger than L2 (the batch's A alone is 0.39 GB in FP32)",
+                   "parallelism": f"replicas x{world}"},
+        "vs_per_matrix": {"ms_per_batch": per_matrix_ms, "speedup": per_matrix_ms / (ms_max / args.steps)},
+        "status": status, "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+        "gpu_launches": args.steps * info["launches"] * ((len(mats) + 2047) // 2048),
+        "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batched(wl, mats)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    del np
+
+
+def cpu_baseline_batched(wl, mats, budget_s=10.0):
+    """The oracle on the host cores: the same scheme on matrices of the batch, one
+    after another, for about `budget_s` seconds, scaled to S_k/s."""
+    from oracle import evaluate as EV
+
+    t0 = time.perf_counter()
+    done = 0
+    for m in mats:
+        EV.evaluate(m["A"], wl["k"], wl["radix"])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {done} of {len(mats)} matrices (same order of draw), FP64 NumPy; {dt:.1f} s"}
+
+
 def run_ours(args, wl):
+    if wl.get("batched"):
+        return run_batched(args, wl)
     import numpy as np
     import torch
     import torch.distributed as dist

@@ -94,6 +94,29 @@ class BatchedPlan:
                              [o.data_ptr() for o in outs], s.cuda_stream)
         return outs
 
+    def bind(self, As, outs):
+        """Fix the inputs and outputs of later `launch` calls (argument arrays built once)."""
+        import ctypes
+
+        dt = _torch_dtype(self.dtype, self.flags)
+        for a, o in zip(As, outs):
+            if a.dtype != dt or o.dtype != dt or not a.is_contiguous() or not o.is_contiguous():
+                raise ValueError(f"inputs and outputs must be contiguous {dt}")
+        cnt = len(As)
+        self._bound = (cnt, (ctypes.c_int64 * cnt)(*[a.shape[0] for a in As]),
+                       (ctypes.c_void_p * cnt)(*[a.data_ptr() for a in As]),
+                       (ctypes.c_void_p * cnt)(*[o.data_ptr() for o in outs]), As, outs)
+
+    def launch(self, stream=None):
+        """Evaluate the bound batch on `stream` (default: the current stream)."""
+        import torch
+
+        from ._capi import _check, _lib
+
+        cnt, na, aa, sa, As, _ = self._bound
+        s = torch.cuda.current_stream(As[0].device) if stream is None else stream
+        _check(_lib.neumann_eval_batched(self.handle, cnt, na, aa, sa, s.cuda_stream), "neumann_eval_batched")
+
     def status(self) -> int:
         return neumann_last_status(self.handle)
 

@@ -5,6 +5,9 @@
 // writing each result in every representation its consumers read: FP32 / FP64
 // row-major, and hi/lo BF16 pairs row-major (left operands) or transposed
 // (right operands of the tensor-core product).
+//
+// An EpiCtx fixes the matrix a tile belongs to: its order n and the offset of
+// its slab in the workspace buffers (0 for a single evaluation).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -13,30 +16,72 @@
 
 namespace neumann {
 
-__device__ __forceinline__ void split_store(const EpiSplit& s, int r, int c, float v) {
+struct EpiCtx {
+  int n;        // order of this matrix
+  int mat;      // index in the batch (0 for a single evaluation)
+  int64_t off;  // element offset of its slab in every workspace buffer
+};
+
+__device__ __forceinline__ EpiCtx epi_ctx(const EpiParams& P, int mat) {
+  EpiCtx x;
+  x.mat = mat;
+  if (P.mat_n) {
+    x.n = P.mat_n[mat];
+    x.off = (int64_t)mat * P.mat_stride;
+  } else {
+    x.n = P.n;
+    x.off = 0;
+  }
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ const T* in_base(const EpiIn& in, const EpiCtx& x, int64_t* ld) {
+  if (in.mode == EPI_WS) {
+    *ld = in.ld;
+    return reinterpret_cast<const T*>(in.p) + x.off;
+  }
+  if (in.mode == EPI_TABLE) {
+    *ld = x.n;
+    return reinterpret_cast<const T*>(reinterpret_cast<const void* const*>(in.p)[x.mat]);
+  }
+  *ld = in.ld;
+  return reinterpret_cast<const T*>(in.p);
+}
+
+template <typename T>
+__device__ __forceinline__ T* dst_base(const EpiDst& ds, const EpiCtx& x, int64_t* ld) {
+  if (ds.mode == EPI_WS) {
+    *ld = ds.ld;
+    return reinterpret_cast<T*>(ds.p) + x.off;
+  }
+  if (ds.mode == EPI_TABLE) {
+    *ld = x.n;
+    return reinterpret_cast<T*>(reinterpret_cast<void* const*>(ds.p)[x.mat]);
+  }
+  *ld = ds.ld;
+  return reinterpret_cast<T*>(ds.p);
+}
+
+__device__ __forceinline__ void split_store(const EpiSplit& s, const EpiCtx& x, int r, int c, float v) {
   __nv_bfloat16 hi = __float2bfloat16_rn(v);
   __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-  int64_t off = s.transposed ? (int64_t)c * s.ld + r : (int64_t)r * s.ld + c;
+  int64_t off = x.off + (s.transposed ? (int64_t)c * s.ld + r : (int64_t)r * s.ld + c);
   reinterpret_cast<__nv_bfloat16*>(s.hi)[off] = hi;
   reinterpret_cast<__nv_bfloat16*>(s.lo)[off] = lo;
 }
 
-__device__ __forceinline__ void split_store_d(const EpiSplit& s, int r, int c, double v) {
-  // The pair is formed from RN_fp32(v): FP32 keeps 24 bits, the hi+lo pair 16.
-  split_store(s, r, c, (float)v);
-}
-
-// Write 0 to every workspace destination of element (r, c), n <= r or c < npad
-// (transposed splits excepted when kSkipT).
+// Write 0 to every workspace destination of element (r, c) outside the n x n
+// block (transposed splits excepted when kSkipT).
 template <bool kSkipT = false>
-__device__ __forceinline__ void epi_padding(const EpiParams& P, int r, int c) {
+__device__ __forceinline__ void epi_padding(const EpiParams& P, const EpiCtx& x, int r, int c) {
 #pragma unroll 1
   for (int j = 0; j < P.nout; ++j) {
     const EpiOut& o = P.out[j];
     for (int d = 0; d < o.ndst; ++d) {
       const EpiDst& ds = o.dst[d];
-      if (!ds.pad) continue;
-      int64_t off = (int64_t)r * ds.ld + c;
+      if (ds.mode != EPI_WS) continue;
+      const int64_t off = x.off + (int64_t)r * ds.ld + c;
       if (ds.dt == DT_F64)
         reinterpret_cast<double*>(ds.p)[off] = 0.0;
       else
@@ -45,27 +90,28 @@ __device__ __forceinline__ void epi_padding(const EpiParams& P, int r, int c) {
     for (int s = 0; s < o.nsplit; ++s) {
       const EpiSplit& sp = o.split[s];
       if (kSkipT && sp.transposed) continue;
-      int64_t off = sp.transposed ? (int64_t)c * sp.ld + r : (int64_t)r * sp.ld + c;
+      const int64_t off = x.off + (sp.transposed ? (int64_t)c * sp.ld + r : (int64_t)r * sp.ld + c);
       reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = __float2bfloat16_rn(0.f);
       reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = __float2bfloat16_rn(0.f);
     }
   }
 }
 
-// Apply every output of the epilogue to element (r, c) with accumulator value
-// acc; r, c < npad. Inside the n x n block the outputs are formed; in the
+// Apply every output of the epilogue to element (r, c) of matrix x with
+// accumulator value acc. Inside the n x n block the outputs are formed; in the
 // padding only workspace buffers are written (with 0). Returns true on a
 // non-finite result.
 // kDeferT: outputs' transposed split stores are not written; the value they
 // would split (RN_fp32 of the output) is left in tv[j] for the caller to write
 // through a shared-memory transpose (0 in the padding).
 template <typename AccT, bool kDeferT>
-__device__ __forceinline__ bool epi_element_impl(const EpiParams& P, int r, int c, AccT acc, float* tv) {
+__device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCtx& x, int r, int c, AccT acc,
+                                                 float* tv) {
   bool bad = false;
-  if (r >= P.n || c >= P.n) {
+  if (r >= x.n || c >= x.n) {
     if (kDeferT)
       for (int j = 0; j < kMaxOut; ++j) tv[j] = 0.f;
-    epi_padding<kDeferT>(P, r, c);
+    epi_padding<kDeferT>(P, x, r, c);
     return false;
   }
   float fin[kMaxIn];
@@ -76,20 +122,20 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, int r, int 
     din[i] = 0.0;
     if (i < P.nin) {
       const EpiIn& in = P.in[i];
-      int64_t off = (int64_t)r * in.ld + c;
-      if (in.dt == DT_F64) {
-        din[i] = reinterpret_cast<const double*>(in.p)[off];
-      } else {
-        fin[i] = reinterpret_cast<const float*>(in.p)[off];
-      }
+      int64_t ld;
+      if (in.dt == DT_F64)
+        din[i] = in_base<double>(in, x, &ld)[(int64_t)r * ld + c];
+      else
+        fin[i] = in_base<float>(in, x, &ld)[(int64_t)r * ld + c];
     }
   }
   const bool diag = (r == c);
 #pragma unroll 1
   for (int j = 0; j < P.nout; ++j) {
     const EpiOut& o = P.out[j];
+    double v;
+    float vf;
     if (o.f64) {
-      double v;
       if (sizeof(AccT) == 8) {
         v = o.acc_d * (double)acc + (diag ? o.id_d : 0.0);
 #pragma unroll
@@ -100,52 +146,41 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, int r, int 
       } else {
         // FP32 terms summed in FP32 (they carry FP32 rounding already); the FP64
         // inputs (a partial sum Y or residual R) are added in FP64, one DFMA each.
-        float vf = o.acc_f * (float)acc;
+        float t = o.acc_f * (float)acc;
 #pragma unroll
         for (int i = 0; i < kMaxIn; ++i)
-          if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) vf = fmaf(o.in_f[i], fin[i], vf);
-        v = (double)vf + (diag ? o.id_d : 0.0);
+          if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) t = fmaf(o.in_f[i], fin[i], t);
+        v = (double)t + (diag ? o.id_d : 0.0);
 #pragma unroll
         for (int i = 0; i < kMaxIn; ++i)
           if (i < P.nin && o.in_d[i] != 0.0 && P.in[i].dt == DT_F64) v = fma(o.in_d[i], din[i], v);
       }
+      vf = (float)v;
       if (!isfinite(v)) bad = true;
-      for (int d = 0; d < o.ndst; ++d) {
-        const EpiDst& ds = o.dst[d];
-        int64_t off = (int64_t)r * ds.ld + c;
-        if (ds.dt == DT_F64)
-          reinterpret_cast<double*>(ds.p)[off] = v;
-        else
-          reinterpret_cast<float*>(ds.p)[off] = (float)v;
-      }
-      for (int s = 0; s < o.nsplit; ++s) {
-        if (kDeferT && o.split[s].transposed)
-          tv[j] = (float)v;
-        else
-          split_store_d(o.split[s], r, c, v);
-      }
     } else {
-      float v = o.acc_f * (float)acc + (diag ? o.id_f : 0.f);
+      vf = o.acc_f * (float)acc + (diag ? o.id_f : 0.f);
 #pragma unroll
       for (int i = 0; i < kMaxIn; ++i) {
         if (i < P.nin && o.in_f[i] != 0.f)
-          v = fmaf(o.in_f[i], P.in[i].dt == DT_F64 ? (float)din[i] : fin[i], v);
+          vf = fmaf(o.in_f[i], P.in[i].dt == DT_F64 ? (float)din[i] : fin[i], vf);
       }
-      if (!isfinite(v)) bad = true;
-      for (int d = 0; d < o.ndst; ++d) {
-        const EpiDst& ds = o.dst[d];
-        int64_t off = (int64_t)r * ds.ld + c;
-        if (ds.dt == DT_F64)
-          reinterpret_cast<double*>(ds.p)[off] = (double)v;
-        else
-          reinterpret_cast<float*>(ds.p)[off] = v;
-      }
-      for (int s = 0; s < o.nsplit; ++s) {
-        if (kDeferT && o.split[s].transposed)
-          tv[j] = v;
-        else
-          split_store(o.split[s], r, c, v);
-      }
+      v = 0.0;  // unused: no FP64 destination is written from an FP32 output
+      if (!isfinite(vf)) bad = true;
+    }
+    for (int d = 0; d < o.ndst; ++d) {
+      const EpiDst& ds = o.dst[d];
+      int64_t ld;
+      if (ds.dt == DT_F64)
+        dst_base<double>(ds, x, &ld)[(int64_t)r * ld + c] = o.f64 ? v : (double)vf;
+      else
+        dst_base<float>(ds, x, &ld)[(int64_t)r * ld + c] = vf;
+    }
+    // hi/lo pairs are formed from RN_fp32 of the output: FP32 keeps 24 bits, the pair 16
+    for (int s = 0; s < o.nsplit; ++s) {
+      if (kDeferT && o.split[s].transposed)
+        tv[j] = vf;
+      else
+        split_store(o.split[s], x, r, c, vf);
     }
   }
   return bad;
@@ -154,18 +189,17 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, int r, int 
 // One copy serves every call site of the GEMM kernels; P is a __grid_constant__
 // kernel parameter, so passing it by reference copies nothing.
 template <typename AccT>
-__device__ __noinline__ bool epi_element(const EpiParams& P, int r, int c, AccT acc) {
-  return epi_element_impl<AccT, false>(P, r, c, acc, nullptr);
+__device__ __noinline__ bool epi_element(const EpiParams& P, EpiCtx x, int r, int c, AccT acc) {
+  return epi_element_impl<AccT, false>(P, x, r, c, acc, nullptr);
 }
 
 // ---------------------------------------------------------------------------
 // Vector form: W consecutive columns c0 .. c0+W-1 of row r, c0 % W == 0.
 // Every input is loaded (as W-wide vectors) before any output is formed, so a
-// thread keeps all of its loads in flight at once. Requires that every input
-// and every pad destination is a workspace buffer (16-byte aligned, leading
-// dimension a multiple of 8); the user's output (pad == 0) is written with
-// scalar stores. Rows or columns outside the n x n block fall back to
-// epi_element.
+// thread keeps all of its loads in flight at once. Used by the products,
+// whose inputs are all workspace buffers (16-byte aligned, leading dimension a
+// multiple of 8); caller-owned outputs are written with scalar stores. Rows or
+// columns outside the n x n block fall back to epi_element.
 
 template <int W>
 __device__ __forceinline__ void ld_vec(const float* p, float (&v)[W]) {
@@ -185,25 +219,29 @@ __device__ __forceinline__ void ld_vec(const double* p, double (&v)[W]) {
   }
 }
 
-template <int W, typename V>
-__device__ __forceinline__ void st_row(const EpiOut& o, int r, int c0, const V (&v)[W]) {
+// kWsOnly: write workspace destinations only (padding zeros never go to the caller).
+template <int W, typename V, bool kWsOnly = false>
+__device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, int c0, const V (&v)[W]) {
   for (int d = 0; d < o.ndst; ++d) {
     const EpiDst& ds = o.dst[d];
-    const int64_t off = (int64_t)r * ds.ld + c0;
-    if (!ds.pad) {  // caller's matrix: any leading dimension
+    int64_t ld;
+    if (kWsOnly && ds.mode != EPI_WS) continue;
+    if (ds.mode != EPI_WS) {  // caller's matrix: any leading dimension
       if (ds.dt == DT_F64) {
+        double* q = dst_base<double>(ds, x, &ld) + (int64_t)r * ld + c0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) reinterpret_cast<double*>(ds.p)[off + w] = (double)v[w];
+        for (int w = 0; w < W; ++w) q[w] = (double)v[w];
       } else {
+        float* q = dst_base<float>(ds, x, &ld) + (int64_t)r * ld + c0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) reinterpret_cast<float*>(ds.p)[off + w] = (float)v[w];
+        for (int w = 0; w < W; ++w) q[w] = (float)v[w];
       }
     } else if (ds.dt == DT_F64) {
-      double* q = reinterpret_cast<double*>(ds.p) + off;
+      double* q = dst_base<double>(ds, x, &ld) + (int64_t)r * ld + c0;
 #pragma unroll
       for (int w = 0; w < W; w += 2) *reinterpret_cast<double2*>(q + w) = make_double2((double)v[w], (double)v[w + 1]);
     } else {
-      float* q = reinterpret_cast<float*>(ds.p) + off;
+      float* q = dst_base<float>(ds, x, &ld) + (int64_t)r * ld + c0;
 #pragma unroll
       for (int w = 0; w < W; w += 4)
         *reinterpret_cast<float4*>(q + w) = make_float4((float)v[w], (float)v[w + 1], (float)v[w + 2], (float)v[w + 3]);
@@ -221,12 +259,12 @@ __device__ __forceinline__ void st_row(const EpiOut& o, int r, int c0, const V (
     if (sp.transposed) {
 #pragma unroll
       for (int w = 0; w < W; ++w) {
-        const int64_t off = (int64_t)(c0 + w) * sp.ld + r;
+        const int64_t off = x.off + (int64_t)(c0 + w) * sp.ld + r;
         reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = hi[w];
         reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = lo[w];
       }
     } else {
-      const int64_t off = (int64_t)r * sp.ld + c0;
+      const int64_t off = x.off + (int64_t)r * sp.ld + c0;
       static_assert(W == 4 || W == 8, "vector width");
       uint32_t ph[W / 2], pl[W / 2];
 #pragma unroll
@@ -247,12 +285,28 @@ __device__ __forceinline__ void st_row(const EpiOut& o, int r, int c0, const V (
   }
 }
 
+// Zeros for W consecutive padding elements of row r (r >= n) in every workspace
+// destination.
+template <int W>
+__device__ __forceinline__ void epi_row_zero(const EpiParams& P, const EpiCtx& x, int r, int c0) {
+  float z[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) z[w] = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < P.nout; ++j) st_row<W, float, true>(P.out[j], x, r, c0, z);
+}
+
 template <int W, typename AccT>
-__device__ __forceinline__ bool epi_row(const EpiParams& P, int r, int c0, const AccT (&acc)[W]) {
-  if (r >= P.n || c0 + W > P.n) {
+__device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int r, int c0,
+                                        const AccT (&acc)[W]) {
+  if (r >= x.n) {
+    epi_row_zero<W>(P, x, r, c0);
+    return false;
+  }
+  if (c0 + W > x.n) {
     bool bad = false;
 #pragma unroll
-    for (int w = 0; w < W; ++w) bad |= epi_element<AccT>(P, r, c0 + w, acc[w]);
+    for (int w = 0; w < W; ++w) bad |= epi_element<AccT>(P, x, r, c0 + w, acc[w]);
     return bad;
   }
   float fin[kMaxIn][W];
@@ -261,7 +315,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, int r, int c0, const
   for (int i = 0; i < kMaxIn; ++i) {
     if (i < P.nin) {
       const EpiIn& in = P.in[i];
-      const int64_t off = (int64_t)r * in.ld + c0;
+      const int64_t off = x.off + (int64_t)r * in.ld + c0;
       if (in.dt == DT_F64)
         ld_vec<W>(reinterpret_cast<const double*>(in.p) + off, din[i]);
       else
@@ -286,7 +340,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, int r, int c0, const
           }
         }
       } else {
-        // FP32 terms in FP32, then one DFMA per FP64 input (see epi_element)
+        // FP32 terms in FP32, then one DFMA per FP64 input (see epi_element_impl)
         float vf[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) vf[w] = o.acc_f * (float)acc[w];
@@ -309,7 +363,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, int r, int c0, const
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      st_row<W, double>(o, r, c0, v);
+      st_row<W, double>(o, x, r, c0, v);
     } else {
       float v[W];
 #pragma unroll
@@ -324,7 +378,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, int r, int c0, const
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      st_row<W, float>(o, r, c0, v);
+      st_row<W, float>(o, x, r, c0, v);
     }
   }
   return bad;

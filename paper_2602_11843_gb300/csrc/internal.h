@@ -15,11 +15,22 @@ constexpr int kMaxOut = 4;
 constexpr int kMaxDst = 2;
 constexpr int kMaxSplit = 2;
 
+// How an epilogue input or plain destination is addressed. The zero value is
+// the caller's-matrix mode, which never writes outside the n x n block.
+enum : int {
+  EPI_PTR = 0,    // caller's matrix: p, leading dimension ld (single evaluation)
+  EPI_WS = 1,     // workspace buffer: p + slab offset of the matrix, leading dimension ld;
+                  // its padding (row or column >= n) is written as 0
+  EPI_TABLE = 2,  // caller's matrices: p is a device array of per-matrix pointers,
+                  // leading dimension n of that matrix (batched evaluation)
+};
+
 // An epilogue input: an n x n matrix read at the output element's (r, c).
 struct EpiIn {
   const void* p;
   int64_t ld;
   int dt;
+  int mode;
 };
 
 // A plain store of an output (row-major).
@@ -27,7 +38,7 @@ struct EpiDst {
   void* p;
   int64_t ld;
   int dt;
-  int pad;  // workspace buffer: elements in [n, npad) are written as 0
+  int mode;
 };
 
 // A split store: hi = RN_bf16(v), lo = RN_bf16(v - hi), row-major or transposed.
@@ -60,6 +71,11 @@ struct EpiParams {
   int nout;
   EpiOut out[kMaxOut];
   unsigned* status;  // device word, NEUMANN_STATUS_* bits are OR-ed in
+  // Batched (grouped) launches: matrix m has order mat_n[m] and occupies
+  // elements [m * mat_stride, (m + 1) * mat_stride) of every workspace buffer.
+  // nullptr for a single evaluation (order n, offset 0).
+  const int* mat_n;
+  int64_t mat_stride;
 };
 
 // Split-operand tensor maps of one tensor-core product C = A B:
@@ -70,17 +86,27 @@ struct TcMaps {
 };
 
 // ---- launchers (kernels_simt.cu) ----
-cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad,
-                                 const EpiParams& P, cudaStream_t s);
-cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad,
-                                 const EpiParams& P, cudaStream_t s);
-// Element-wise epilogue with acc = 0 over the n x n elements.
-cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s);
+// tiles == nullptr: one padded npad x npad product. Otherwise a grouped launch
+// over a batch: ntiles entries {matrix, tile row, tile column, K steps of 8}.
+cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad, const int4* tiles,
+                                 int ntiles, const EpiParams& P, cudaStream_t s);
+cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad, const int4* tiles,
+                                 int ntiles, const EpiParams& P, cudaStream_t s);
+// Element-wise epilogue with acc = 0: over the npad x npad elements, or (grouped)
+// over ntiles 32 x 32 tiles {matrix, tile row, tile column}.
+cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles = nullptr, int ntiles = 0);
 
 // ---- launchers (kernels_tc.cu) ----
-// Encode the four tensor maps over padded_n x padded_n BF16 arrays with leading dimension ld.
-bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld);
-cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s);
+// Encode the four tensor maps over padded_n x padded_n BF16 arrays with leading
+// dimension ld; with count > 0, over count stacked padded_n x padded_n slabs
+// (3-D maps, one slab per matrix of a batch).
+bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
+                  int count = 0);
+// tiles == nullptr: one npad x npad product. Otherwise a grouped launch over a
+// batch (3-D maps): ntiles entries {matrix, tile row, K steps of 32, 0}; each
+// tile covers 128 rows and all 256 columns of its matrix's slab.
+cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,
+                           const int4* tiles = nullptr, int ntiles = 0);
 
 // ---- radix-15 coefficients (radix15.cpp) ----
 // set 0: refined, 1: printed. Returns false if the refinement did not converge.

@@ -25,15 +25,30 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
   v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
 }
 
+// tiles == nullptr: one matrix, CTA (blockIdx.y, blockIdx.x) computes tile
+// (tm, tn) over `ktiles` K steps. Otherwise (grouped launch over a batch) CTA b
+// computes tiles[b] = {matrix, tm, tn, K steps}; every operand and workspace
+// buffer then holds matrix m at element offset m * P.mat_stride.
 template <typename T>
 __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B,
-                                                        int64_t ld, int ktiles,
+                                                        int64_t ld, int ktiles, const int4* __restrict__ tiles,
                                                         const __grid_constant__ EpiParams P) {
   __shared__ __align__(16) T As[2][BK][BM + 4];
   __shared__ __align__(16) T Bs[2][BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  int mat = 0, tm = blockIdx.y, tn = blockIdx.x;
+  if (tiles) {
+    const int4 t = tiles[blockIdx.x];
+    mat = t.x;
+    tm = t.y;
+    tn = t.z;
+    ktiles = t.w;
+    A += (int64_t)mat * P.mat_stride;
+    B += (int64_t)mat * P.mat_stride;
+  }
+  const EpiCtx x = epi_ctx(P, mat);
+  const int m0 = tm * BM, n0 = tn * BN;
   const int a_row = tid >> 1, a_col = (tid & 1) * 4;   // A tile: 128 rows x 8
   const int b_row = tid >> 5, b_col = (tid & 31) * 4;  // B tile: 8 rows x 128
   const T* Ap = A + (int64_t)(m0 + a_row) * ld + a_col;
@@ -112,14 +127,19 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
     __syncthreads();
   }
 
+  // A grouped launch writes each matrix below its order rounded up to 32: that
+  // covers the K padding later products read; the rest feeds only discarded outputs.
+  const int lim = tiles ? (x.n + 31) / 32 * 32 : (1 << 30);
   bool bad = false;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      const int c0 = n0 + h * 64 + tx * 4;
+      if (r >= lim || c0 >= lim) continue;
       const T(&a4)[4] = *reinterpret_cast<const T(*)[4]>(&acc[i][4 * h]);
-      bad |= epi_row<4, T>(P, r, n0 + h * 64 + tx * 4, a4);
+      bad |= epi_row<4, T>(P, x, r, c0, a4);
     }
   }
   epi_flag(P, bad);
@@ -128,15 +148,25 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
 // Element-wise pass (acc = 0) over one 32 x 32 tile per 256-thread CTA.
 // Row-major stores are coalesced along the warp; transposed hi/lo stores go
 // through a shared-memory tile so that they are coalesced too.
-__global__ void __launch_bounds__(256) ewise_kernel(const __grid_constant__ EpiParams P) {
+// tiles != nullptr (grouped launch): CTA b handles tiles[b] = {matrix, tile row, tile column}.
+__global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ tiles,
+                                                     const __grid_constant__ EpiParams P) {
   __shared__ float tile[kMaxOut][32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  int mat = 0, tr = blockIdx.y, tc = blockIdx.x;
+  if (tiles) {
+    const int4 t = tiles[blockIdx.x];
+    mat = t.x;
+    tr = t.y;
+    tc = t.z;
+  }
+  const EpiCtx x = epi_ctx(P, mat);
+  const int r0 = tr * 32, c0 = tc * 32;
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float tv[kMaxOut];
-    bad |= epi_element_impl<float, true>(P, r0 + ty + 8 * q, c0 + tx, 0.f, tv);
+    bad |= epi_element_impl<float, true>(P, x, r0 + ty + 8 * q, c0 + tx, 0.f, tv);
 #pragma unroll
     for (int j = 0; j < kMaxOut; ++j) tile[j][ty + 8 * q][tx] = tv[j];
   }
@@ -152,7 +182,7 @@ __global__ void __launch_bounds__(256) ewise_kernel(const __grid_constant__ EpiP
         const float v = tile[j][tx][ty + 8 * q];
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        const int64_t off = (int64_t)(c0 + ty + 8 * q) * sp.ld + (r0 + tx);
+        const int64_t off = x.off + (int64_t)(c0 + ty + 8 * q) * sp.ld + (r0 + tx);
         reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = hi;
         reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = lo;
       }
@@ -162,29 +192,40 @@ __global__ void __launch_bounds__(256) ewise_kernel(const __grid_constant__ EpiP
 }
 
 template <typename T>
-cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const EpiParams& P, cudaStream_t s) {
+cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const int4* tiles, int ntiles,
+                        const EpiParams& P, cudaStream_t s) {
   if (npad % BM != 0 || npad % BN != 0 || ld < npad) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)(npad / BN), (unsigned)(npad / BM));
-  simt_gemm_kernel<T><<<grid, TPB, 0, s>>>(A, B, ld, (int)(npad / BK), P);
+  if (tiles) {
+    if (ntiles <= 0) return cudaSuccess;
+    simt_gemm_kernel<T><<<ntiles, TPB, 0, s>>>(A, B, ld, 0, tiles, P);
+  } else {
+    dim3 grid((unsigned)(npad / BN), (unsigned)(npad / BM));
+    simt_gemm_kernel<T><<<grid, TPB, 0, s>>>(A, B, ld, (int)(npad / BK), nullptr, P);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad, const EpiParams& P,
-                                 cudaStream_t s) {
-  return launch_simt<double>(A, B, ld, npad, P, s);
+cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad, const int4* tiles,
+                                 int ntiles, const EpiParams& P, cudaStream_t s) {
+  return launch_simt<double>(A, B, ld, npad, tiles, ntiles, P, s);
 }
 
-cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad, const EpiParams& P,
-                                 cudaStream_t s) {
-  return launch_simt<float>(A, B, ld, npad, P, s);
+cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad, const int4* tiles,
+                                 int ntiles, const EpiParams& P, cudaStream_t s) {
+  return launch_simt<float>(A, B, ld, npad, tiles, ntiles, P, s);
 }
 
-cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s) {
+cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles) {
+  if (tiles) {
+    if (ntiles <= 0) return cudaSuccess;
+    ewise_kernel<<<ntiles, dim3(32, 8), 0, s>>>(tiles, P);
+    return cudaGetLastError();
+  }
   if (P.npad <= 0 || P.npad % 32 != 0) return P.npad <= 0 ? cudaSuccess : cudaErrorInvalidValue;
   dim3 grid((unsigned)(P.npad / 32), (unsigned)(P.npad / 32));
-  ewise_kernel<<<grid, dim3(32, 8), 0, s>>>(P);
+  ewise_kernel<<<grid, dim3(32, 8), 0, s>>>(nullptr, P);
   return cudaGetLastError();
 }
 

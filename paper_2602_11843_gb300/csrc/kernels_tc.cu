@@ -37,7 +37,16 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 32;  // bf16 elements per stage row = 64 bytes
 constexpr int STAGES = 4;
-constexpr int THREADS = 192;
+// Epilogue warps: a single large product has long K loops that hide a 4-warp
+// epilogue working on 8-wide rows; a grouped launch over small matrices has
+// short K loops, so its epilogue is the critical path and gets 8 warps (two per
+// TMEM lane quarter, 4-wide rows to stay within the register budget).
+template <bool kGrouped>
+struct EpiShape {
+  static constexpr int kWarps = kGrouped ? 8 : 4;
+  static constexpr int kThreads = 64 + 32 * kWarps;  // TMA warp, MMA warp, epilogue warps
+  static constexpr int kVec = kGrouped ? 4 : 8;
+};
 constexpr uint32_t A_TILE = BM * BK * 2;  // 8 KiB
 constexpr uint32_t B_TILE = BN * BK * 2;  // 16 KiB
 constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
@@ -97,6 +106,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
           dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 
@@ -162,10 +179,49 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+// Work item `tile` of the launch: matrix, 128-row tile, 256-column tile and the
+// number of 32-deep K stages. A single product walks the grouped raster; a
+// grouped launch reads the host-built table (one 128 x 256 tile per entry,
+// K stages covering that matrix's order rounded up to 32).
+template <bool kGrouped>
+__device__ __forceinline__ void tile_of(int tile, const int4* tiles, int ktiles, int tiles_m, int tiles_n, int* mat,
+                                        int* tm, int* tn, int* nk) {
+  if (kGrouped) {
+    const int4 t = tiles[tile];
+    *mat = t.x;
+    *tm = t.y;
+    *tn = 0;
+    *nk = t.z;
+  } else {
+    *mat = 0;
+    raster(tile, tiles_m, tiles_n, tm, tn);
+    *nk = ktiles;
+  }
+}
+
+template <bool kGrouped>
+__device__ __forceinline__ void load_stage(uint32_t st, const CUtensorMap* ahi, const CUtensorMap* alo,
+                                           const CUtensorMap* bhi, const CUtensorMap* blo, uint32_t bar, int kb,
+                                           int tm, int tn, int mat) {
+  if (kGrouped) {
+    tma_load_3d(st, ahi, bar, kb * BK, tm * BM, mat);
+    tma_load_3d(st + A_TILE, alo, bar, kb * BK, tm * BM, mat);
+    tma_load_3d(st + 2 * A_TILE, bhi, bar, kb * BK, tn * BN, mat);
+    tma_load_3d(st + 2 * A_TILE + B_TILE, blo, bar, kb * BK, tn * BN, mat);
+  } else {
+    tma_load_2d(st, ahi, bar, kb * BK, tm * BM);
+    tma_load_2d(st + A_TILE, alo, bar, kb * BK, tm * BM);
+    tma_load_2d(st + 2 * A_TILE, bhi, bar, kb * BK, tn * BN);
+    tma_load_2d(st + 2 * A_TILE + B_TILE, blo, bar, kb * BK, tn * BN);
+  }
+}
+
+template <bool kGrouped>
+__global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
-                         int ktiles, int tiles_m, int tiles_n, const __grid_constant__ EpiParams P) {
+                         int ktiles, int tiles_m, int tiles_n, const int4* __restrict__ tiles, int ntiles_grouped,
+                         const __grid_constant__ EpiParams P) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain
@@ -174,7 +230,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = tiles_m * tiles_n;
+  const int ntiles = kGrouped ? ntiles_grouped : tiles_m * tiles_n;
   const uint32_t smem_base = smem_u32(smem);
   const uint32_t bar_base = smem_u32(bars);
   auto full_bar = [&](uint32_t s) { return bar_base + 8u * s; };
@@ -190,7 +246,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);  // lane 0 of each epilogue warp
+      mbar_init(tempty_bar(b), EpiShape<kGrouped>::kWarps);  // lane 0 of each epilogue warp
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -217,9 +273,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t kg = 0;  // stage loads issued so far
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        int tm, tn;
-        raster(tile, tiles_m, tiles_n, &tm, &tn);
-        for (int kb = 0; kb < ktiles; ++kb) {
+        int mat, tm, tn, nk;
+        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
+        for (int kb = 0; kb < nk; ++kb) {
           const uint32_t s = kg % STAGES;
           const uint32_t ph = (kg / STAGES) & 1u;
           if (kg >= STAGES && (!mbar_wait(empty_bar(s), ph ^ 1u) || *abort_flag)) {
@@ -228,10 +284,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           const uint32_t st = smem_base + s * STAGE_BYTES;
           mbar_expect_tx(full_bar(s), STAGE_BYTES);
-          tma_load_2d(st, &tm_ahi, full_bar(s), kb * BK, tm * BM);
-          tma_load_2d(st + A_TILE, &tm_alo, full_bar(s), kb * BK, tm * BM);
-          tma_load_2d(st + 2 * A_TILE, &tm_bhi, full_bar(s), kb * BK, tn * BN);
-          tma_load_2d(st + 2 * A_TILE + B_TILE, &tm_blo, full_bar(s), kb * BK, tn * BN);
+          load_stage<kGrouped>(st, &tm_ahi, &tm_alo, &tm_bhi, &tm_blo, full_bar(s), kb, tm, tn, mat);
           ++kg;
         }
       }
@@ -256,8 +309,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         tc_fence_after();
+        int mat, tm, tn, nk;
+        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
         const uint32_t d = tmem + buf * ACC_COLS;
-        for (int kb = 0; kb < ktiles; ++kb) {
+        for (int kb = 0; kb < nk; ++kb) {
           const uint32_t s = kg % STAGES;
           const uint32_t ph = (kg / STAGES) & 1u;
           if (!mbar_wait(full_bar(s), ph) || *abort_flag) {
@@ -287,8 +342,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(drain_bar, 0);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // ---------------- epilogue (warps 2 .. 2 + kWarps) ----------------
+    constexpr int kStep = EpiShape<kGrouped>::kWarps / 4;  // warps per TMEM lane quarter
+    constexpr int W = EpiShape<kGrouped>::kVec;
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;       // warps of one quarter take alternate column chunks
     bool bad = false;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -300,22 +358,31 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       tc_fence_after();
-      int tm, tn;
-      raster(tile, tiles_m, tiles_n, &tm, &tn);
+      int mat, tm, tn, nk;
+      tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
+      const EpiCtx x = epi_ctx(P, mat);
       const int r = tm * BM + q * 32 + lane;
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
+      // A grouped tile writes columns below its matrix's order rounded up to 32
+      // (= nk x 32): with that K padding zero in both operands, later columns only
+      // feed accumulator columns that every consumer discards.
+      // Rows at or past that bound are likewise never read as K padding.
+      const int nchunks = kGrouped ? nk : BN / 32;
+      const bool row_live = !kGrouped || r < nk * 32;
 #pragma unroll 1
-      for (int chunk = 0; chunk < BN / 32; ++chunk) {
+      for (int chunk = half; chunk < nchunks; chunk += kStep) {
         uint32_t v[32];
         __syncwarp();
         tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
         const int c0 = tn * BN + chunk * 32;
+        if (row_live) {
 #pragma unroll
-        for (int sub = 0; sub < 4; ++sub) {
-          float a8[8];
+          for (int sub = 0; sub < 32 / W; ++sub) {
+            float aw[W];
 #pragma unroll
-          for (int w = 0; w < 8; ++w) a8[w] = __uint_as_float(v[sub * 8 + w]);
-          bad |= epi_row<8, float>(P, r, c0 + sub * 8, a8);
+            for (int w = 0; w < W; ++w) aw[w] = __uint_as_float(v[sub * W + w]);
+            bad |= epi_row<W, float>(P, x, r, c0 + sub * W, aw);
+          }
         }
       }
       tc_fence_before();
@@ -352,33 +419,40 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box_rows) {
+// count == 0: 2-D map over one npad x npad array; count > 0: 3-D map over
+// count stacked slabs.
+bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box_rows, int count) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)npad};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)npad, (cuuint64_t)(count > 0 ? count : 1)};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)npad * (cuuint64_t)ld * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, count > 0 ? 3 : 2, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld) {
+bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
+                  int count) {
   if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0) return false;
-  return make_map(&m->a_hi, a_hi, npad, ld, BM) && make_map(&m->a_lo, a_lo, npad, ld, BM) &&
-         make_map(&m->b_hi, bt_hi, npad, ld, BN) && make_map(&m->b_lo, bt_lo, npad, ld, BN);
+  return make_map(&m->a_hi, a_hi, npad, ld, BM, count) && make_map(&m->a_lo, a_lo, npad, ld, BM, count) &&
+         make_map(&m->b_hi, bt_hi, npad, ld, BN, count) && make_map(&m->b_lo, bt_lo, npad, ld, BN, count);
 }
 
-cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s) {
+cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,
+                           const int4* tiles, int ntiles) {
   if (npad % BN != 0) return cudaErrorInvalidValue;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)SMEM_BYTES);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
   static int sms = 0;
@@ -387,10 +461,17 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
   }
+  if (tiles) {
+    if (ntiles <= 0) return cudaSuccess;
+    const int grid = ntiles < sms ? ntiles : sms;
+    tc_split_gemm_kernel<true><<<grid, EpiShape<true>::kThreads, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0,
+                                                                 0, tiles, ntiles, P);
+    return cudaGetLastError();
+  }
   const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
-  tc_split_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
-                                                         (int)(npad / BK), tiles_m, tiles_n, P);
+  tc_split_gemm_kernel<false><<<grid, EpiShape<false>::kThreads, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
+                                                                (int)(npad / BK), tiles_m, tiles_n, nullptr, 0, P);
   return cudaGetLastError();
 }
 

@@ -75,7 +75,7 @@ EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char
   P.n = (int)n;
   P.npad = (int)npad;
   P.nin = 1;
-  P.in[0] = EpiIn{X, ldx, DT_F64};
+  P.in[0] = EpiIn{X, ldx, DT_F64, EPI_PTR};
   P.nout = 1;
   EpiOut& o = P.out[0];
   o.in_d[0] = 1.0;
@@ -126,7 +126,7 @@ extern "C" int neumann_matmul_noalloc(int64_t n, const void* A, int64_t lda, con
   pc.out[0].acc_f = 1.0f;
   pc.out[0].f64 = 1;
   pc.out[0].ndst = 1;
-  pc.out[0].dst[0] = EpiDst{C, ldc, DT_F64, 0};
+  pc.out[0].dst[0] = EpiDst{C, ldc, DT_F64, EPI_PTR};
   pc.status = nullptr;
   if (launch_tc_gemm(maps, npad, pc, s) != cudaSuccess) return NEUMANN_ECUDA;
   return NEUMANN_OK;

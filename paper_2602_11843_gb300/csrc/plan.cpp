@@ -16,6 +16,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <utility>
 #include <new>
@@ -62,6 +63,8 @@ struct Op {
 enum Path { PATH_F64, PATH_F32, PATH_TC };
 
 constexpr int kMaxTimedProducts = 1 << 16;
+constexpr int64_t kGroupedMaxN = 256;  // batched orders up to this run as grouped launches
+constexpr int kGroupedChunk = 2048;    // matrices per grouped pass
 
 struct SlotBufs {
   size_t w, f64, a_hi, a_lo, b_hi, b_lo;
@@ -144,7 +147,33 @@ struct neumann_plan_s {
   bool batched = false;
   int count = 0;
   int64_t max_n = 0;
-  std::map<int64_t, neumann_plan_s*> sub;
+  std::map<int64_t, neumann_plan_s*> sub;  // per-order plans (max_n > 256)
+  // Grouped batched evaluation (max_n <= 256): `chunk` matrices at a time sit
+  // in stacked npad x npad slabs of every workspace buffer, and each operation
+  // of the scheme is one launch over all of them, driven by tile tables.
+  bool grouped = false;
+  int chunk = 0;
+  size_t slab = 0;  // elements per slab
+  // device tables for every chunk of the batch (offsets into the workspace)
+  size_t off_matn = 0, off_atab = 0, off_stab = 0, off_tc = 0, off_simt = 0, off_ew = 0;
+  // the chunk being launched: device pointers into those tables, entry counts
+  const int* cur_matn = nullptr;
+  const void* cur_atab = nullptr;
+  const void* cur_stab = nullptr;
+  const int4 *cur_tc = nullptr, *cur_simt = nullptr, *cur_ew = nullptr;
+  int n_tc = 0, n_simt = 0, n_ew = 0;
+  // pinned host image of the tables, the call it was built for, and the event
+  // after its upload (the image is rewritten only once that copy is done)
+  char* h_tab = nullptr;
+  size_t h_tab_bytes = 0;
+  cudaEvent_t tab_event = nullptr;
+  std::vector<int64_t> last_n;
+  std::vector<const void*> last_a;
+  std::vector<void*> last_s;
+  struct Chunk {
+    int first, count, tc0, ntc, simt0, nsimt, ew0, new_;
+  };
+  std::vector<Chunk> chunks;
 };
 
 namespace {
@@ -469,13 +498,25 @@ void note_reps(neumann_plan_s* p, const std::vector<Op>& ops) {
 }
 
 void layout(neumann_plan_s* p) {
-  const size_t nn = (size_t)p->npad * (size_t)p->npad;
+  // one matrix, or `chunk` stacked slabs in a grouped batched plan
+  const size_t nn = (size_t)p->npad * (size_t)p->npad * (size_t)(p->grouped ? p->chunk : 1);
   size_t off = 256;  // device status word(s)
   auto take = [&](size_t bytes) {
     size_t o = off;
     off += (bytes + 255) & ~(size_t)255;
     return o;
   };
+  if (p->grouped) {
+    const size_t c = (size_t)p->count;  // tables for every chunk of a full batch
+    const size_t tiles_per = (size_t)(p->npad / 128) * (size_t)(p->npad / 128);  // per matrix, at most
+    p->slab = (size_t)p->npad * (size_t)p->npad;
+    p->off_matn = take(c * sizeof(int));
+    p->off_atab = take(c * sizeof(void*));
+    p->off_stab = take(c * sizeof(void*));
+    p->off_tc = take(c * tiles_per * sizeof(int4));
+    p->off_simt = take(c * tiles_per * sizeof(int4));
+    p->off_ew = take(c * (size_t)(p->npad / 32) * (size_t)(p->npad / 32) * sizeof(int4));
+  }
   for (int s = 0; s < SL_N; ++s) {
     SlotBufs& b = p->bufs[s];
     b.w = b.f64 = b.a_hi = b.a_lo = b.b_hi = b.b_lo = NOBUF;
@@ -603,14 +644,17 @@ struct UserPtrs {
 
 EpiIn resolve_in(const neumann_plan_s* p, const InRef& r, const UserPtrs& u) {
   EpiIn e;
+  e.mode = EPI_WS;
   if (r.slot == SL_USER_A) {
-    e.p = u.A;
+    e.p = p->grouped ? p->cur_atab : u.A;
     e.ld = u.lda;
     e.dt = p->dt_io;
+    e.mode = p->grouped ? EPI_TABLE : EPI_PTR;
   } else if (r.slot == SL_USER_B) {
     e.p = u.B;
     e.ld = p->n;
     e.dt = p->dt_io;
+    e.mode = EPI_PTR;
   } else {
     const SlotBufs& b = p->bufs[r.slot];
     e.ld = p->npad;
@@ -639,22 +683,25 @@ EpiOut resolve_out(const neumann_plan_s* p, const OutSpec& s, const EpiIn* ins, 
     o.in_d[i] = s.in[i];
     o.in_f[i] = (float)s.in[i];
   }
-  auto dst = [&](void* ptr, int64_t ld, int dt, int pad) { o.dst[o.ndst++] = EpiDst{ptr, ld, dt, pad}; };
+  auto dst = [&](void* ptr, int64_t ld, int dt, int mode) { o.dst[o.ndst++] = EpiDst{ptr, ld, dt, mode}; };
   auto split = [&](size_t hi, size_t lo, int tr) {
     o.split[o.nsplit++] = EpiSplit{p->ws + hi, p->ws + lo, p->npad, tr};
   };
   if (s.slot == SL_USER_S) {
-    dst(u.S, u.lds, p->dt_io, 0);
+    if (p->grouped)
+      dst(const_cast<void*>(p->cur_stab), 0, p->dt_io, EPI_TABLE);
+    else
+      dst(u.S, u.lds, p->dt_io, EPI_PTR);
   } else {
     const SlotBufs& b = p->bufs[s.slot];
     if (p->path == PATH_F64) {
-      dst(p->ws + b.w, p->npad, DT_F64, 1);
+      dst(p->ws + b.w, p->npad, DT_F64, EPI_WS);
     } else if (p->path == PATH_F32) {
-      if (s.reps & (REP_W | REP_OPA | REP_OPB)) dst(p->ws + b.w, p->npad, DT_F32, 1);
-      if (s.reps & REP_F64) dst(p->ws + b.f64, p->npad, DT_F64, 1);
+      if (s.reps & (REP_W | REP_OPA | REP_OPB)) dst(p->ws + b.w, p->npad, DT_F32, EPI_WS);
+      if (s.reps & REP_F64) dst(p->ws + b.f64, p->npad, DT_F64, EPI_WS);
     } else {
-      if (s.reps & REP_W) dst(p->ws + b.w, p->npad, DT_F32, 1);
-      if (s.reps & REP_F64) dst(p->ws + b.f64, p->npad, DT_F64, 1);
+      if (s.reps & REP_W) dst(p->ws + b.w, p->npad, DT_F32, EPI_WS);
+      if (s.reps & REP_F64) dst(p->ws + b.f64, p->npad, DT_F64, EPI_WS);
       if (s.reps & REP_OPA) split(b.a_hi, b.a_lo, 0);
       if (s.reps & REP_OPB) split(b.b_hi, b.b_lo, 1);
     }
@@ -671,6 +718,10 @@ void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiPa
   P->n = (int)p->n;
   P->npad = (int)p->npad;
   P->status = reinterpret_cast<unsigned*>(p->ws);
+  if (p->grouped) {
+    P->mat_n = p->cur_matn;
+    P->mat_stride = (int64_t)p->slab;
+  }
   P->nin = op.nin;
   for (int i = 0; i < op.nin; ++i) P->in[i] = resolve_in(p, op.in[i], u);
   P->nout = op.nout;
@@ -685,7 +736,7 @@ bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMap
     const SlotBufs& a = p->bufs[op.a];
     const SlotBufs& b = p->bufs[op.b];
     if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + b.b_hi, p->ws + b.b_lo, p->npad,
-                      p->npad))
+                      p->npad, p->grouped ? p->chunk : 0))
       return false;
   }
   return true;
@@ -740,18 +791,23 @@ int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcM
     const Op& op = ops[i];
     make_params(p, op, u, &P);
     cudaError_t err;
+    const int4* ew = p->grouped ? p->cur_ew : nullptr;
+    const int4* st = p->grouped ? p->cur_simt : nullptr;
+    const int4* tt = p->grouped ? p->cur_tc : nullptr;
     if (op.kind == OP_EWISE) {
-      err = launch_ewise(P, s);
+      err = launch_ewise(P, s, ew, p->n_ew);
     } else {
       if (timing) cudaEventRecord(p->events[2 * gi], s);
       if (p->path == PATH_F64) {
         err = launch_simt_gemm_f64(reinterpret_cast<const double*>(p->ws + p->bufs[op.a].w),
-                                   reinterpret_cast<const double*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, P, s);
+                                   reinterpret_cast<const double*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, st,
+                                   p->n_simt, P, s);
       } else if (p->path == PATH_F32) {
         err = launch_simt_gemm_f32(reinterpret_cast<const float*>(p->ws + p->bufs[op.a].w),
-                                   reinterpret_cast<const float*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, P, s);
+                                   reinterpret_cast<const float*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, st,
+                                   p->n_simt, P, s);
       } else {
-        err = launch_tc_gemm(maps[i], p->npad, P, s);
+        err = launch_tc_gemm(maps[i], p->npad, P, s, tt, p->n_tc);
       }
       if (timing) cudaEventRecord(p->events[2 * gi + 1], s);
       ++gi;
@@ -779,6 +835,135 @@ int eval_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t lds
   p->last_stream = s;
   UserPtrs u{A, lda, nullptr, S, lds};
   return run_ops(p, p->ops, p->maps, u, s, (p->flags & NEUMANN_FLAG_TIMING) != 0);
+}
+
+// True if some S_i overlaps some A_j (n x n with leading dimension n): one
+// sweep over the intervals sorted by start address.
+bool batch_aliases(int count, const int64_t* n, const void* const* A, void* const* S, size_t es) {
+  struct Iv {
+    uintptr_t lo, hi;
+    bool s;
+  };
+  std::vector<Iv> iv;
+  iv.reserve(2 * (size_t)count);
+  for (int i = 0; i < count; ++i) {
+    const uintptr_t b = (uintptr_t)n[i] * (uintptr_t)n[i] * es;
+    iv.push_back(Iv{(uintptr_t)A[i], (uintptr_t)A[i] + b, false});
+    iv.push_back(Iv{(uintptr_t)S[i], (uintptr_t)S[i] + b, true});
+  }
+  std::sort(iv.begin(), iv.end(), [](const Iv& a, const Iv& b) { return a.lo < b.lo; });
+  uintptr_t end_a = 0, end_s = 0;
+  for (const Iv& x : iv) {
+    if (x.s ? x.lo < end_a : x.lo < end_s) return true;
+    if (x.s)
+      end_s = end_s > x.hi ? end_s : x.hi;
+    else
+      end_a = end_a > x.hi ? end_a : x.hi;
+  }
+  return false;
+}
+
+// Grouped batched evaluation. Matrices run in decreasing order (the longest
+// work first, for the persistent product kernel), `chunk` at a time. The host
+// builds, for the whole batch, the order table, the caller-pointer tables and
+// the tile tables of every chunk, copies them into the workspace from pinned
+// memory (skipped when orders and pointers repeat the previous call), and then
+// runs the plan's operations once per chunk.
+int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* const* A, void* const* S,
+                 cudaStream_t s) {
+  const bool same = (int)p->last_n.size() == count && std::equal(n, n + count, p->last_n.begin()) &&
+                    std::equal(A, A + count, p->last_a.begin()) && std::equal(S, S + count, p->last_s.begin());
+  if (!same) {
+    if (batch_aliases(count, n, A, S, elem_bytes(p->dt_io))) return NEUMANN_EINVAL;
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    std::vector<int> matn(count);
+    std::vector<const void*> atab(count);
+    std::vector<void*> stab(count);
+    std::vector<int4> tc, simt, ew;
+    p->chunks.clear();
+    for (int c0 = 0; c0 < count; c0 += p->chunk) {
+      const int cn = count - c0 < p->chunk ? count - c0 : p->chunk;
+      neumann_plan_s::Chunk ch{c0, cn, (int)tc.size(), 0, (int)simt.size(), 0, (int)ew.size(), 0};
+      for (int j = 0; j < cn; ++j) {
+        const int i = order[c0 + j];
+        const int ni = (int)n[i];
+        matn[c0 + j] = ni;
+        atab[c0 + j] = A[i];
+        stab[c0 + j] = S[i];
+        const int mt = (ni + 127) / 128;  // 128-row tiles
+        for (int tm = 0; tm < mt; ++tm) tc.push_back(make_int4(j, tm, (ni + 31) / 32, 0));
+        for (int tm = 0; tm < mt; ++tm)
+          for (int tn = 0; tn < mt; ++tn) simt.push_back(make_int4(j, tm, tn, (ni + 7) / 8));
+        // element-wise passes, like the products, write rows and columns below the
+        // order rounded up to 32: the K padding every later product reads
+        for (int tr = 0; tr < (ni + 31) / 32; ++tr)
+          for (int tcol = 0; tcol < (ni + 31) / 32; ++tcol) ew.push_back(make_int4(j, tr, tcol, 0));
+      }
+      ch.ntc = (int)tc.size() - ch.tc0;
+      ch.nsimt = (int)simt.size() - ch.simt0;
+      ch.new_ = (int)ew.size() - ch.ew0;
+      p->chunks.push_back(ch);
+    }
+    // pinned host image: [matn | atab | stab | tc | simt | ew], each 256-byte aligned
+    size_t o_matn = 0, o_atab, o_stab, o_tc, o_simt, o_ew, total;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    o_atab = al(o_matn + count * sizeof(int));
+    o_stab = al(o_atab + count * sizeof(void*));
+    o_tc = al(o_stab + count * sizeof(void*));
+    o_simt = al(o_tc + tc.size() * sizeof(int4));
+    o_ew = al(o_simt + simt.size() * sizeof(int4));
+    total = al(o_ew + ew.size() * sizeof(int4));
+    if (p->tab_event && cudaEventSynchronize(p->tab_event) != cudaSuccess) return NEUMANN_ECUDA;
+    if (total > p->h_tab_bytes) {
+      if (p->h_tab) cudaFreeHost(p->h_tab);
+      p->h_tab = nullptr;
+      p->h_tab_bytes = 0;
+      if (cudaMallocHost(reinterpret_cast<void**>(&p->h_tab), total) != cudaSuccess) {
+        cudaGetLastError();
+        return NEUMANN_ENOMEM;
+      }
+      p->h_tab_bytes = total;
+    }
+    if (!p->tab_event && cudaEventCreateWithFlags(&p->tab_event, cudaEventDisableTiming) != cudaSuccess)
+      return NEUMANN_ECUDA;
+    memcpy(p->h_tab + o_matn, matn.data(), count * sizeof(int));
+    memcpy(p->h_tab + o_atab, atab.data(), count * sizeof(void*));
+    memcpy(p->h_tab + o_stab, stab.data(), count * sizeof(void*));
+    memcpy(p->h_tab + o_tc, tc.data(), tc.size() * sizeof(int4));
+    memcpy(p->h_tab + o_simt, simt.data(), simt.size() * sizeof(int4));
+    memcpy(p->h_tab + o_ew, ew.data(), ew.size() * sizeof(int4));
+    char* ws = p->ws;
+    if (cudaMemcpyAsync(ws + p->off_matn, p->h_tab + o_matn, count * sizeof(int), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(ws + p->off_atab, p->h_tab + o_atab, count * sizeof(void*), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(ws + p->off_stab, p->h_tab + o_stab, count * sizeof(void*), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(ws + p->off_tc, p->h_tab + o_tc, tc.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(ws + p->off_simt, p->h_tab + o_simt, simt.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                        s) ||
+        cudaMemcpyAsync(ws + p->off_ew, p->h_tab + o_ew, ew.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
+        cudaEventRecord(p->tab_event, s))
+      return NEUMANN_ECUDA;
+    p->last_n.assign(n, n + count);
+    p->last_a.assign(A, A + count);
+    p->last_s.assign(S, S + count);
+  }
+  char* ws = p->ws;
+  for (const neumann_plan_s::Chunk& ch : p->chunks) {
+    p->cur_matn = reinterpret_cast<const int*>(ws + p->off_matn) + ch.first;
+    p->cur_atab = reinterpret_cast<const void* const*>(ws + p->off_atab) + ch.first;
+    p->cur_stab = reinterpret_cast<void* const*>(ws + p->off_stab) + ch.first;
+    p->cur_tc = reinterpret_cast<const int4*>(ws + p->off_tc) + ch.tc0;
+    p->cur_simt = reinterpret_cast<const int4*>(ws + p->off_simt) + ch.simt0;
+    p->cur_ew = reinterpret_cast<const int4*>(ws + p->off_ew) + ch.ew0;
+    p->n_tc = ch.ntc;
+    p->n_simt = ch.nsimt;
+    p->n_ew = ch.new_;
+    UserPtrs u{nullptr, 0, nullptr, nullptr, 0};
+    int rc = run_ops(p, p->ops, p->maps, u, s, (p->flags & NEUMANN_FLAG_TIMING) != 0);
+    if (rc) return rc;
+  }
+  return NEUMANN_OK;
 }
 
 }  // namespace
@@ -874,6 +1059,18 @@ int neumann_plan_create_batched(neumann_plan_t* out, int count, int64_t max_n, i
   p->batched = true;
   p->count = count;
   p->max_n = max_n;
+  if (max_n <= kGroupedMaxN && count > 0) {
+    // one padded slab per matrix; up to kGroupedChunk matrices per grouped pass
+    p->grouped = true;
+    p->chunk = count < kGroupedChunk ? count : kGroupedChunk;
+    p->npad = kGroupedMaxN;
+    try {
+      layout(p);
+    } catch (...) {
+      neumann_plan_destroy(p);
+      return NEUMANN_ENOMEM;
+    }
+  }
   *out = p;
   return NEUMANN_OK;
 }
@@ -890,6 +1087,7 @@ int neumann_eval_batched(neumann_plan_t p, int count, const int64_t* n, const vo
     int rc = ensure_workspace(p, s);
     if (rc) return rc;
     p->last_stream = s;
+    if (p->grouped) return eval_grouped(p, count, n, A, S, s);
     for (int i = 0; i < count; ++i) {
       neumann_plan_s*& sp = p->sub[n[i]];
       if (!sp) {
@@ -953,6 +1151,8 @@ void neumann_plan_destroy(neumann_plan_t p) {
     neumann_plan_destroy(kv.second);
   }
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->tab_event) cudaEventDestroy(p->tab_event);
+  if (p->h_tab) cudaFreeHost(p->h_tab);
   if (p->ws_owned) cudaFree(p->ws);
   delete p;
 }

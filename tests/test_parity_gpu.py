@@ -151,19 +151,63 @@ def test_timing_flag_reports_every_product():
     assert len(t) == p.info["products_executed"] == 10 and all(x > 0 for x in t)
 
 
-def test_batched_matches_oracle():
+BATCH_TOL = {"fp64": 1e-12, "fp32": 1e-5, "split_bf16": 2e-3}
+
+
+def _batch_check(bp, mats, k, radix, dtype):
+    dt = torch.float32 if dtype == "fp32" else torch.float64
+    As = [torch.tensor(m["A"], dtype=dt, device="cuda") for m in mats]
+    outs = bp(As)
+    torch.cuda.synchronize()
+    assert bp.status() == 0
+    for m, o in zip(mats, outs):
+        ref, _ = EV.evaluate(m["A"], k, radix)
+        err = CF.rel_fro(o.double().cpu().numpy(), ref)
+        assert err < BATCH_TOL[dtype], (m["n"], err)
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+@pytest.mark.parametrize("k,radix", [(81, 9), (225, 15), (64, 2), (81, 1)])
+def test_batched_grouped_matches_oracle(dtype, k, radix):
+    """Grouped launches over damped-Jacobi matrices of mixed order (cfg-4 construction)."""
     nm = _nm()
-    mats = G.jacobi_batch(24, 4001)
+    mats = G.jacobi_batch(20, 4001, sizes=(16, 48, 128, 144, 256))
+    mats += [{"n": n, "A": G.gaussian_scaled(n, 0.5, 50 + n)["A"]} for n in (1, 17, 129)]
+    bp = nm.BatchedPlan(len(mats), 256, k, radix, dtype)
+    _batch_check(bp, mats, k, radix, dtype)
+
+
+def test_batched_reuses_dirty_slabs():
+    """A second call with smaller matrices on slabs that held larger ones: every
+    buffer a product reads is rewritten up to its K padding."""
+    nm = _nm()
     for dtype in ("fp32", "split_bf16"):
-        bp = nm.BatchedPlan(len(mats), 256, 81, 9, dtype)
-        dt = torch.float32 if dtype == "fp32" else torch.float64
-        As = [torch.tensor(m["A"], dtype=dt, device="cuda") for m in mats]
-        outs = bp(As)
-        torch.cuda.synchronize()
-        assert bp.status() == 0
-        for m, o in zip(mats, outs):
-            ref, _ = EV.evaluate(m["A"], 81, 9)
-            assert CF.rel_fro(o.double().cpu().numpy(), ref) < (1e-5 if dtype == "fp32" else 2e-3)
+        bp = nm.BatchedPlan(6, 256, 81, 9, dtype)
+        big = [{"n": 256, "A": G.gaussian_scaled(256, 0.5, 60 + i)["A"]} for i in range(6)]
+        _batch_check(bp, big, 81, 9, dtype)
+        small = [{"n": n, "A": G.gaussian_scaled(n, 0.5, 70 + n)["A"]} for n in (5, 16, 31, 33, 100, 200)]
+        _batch_check(bp, small, 81, 9, dtype)
+
+
+def test_batched_more_than_one_chunk():
+    nm = _nm()
+    mats = [{"n": 16, "A": G.gaussian_scaled(16, 0.5, 9000 + i)["A"]} for i in range(2100)]
+    bp = nm.BatchedPlan(len(mats), 16, 81, 9, "split_bf16")
+    dt = torch.float64
+    As = [torch.tensor(m["A"], dtype=dt, device="cuda") for m in mats]
+    outs = bp(As)
+    torch.cuda.synchronize()
+    assert bp.status() == 0
+    for i in (0, 1, 1000, 2047, 2048, 2099):
+        ref, _ = EV.evaluate(mats[i]["A"], 81, 9)
+        assert CF.rel_fro(outs[i].cpu().numpy(), ref) < BATCH_TOL["split_bf16"]
+
+
+def test_batched_large_orders_fall_back_per_matrix():
+    nm = _nm()
+    mats = [{"n": n, "A": G.gaussian_scaled(n, 0.5, 80 + n)["A"]} for n in (300, 40)]
+    bp = nm.BatchedPlan(2, 300, 81, 9, "fp32")
+    _batch_check(bp, mats, 81, 9, "fp32")
 
 
 # ---------------------------------------------------------------- full-size workloads
