@@ -384,6 +384,148 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
   return bad;
 }
 
+// ---------------------------------------------------------------------------
+// Column form: W consecutive rows r0 .. r0+W-1 of column c (r0 % W == 0). A
+// warp whose lanes own consecutive columns reads and writes every row-major
+// buffer one cache line per instruction; a transposed hi/lo store is one
+// W x 2-byte run per lane. Requires W == 8 (16-byte transposed runs).
+
+template <int W>
+__device__ __forceinline__ void st_col_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[W]) {
+  __nv_bfloat16 hi[W], lo[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    hi[w] = __float2bfloat16_rn(v[w]);
+    lo[w] = __float2bfloat16_rn(v[w] - __bfloat162float(hi[w]));
+  }
+  if (sp.transposed) {
+    uint32_t ph[W / 2], pl[W / 2];
+#pragma unroll
+    for (int q = 0; q < W / 2; ++q) {
+      ph[q] = (uint32_t)__bfloat16_as_ushort(hi[2 * q]) | ((uint32_t)__bfloat16_as_ushort(hi[2 * q + 1]) << 16);
+      pl[q] = (uint32_t)__bfloat16_as_ushort(lo[2 * q]) | ((uint32_t)__bfloat16_as_ushort(lo[2 * q + 1]) << 16);
+    }
+    const int64_t off = x.off + (int64_t)c * sp.ld + r0;
+    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(sp.hi) + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(sp.lo) + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+  } else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const int64_t off = x.off + (int64_t)(r0 + w) * sp.ld + c;
+      reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = hi[w];
+      reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = lo[w];
+    }
+  }
+}
+
+// kWsOnly: padding, workspace destinations only
+template <int W, typename V, bool kWsOnly = false>
+__device__ __forceinline__ void st_col(const EpiOut& o, const EpiCtx& x, int r0, int c, const V (&v)[W]) {
+  for (int d = 0; d < o.ndst; ++d) {
+    const EpiDst& ds = o.dst[d];
+    if (kWsOnly && ds.mode != EPI_WS) continue;
+    int64_t ld;
+    if (ds.dt == DT_F64) {
+      double* q = dst_base<double>(ds, x, &ld) + c;
+#pragma unroll
+      for (int w = 0; w < W; ++w) q[(int64_t)(r0 + w) * ld] = (double)v[w];
+    } else {
+      float* q = dst_base<float>(ds, x, &ld) + c;
+#pragma unroll
+      for (int w = 0; w < W; ++w) q[(int64_t)(r0 + w) * ld] = (float)v[w];
+    }
+  }
+  if (o.nsplit) {
+    float vf[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) vf[w] = (float)v[w];  // pairs from RN_fp32 of the output
+    for (int s = 0; s < o.nsplit; ++s) st_col_split<W>(o.split[s], x, r0, c, vf);
+  }
+}
+
+template <int W, typename AccT>
+__device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int r0, int c, const AccT (&acc)[W]) {
+  static_assert(W == 8, "transposed runs are 16 bytes");
+  static_assert(sizeof(AccT) == 4, "FP32 accumulators (tensor-core products)");
+  if (c >= x.n || r0 >= x.n) {  // the whole run is padding
+    float z[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) z[w] = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < P.nout; ++j) st_col<W, float, true>(P.out[j], x, r0, c, z);
+    return false;
+  }
+  if (r0 + W > x.n) {  // ragged edge
+    bool bad = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) bad |= epi_element<AccT>(P, x, r0 + w, c, acc[w]);
+    return bad;
+  }
+  float fin[kMaxIn][W];
+  double din[kMaxIn][W];
+#pragma unroll
+  for (int i = 0; i < kMaxIn; ++i) {
+    if (i < P.nin) {
+      const EpiIn& in = P.in[i];
+      if (in.dt == DT_F64) {
+        const double* q = reinterpret_cast<const double*>(in.p) + x.off + (int64_t)r0 * in.ld + c;
+#pragma unroll
+        for (int w = 0; w < W; ++w) din[i][w] = q[(int64_t)w * in.ld];
+      } else {
+        const float* q = reinterpret_cast<const float*>(in.p) + x.off + (int64_t)r0 * in.ld + c;
+#pragma unroll
+        for (int w = 0; w < W; ++w) fin[i][w] = q[(int64_t)w * in.ld];
+      }
+    }
+  }
+  bool bad = false;
+#pragma unroll 1
+  for (int j = 0; j < P.nout; ++j) {
+    const EpiOut& o = P.out[j];
+    if (o.f64) {
+      double v[W];
+      float vf[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) vf[w] = o.acc_f * (float)acc[w];
+#pragma unroll
+      for (int i = 0; i < kMaxIn; ++i) {
+        if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) vf[w] = fmaf(o.in_f[i], fin[i][w], vf[w]);
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[w] = (double)vf[w] + (r0 + w == c ? o.id_d : 0.0);
+#pragma unroll
+      for (int i = 0; i < kMaxIn; ++i) {
+        if (i < P.nin && o.in_d[i] != 0.0 && P.in[i].dt == DT_F64) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) v[w] = fma(o.in_d[i], din[i][w], v[w]);
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
+      st_col<W, double>(o, x, r0, c, v);
+    } else {
+      float v[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[w] = o.acc_f * (float)acc[w] + (r0 + w == c ? o.id_f : 0.f);
+#pragma unroll
+      for (int i = 0; i < kMaxIn; ++i) {
+        if (i < P.nin && o.in_f[i] != 0.f) {
+          const bool f = P.in[i].dt == DT_F64;
+#pragma unroll
+          for (int w = 0; w < W; ++w) v[w] = fmaf(o.in_f[i], f ? (float)din[i][w] : fin[i][w], v[w]);
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
+      st_col<W, float>(o, x, r0, c, v);
+    }
+  }
+  return bad;
+}
+
 __device__ __forceinline__ void epi_flag(const EpiParams& P, bool bad) {
   if (bad && P.status) atomicOr(P.status, 1u);
 }

@@ -37,20 +37,21 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 32;  // bf16 elements per stage row = 64 bytes
 constexpr int STAGES = 4;
+
+constexpr uint32_t A_TILE = BM * BK * 2;  // 8 KiB
+constexpr uint32_t B_TILE = BN * BK * 2;  // 16 KiB
+constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+constexpr uint32_t STG_FLOATS = 32 * 33;  // one epilogue warp's 32 x 32 staging tile, padded
 // Epilogue warps: a single large product has long K loops that hide a 4-warp
-// epilogue working on 8-wide rows; a grouped launch over small matrices has
-// short K loops, so its epilogue is the critical path and gets 8 warps (two per
-// TMEM lane quarter, 4-wide rows to stay within the register budget).
+// epilogue; a grouped launch over small matrices has short K loops, so its
+// epilogue is the critical path and gets 8 warps (two per TMEM lane quarter).
 template <bool kGrouped>
 struct EpiShape {
   static constexpr int kWarps = kGrouped ? 8 : 4;
   static constexpr int kThreads = 64 + 32 * kWarps;  // TMA warp, MMA warp, epilogue warps
-  static constexpr int kVec = kGrouped ? 4 : 8;
+  // stages | barriers, TMEM address, abort flag (256 B) | staging tiles (+ alignment slack)
+  static constexpr uint32_t kSmem = STAGES * STAGE_BYTES + 256 + kWarps * STG_FLOATS * 4 + 1024;
 };
-constexpr uint32_t A_TILE = BM * BK * 2;  // 8 KiB
-constexpr uint32_t B_TILE = BN * BK * 2;  // 16 KiB
-constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
-constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t ACC_COLS = BN;              // one FP32 accumulator: 128 lanes x 256 columns
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // double-buffered
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s; a whole launch normally takes < 20 ms
@@ -343,10 +344,13 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
     }
   } else {
     // ---------------- epilogue (warps 2 .. 2 + kWarps) ----------------
+    // Each 32 x 32 chunk is read from TMEM one row per lane, staged in shared
+    // memory, and processed one column per lane (epi_col), so that the warp's
+    // global loads and stores of row-major buffers touch one line per instruction.
     constexpr int kStep = EpiShape<kGrouped>::kWarps / 4;  // warps per TMEM lane quarter
-    constexpr int W = EpiShape<kGrouped>::kVec;
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;       // warps of one quarter take alternate column chunks
+    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * STG_FLOATS;
     bool bad = false;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -361,29 +365,32 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
       int mat, tm, tn, nk;
       tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
       const EpiCtx x = epi_ctx(P, mat);
-      const int r = tm * BM + q * 32 + lane;
+      const int rbase = tm * BM + q * 32;
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
-      // A grouped tile writes columns below its matrix's order rounded up to 32
-      // (= nk x 32): with that K padding zero in both operands, later columns only
-      // feed accumulator columns that every consumer discards.
-      // Rows at or past that bound are likewise never read as K padding.
+      // A grouped tile writes rows and columns below its matrix's order rounded
+      // up to 32 (= nk x 32): with that K padding zero in both operands, later
+      // rows and columns only feed accumulator entries every consumer discards.
       const int nchunks = kGrouped ? nk : BN / 32;
-      const bool row_live = !kGrouped || r < nk * 32;
+      const int lim = kGrouped ? nk * 32 : (1 << 30);
 #pragma unroll 1
       for (int chunk = half; chunk < nchunks; chunk += kStep) {
         uint32_t v[32];
         __syncwarp();
         tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
-        const int c0 = tn * BN + chunk * 32;
-        if (row_live) {
 #pragma unroll
-          for (int sub = 0; sub < 32 / W; ++sub) {
-            float aw[W];
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int c = tn * BN + chunk * 32 + lane;
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+          const int r0 = rbase + 8 * g;
+          if (r0 >= lim) break;
+          float a8[8];
 #pragma unroll
-            for (int w = 0; w < W; ++w) aw[w] = __uint_as_float(v[sub * W + w]);
-            bad |= epi_row<W, float>(P, x, r, c0 + sub * W, aw);
-          }
+          for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
+          bad |= epi_col<8, float>(P, x, r0, c, a8);
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -449,10 +456,10 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
     attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)SMEM_BYTES);
+                                    (int)EpiShape<false>::kSmem);
     if (attr_err == cudaSuccess)
       attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)SMEM_BYTES);
+                                      (int)EpiShape<true>::kSmem);
   });
   if (attr_err != cudaSuccess) return attr_err;
   static int sms = 0;
@@ -464,13 +471,13 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
     const int grid = ntiles < sms ? ntiles : sms;
-    tc_split_gemm_kernel<true><<<grid, EpiShape<true>::kThreads, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0,
+    tc_split_gemm_kernel<true><<<grid, EpiShape<true>::kThreads, EpiShape<true>::kSmem, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0,
                                                                  0, tiles, ntiles, P);
     return cudaGetLastError();
   }
   const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
-  tc_split_gemm_kernel<false><<<grid, EpiShape<false>::kThreads, SMEM_BYTES, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
+  tc_split_gemm_kernel<false><<<grid, EpiShape<false>::kThreads, EpiShape<false>::kSmem, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
                                                                 (int)(npad / BK), tiles_m, tiles_n, nullptr, 0, P);
   return cudaGetLastError();
 }
