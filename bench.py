@@ -68,6 +68,23 @@ def _src_sha(name):
         return hashlib.sha1(f.read()).hexdigest()[:12]
 
 
+def reduce_max_ms(ms, world, device=None):
+    """The job time: the maximum over ranks of each rank's timed region (ms)."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step, steps, world, ms_max):
+    """Whole-job throughput: the units every rank processed over the job time."""
+    return units_per_rank_step * steps * world / (ms_max / 1e3)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -289,14 +306,12 @@ def run_batched(args, wl):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max_ms(ms, world, dev)
     prod_ms = nm.neumann_plan_timing(bp.handle, 1 << 16)
     status = bp.status()
-    value = len(mats) * args.steps * world / (ms_max / 1e3)
+    value = job_value(len(mats), args.steps, world, ms_max)
     info = nm.neumann_plan_info(bp.handle)
     # the same batch, one plan per matrix order and one evaluation (own launches) per matrix
     plans = {}
@@ -328,7 +343,7 @@ def run_batched(args, wl):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_value = len(mats) * args.steps * world / (e0.elapsed_time(e1) / 1e3)
+    e2e_value = job_value(len(mats), args.steps, world, reduce_max_ms(e0.elapsed_time(e1), world, dev))
     nm.neumann_plan_timing(bp.handle, 1 << 16)
     peaks, peak_src = _peaks()
     tc = wl["dtype"].startswith("split")
@@ -445,15 +460,11 @@ def run_ours(args, wl):
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max_ms(ev0.elapsed_time(ev1), world, dev)
     prod_ms = plan.timing()
     status = plan.status()
     info = plan.info
-    value = args.steps * world / (ms_max / 1e3)
+    value = job_value(1, args.steps, world, ms_max)
 
     # repeated squaring on the same input and arithmetic (the paper's binary comparator)
     sq = nm.Plan(n, wl["sq_k"], 2, wl["dtype"])
@@ -467,6 +478,26 @@ def run_ours(args, wl):
     e1.record(stream)
     torch.cuda.synchronize()
     sq_ms = e0.elapsed_time(e1) / args.steps
+
+    # the plain FP64 path on the same input: one evaluation (GB300 runs FP64 at
+    # 1/64 of the FP32 rate, so this takes seconds), and the split result's
+    # relative Frobenius distance from it
+    fp64 = None
+    if wl["dtype"] != "fp64" and not args.no_fp64:
+        p64 = nm.Plan(n, k, wl["radix"], "fp64")
+        A64 = A.double() if A.dtype != torch.float64 else A
+        S64 = torch.empty_like(A64)
+        e0.record(stream)
+        p64(A64, out=S64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e0.elapsed_time(e1)
+        plan(A, out=S)
+        torch.cuda.synchronize()
+        diff = float(torch.linalg.norm(S.double() - S64) / torch.linalg.norm(S64))
+        fp64 = {"ms_per_step": fp64_ms, "speedup": fp64_ms / (ms_max / args.steps), "rel_fro_vs_fp64": diff,
+                "products": p64.info["products_executed"]}
+        del p64, A64, S64
 
     # end to end through the C ABI: pinned host A in, host S out, every step
     A_host = torch.tensor(A_np, dtype=io).pin_memory()
@@ -485,11 +516,7 @@ def run_ours(args, wl):
         S_host.copy_(S, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = args.steps * world / (float(te.item()) / 1e3)
+    e2e_value = job_value(1, args.steps, world, reduce_max_ms(e0.elapsed_time(e1), world, dev))
     plan.timing()
 
     peaks, peak_src = _peaks()
@@ -537,6 +564,7 @@ def run_ours(args, wl):
         "vs_squaring": {"k": wl["sq_k"], "ms_per_step": sq_ms, "speedup": sq_ms / (ms_max / args.steps),
                         "products_executed": sq.info["products_executed"],
                         "formula_ratio": sq.info["products_formula"] / info["products_formula"]},
+        "vs_fp64": fp64,
         "status": status,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": A_host.numel() * A_host.element_size(),
@@ -560,6 +588,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison evaluation")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
