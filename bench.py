@@ -35,6 +35,8 @@ UNIT = "S_k/s"
 WORKLOADS = {
     "precision-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096),
     "precision-r9-bf16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_bf16", sq_k=8192),
+    "precision-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096),
+    "precision-r9-fp16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_fp16", sq_k=8192),
     "plain-r9-fp32-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
     "plain-r15-fp32-n4096-k225": dict(cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
     "plain-r9-fp64-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
@@ -553,8 +555,10 @@ def run_ours(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if tc else ("f32" if wl["dtype"] == "fp32" else "f64"),
+        "vs_baseline": None,
+        "dtype": {"split_bf16": "bf16", "split_fp16": "f16", "fp32": "f32", "fp64": "f64"}[wl["dtype"]],
         "precision": {"split_bf16": "hi+lo BF16 operands, 3 products, FP32 accumulate, FP64 Y and R",
+                      "split_fp16": "hi+lo FP16 operands of x*2^8, 3 products, FP32 accumulate, FP64 Y and R",
                       "fp32": "FP32 products, FP64 Y and R", "fp64": "FP64"}[wl["dtype"]],
         "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "k": k, "radix": wl["radix"], "scheme": wl["dtype"],

@@ -30,7 +30,10 @@
  *               operands (x = hi + lo, three products hi*hi + hi*lo + lo*hi,
  *               FP32 accumulation in tensor memory); Y and R accumulated in
  *               FP64. A and S are double unless NEUMANN_FLAG_IO_FP32.
- *   SPLIT_FP16  reserved; neumann_plan_create returns NEUMANN_ENOTSUP.
+ *   SPLIT_FP16  as SPLIT_BF16 with FP16 hi+lo operands of x * 2^8 (x = hi + lo to
+ *               ~2^-22 relative for |x| >= 2^-11, ~2^-32 absolute below); every
+ *               entry of every intermediate must stay below 255 in magnitude, an
+ *               overflow sets NEUMANN_STATUS_NONFINITE.
  *
  * Conventions shared by every call:
  *   - Matrices are dense, row-major, n x n, with a leading dimension (in

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.h"
 
@@ -63,12 +64,31 @@ __device__ __forceinline__ T* dst_base(const EpiDst& ds, const EpiCtx& x, int64_
   return reinterpret_cast<T*>(ds.p);
 }
 
+// The 16-bit hi/lo pair of v as raw bits (BF16, or scaled FP16; see EpiSplit).
+__device__ __forceinline__ void split_bits(float v, int fp16, unsigned short* hi, unsigned short* lo) {
+  if (fp16) {
+    const float w = v * kFp16SplitScale;
+    const __half h = __float2half_rn(w);
+    *hi = __half_as_ushort(h);
+    *lo = __half_as_ushort(__float2half_rn(w - __half2float(h)));
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    *hi = __bfloat16_as_ushort(h);
+    *lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+  }
+}
+
+// An FP16 hi that overflowed (|v| * 2^8 beyond the FP16 range) is non-finite.
+__device__ __forceinline__ bool split_bad(float v, int fp16) {
+  return fp16 && !isfinite(__half2float(__float2half_rn(v * kFp16SplitScale)));
+}
+
 __device__ __forceinline__ void split_store(const EpiSplit& s, const EpiCtx& x, int r, int c, float v) {
-  __nv_bfloat16 hi = __float2bfloat16_rn(v);
-  __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  unsigned short hi, lo;
+  split_bits(v, s.fp16, &hi, &lo);
   int64_t off = x.off + (s.transposed ? (int64_t)c * s.ld + r : (int64_t)r * s.ld + c);
-  reinterpret_cast<__nv_bfloat16*>(s.hi)[off] = hi;
-  reinterpret_cast<__nv_bfloat16*>(s.lo)[off] = lo;
+  reinterpret_cast<unsigned short*>(s.hi)[off] = hi;
+  reinterpret_cast<unsigned short*>(s.lo)[off] = lo;
 }
 
 // Write 0 to every workspace destination of element (r, c) outside the n x n
@@ -91,8 +111,8 @@ __device__ __forceinline__ void epi_padding(const EpiParams& P, const EpiCtx& x,
       const EpiSplit& sp = o.split[s];
       if (kSkipT && sp.transposed) continue;
       const int64_t off = x.off + (sp.transposed ? (int64_t)c * sp.ld + r : (int64_t)r * sp.ld + c);
-      reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = __float2bfloat16_rn(0.f);
-      reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = __float2bfloat16_rn(0.f);
+      reinterpret_cast<unsigned short*>(sp.hi)[off] = 0;  // +0 in BF16 and FP16
+      reinterpret_cast<unsigned short*>(sp.lo)[off] = 0;
     }
   }
 }
@@ -177,6 +197,7 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
     }
     // hi/lo pairs are formed from RN_fp32 of the output: FP32 keeps 24 bits, the pair 16
     for (int s = 0; s < o.nsplit; ++s) {
+      bad |= split_bad(vf, o.split[s].fp16);
       if (kDeferT && o.split[s].transposed)
         tv[j] = vf;
       else
@@ -249,19 +270,15 @@ __device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, 
   }
   for (int s = 0; s < o.nsplit; ++s) {
     const EpiSplit& sp = o.split[s];
-    __nv_bfloat16 hi[W], lo[W];
+    unsigned short hi[W], lo[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) {  // from RN_fp32(v): FP32 keeps 24 bits, the pair 16
-      const float vf = (float)v[w];
-      hi[w] = __float2bfloat16_rn(vf);
-      lo[w] = __float2bfloat16_rn(vf - __bfloat162float(hi[w]));
-    }
+    for (int w = 0; w < W; ++w) split_bits((float)v[w], sp.fp16, &hi[w], &lo[w]);  // from RN_fp32(v)
     if (sp.transposed) {
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         const int64_t off = x.off + (int64_t)(c0 + w) * sp.ld + r;
-        reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = hi[w];
-        reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = lo[w];
+        reinterpret_cast<unsigned short*>(sp.hi)[off] = hi[w];
+        reinterpret_cast<unsigned short*>(sp.lo)[off] = lo[w];
       }
     } else {
       const int64_t off = x.off + (int64_t)r * sp.ld + c0;
@@ -269,11 +286,11 @@ __device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, 
       uint32_t ph[W / 2], pl[W / 2];
 #pragma unroll
       for (int q = 0; q < W / 2; ++q) {
-        ph[q] = (uint32_t)__bfloat16_as_ushort(hi[2 * q]) | ((uint32_t)__bfloat16_as_ushort(hi[2 * q + 1]) << 16);
-        pl[q] = (uint32_t)__bfloat16_as_ushort(lo[2 * q]) | ((uint32_t)__bfloat16_as_ushort(lo[2 * q + 1]) << 16);
+        ph[q] = (uint32_t)hi[2 * q] | ((uint32_t)hi[2 * q + 1] << 16);
+        pl[q] = (uint32_t)lo[2 * q] | ((uint32_t)lo[2 * q + 1] << 16);
       }
-      __nv_bfloat16* qh = reinterpret_cast<__nv_bfloat16*>(sp.hi) + off;
-      __nv_bfloat16* ql = reinterpret_cast<__nv_bfloat16*>(sp.lo) + off;
+      unsigned short* qh = reinterpret_cast<unsigned short*>(sp.hi) + off;
+      unsigned short* ql = reinterpret_cast<unsigned short*>(sp.lo) + off;
       if constexpr (W == 8) {
         *reinterpret_cast<uint4*>(qh) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
         *reinterpret_cast<uint4*>(ql) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
@@ -294,6 +311,18 @@ __device__ __forceinline__ void epi_row_zero(const EpiParams& P, const EpiCtx& x
   for (int w = 0; w < W; ++w) z[w] = 0.f;
 #pragma unroll 1
   for (int j = 0; j < P.nout; ++j) st_row<W, float, true>(P.out[j], x, r, c0, z);
+}
+
+// A scaled FP16 split of any of these values overflows.
+template <int W, typename V>
+__device__ __forceinline__ bool fp16_overflow(const EpiOut& o, const V (&v)[W]) {
+  bool any = false;
+  for (int s = 0; s < o.nsplit; ++s) any |= o.split[s].fp16 != 0;
+  if (!any) return false;
+  bool bad = false;
+#pragma unroll
+  for (int w = 0; w < W; ++w) bad |= !(fabsf((float)v[w]) * kFp16SplitScale < 65504.f);
+  return bad;
 }
 
 template <int W, typename AccT>
@@ -363,6 +392,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
+      bad |= fp16_overflow<W, double>(o, v);
       st_row<W, double>(o, x, r, c0, v);
     } else {
       float v[W];
@@ -378,6 +408,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
+      bad |= fp16_overflow<W, float>(o, v);
       st_row<W, float>(o, x, r, c0, v);
     }
   }
@@ -392,28 +423,25 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
 
 template <int W>
 __device__ __forceinline__ void st_col_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[W]) {
-  __nv_bfloat16 hi[W], lo[W];
+  unsigned short hi[W], lo[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) {
-    hi[w] = __float2bfloat16_rn(v[w]);
-    lo[w] = __float2bfloat16_rn(v[w] - __bfloat162float(hi[w]));
-  }
+  for (int w = 0; w < W; ++w) split_bits(v[w], sp.fp16, &hi[w], &lo[w]);
   if (sp.transposed) {
     uint32_t ph[W / 2], pl[W / 2];
 #pragma unroll
     for (int q = 0; q < W / 2; ++q) {
-      ph[q] = (uint32_t)__bfloat16_as_ushort(hi[2 * q]) | ((uint32_t)__bfloat16_as_ushort(hi[2 * q + 1]) << 16);
-      pl[q] = (uint32_t)__bfloat16_as_ushort(lo[2 * q]) | ((uint32_t)__bfloat16_as_ushort(lo[2 * q + 1]) << 16);
+      ph[q] = (uint32_t)hi[2 * q] | ((uint32_t)hi[2 * q + 1] << 16);
+      pl[q] = (uint32_t)lo[2 * q] | ((uint32_t)lo[2 * q + 1] << 16);
     }
     const int64_t off = x.off + (int64_t)c * sp.ld + r0;
-    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(sp.hi) + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(sp.lo) + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned short*>(sp.hi) + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned short*>(sp.lo) + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   } else {
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       const int64_t off = x.off + (int64_t)(r0 + w) * sp.ld + c;
-      reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = hi[w];
-      reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = lo[w];
+      reinterpret_cast<unsigned short*>(sp.hi)[off] = hi[w];
+      reinterpret_cast<unsigned short*>(sp.lo)[off] = lo[w];
     }
   }
 }
@@ -505,6 +533,7 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
+      bad |= fp16_overflow<W, double>(o, v);
       st_col<W, double>(o, x, r0, c, v);
     } else {
       float v[W];
@@ -520,6 +549,7 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
+      bad |= fp16_overflow<W, float>(o, v);
       st_col<W, float>(o, x, r0, c, v);
     }
   }

@@ -41,13 +41,20 @@ struct EpiDst {
   int mode;
 };
 
-// A split store: hi = RN_bf16(v), lo = RN_bf16(v - hi), row-major or transposed.
+// A split store, row-major or transposed:
+//   BF16: hi = RN_bf16(v), lo = RN_bf16(v - hi)
+//   FP16: w = v * 2^8, hi = RN_fp16(w), lo = RN_fp16(w - hi)  (the fixed power of
+//         two keeps lo out of the FP16 subnormals for |v| >= 2^-11 and limits |v| to
+//         < 2^7; a product of two such operands carries 2^16, removed in the epilogue)
 struct EpiSplit {
   void* hi;
   void* lo;
   int64_t ld;
   int transposed;
+  int fp16;
 };
+
+constexpr float kFp16SplitScale = 256.0f;  // 2^8
 
 // out = acc_coef * acc + sum_i in_coef[i] * in[i] + id_coef * [r == c]
 struct EpiOut {
@@ -80,9 +87,10 @@ struct EpiParams {
 
 // Split-operand tensor maps of one tensor-core product C = A B:
 // A as (hi, lo) row-major, B as (hi, lo) stored transposed (row j of the
-// stored matrix is column j of B), both padded_n x padded_n, BF16.
+// stored matrix is column j of B), both padded_n x padded_n, BF16 or FP16.
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  int fp16;
 };
 
 // ---- launchers (kernels_simt.cu) ----
@@ -101,7 +109,7 @@ cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles =
 // dimension ld; with count > 0, over count stacked padded_n x padded_n slabs
 // (3-D maps, one slab per matrix of a batch).
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count = 0);
+                  int count = 0, int fp16 = 0);
 // tiles == nullptr: one npad x npad product. Otherwise a grouped launch over a
 // batch (3-D maps): ntiles entries {matrix, tile row, K steps of 32, 0}; each
 // tile covers 128 rows and all 256 columns of its matrix's slab.

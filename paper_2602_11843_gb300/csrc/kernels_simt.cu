@@ -180,11 +180,11 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
       for (int q = 0; q < 4; ++q) {
         // lane tx writes element (r0 + tx, c0 + ty + 8q) at row c, column r of the stored transpose
         const float v = tile[j][tx][ty + 8 * q];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        unsigned short hi, lo;
+        split_bits(v, sp.fp16, &hi, &lo);
         const int64_t off = x.off + (int64_t)(c0 + ty + 8 * q) * sp.ld + (r0 + tx);
-        reinterpret_cast<__nv_bfloat16*>(sp.hi)[off] = hi;
-        reinterpret_cast<__nv_bfloat16*>(sp.lo)[off] = lo;
+        reinterpret_cast<unsigned short*>(sp.hi)[off] = hi;
+        reinterpret_cast<unsigned short*>(sp.lo)[off] = lo;
       }
     }
   }

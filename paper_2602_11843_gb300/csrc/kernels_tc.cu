@@ -56,11 +56,12 @@ constexpr uint32_t ACC_COLS = BN;              // one FP32 accumulator: 128 lane
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // double-buffered
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s; a whole launch normally takes < 20 ms
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
-// M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A and B both
+// BF16 (format 1 at bits 7-9 and 10-12) or both FP16 (format 0), both K-major
+// (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -138,12 +139,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
                          int ktiles, int tiles_m, int tiles_n, const int4* __restrict__ tiles, int ntiles_grouped,
-                         const __grid_constant__ EpiParams P) {
+                         uint32_t idesc, const __grid_constant__ EpiParams P) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain
@@ -328,9 +330,9 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
             const uint64_t a_lo = smem_desc(st + A_TILE + 32u * j);
             const uint64_t b_hi = smem_desc(st + 2 * A_TILE + 32u * j);
             const uint64_t b_lo = smem_desc(st + 2 * A_TILE + B_TILE + 32u * j);
-            umma_f16(d, a_hi, b_hi, (kb | j) != 0);
-            umma_f16(d, a_hi, b_lo, 1u);
-            umma_f16(d, a_lo, b_hi, 1u);
+            umma_f16(d, a_hi, b_hi, idesc, (kb | j) != 0);
+            umma_f16(d, a_hi, b_lo, idesc, 1u);
+            umma_f16(d, a_lo, b_hi, idesc, 1u);
           }
           umma_commit(empty_bar(s));
           ++kg;
@@ -428,14 +430,15 @@ EncodeTiledFn encode_fn() {
 
 // count == 0: 2-D map over one npad x npad array; count > 0: 3-D map over
 // count stacked slabs.
-bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box_rows, int count) {
+bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box_rows, int count, int fp16) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)npad, (cuuint64_t)npad, (cuuint64_t)(count > 0 ? count : 1)};
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)npad * (cuuint64_t)ld * 2};
   cuuint32_t box[3] = {(cuuint32_t)BK, box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, count > 0 ? 3 : 2, base, dims, strides, box, estr,
+  return enc(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, count > 0 ? 3 : 2,
+             base, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -443,10 +446,11 @@ bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box
 }  // namespace
 
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count) {
+                  int count, int fp16) {
   if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0) return false;
-  return make_map(&m->a_hi, a_hi, npad, ld, BM, count) && make_map(&m->a_lo, a_lo, npad, ld, BM, count) &&
-         make_map(&m->b_hi, bt_hi, npad, ld, BN, count) && make_map(&m->b_lo, bt_lo, npad, ld, BN, count);
+  m->fp16 = fp16;
+  return make_map(&m->a_hi, a_hi, npad, ld, BM, count, fp16) && make_map(&m->a_lo, a_lo, npad, ld, BM, count, fp16) &&
+         make_map(&m->b_hi, bt_hi, npad, ld, BN, count, fp16) && make_map(&m->b_lo, bt_lo, npad, ld, BN, count, fp16);
 }
 
 cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,
@@ -471,14 +475,15 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
     const int grid = ntiles < sms ? ntiles : sms;
-    tc_split_gemm_kernel<true><<<grid, EpiShape<true>::kThreads, EpiShape<true>::kSmem, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0,
-                                                                 0, tiles, ntiles, P);
+    tc_split_gemm_kernel<true><<<grid, EpiShape<true>::kThreads, EpiShape<true>::kSmem, s>>>(
+        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, tiles, ntiles, maps.fp16 ? kIdescF16 : kIdescBf16, P);
     return cudaGetLastError();
   }
   const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
-  tc_split_gemm_kernel<false><<<grid, EpiShape<false>::kThreads, EpiShape<false>::kSmem, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo,
-                                                                (int)(npad / BK), tiles_m, tiles_n, nullptr, 0, P);
+  tc_split_gemm_kernel<false><<<grid, EpiShape<false>::kThreads, EpiShape<false>::kSmem, s>>>(
+      maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, nullptr, 0,
+      maps.fp16 ? kIdescF16 : kIdescBf16, P);
   return cudaGetLastError();
 }
 

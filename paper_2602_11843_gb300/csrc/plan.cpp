@@ -611,7 +611,6 @@ int validate_and_levels(neumann_plan_s* p) {
 int init_plan(neumann_plan_s* p, int64_t n, int64_t k, int radix, int dtype, uint32_t flags) {
   if (n < 1 || k < 1 || n > (int64_t(1) << 20)) return NEUMANN_EINVAL;
   if (dtype < NEUMANN_FP64 || dtype > NEUMANN_SPLIT_FP16) return NEUMANN_EINVAL;
-  if (dtype == NEUMANN_SPLIT_FP16) return NEUMANN_ENOTSUP;
   p->n = n;
   p->k = k;
   p->radix = radix;
@@ -684,9 +683,14 @@ EpiOut resolve_out(const neumann_plan_s* p, const OutSpec& s, const EpiIn* ins, 
     o.in_f[i] = (float)s.in[i];
   }
   auto dst = [&](void* ptr, int64_t ld, int dt, int mode) { o.dst[o.ndst++] = EpiDst{ptr, ld, dt, mode}; };
+  const int fp16 = p->dtype == NEUMANN_SPLIT_FP16;
   auto split = [&](size_t hi, size_t lo, int tr) {
-    o.split[o.nsplit++] = EpiSplit{p->ws + hi, p->ws + lo, p->npad, tr};
+    o.split[o.nsplit++] = EpiSplit{p->ws + hi, p->ws + lo, p->npad, tr, fp16};
   };
+  if (fp16) {  // both operands of a tensor-core product carry 2^8
+    o.acc_d = s.acc / (double)(kFp16SplitScale * kFp16SplitScale);
+    o.acc_f = (float)o.acc_d;
+  }
   if (s.slot == SL_USER_S) {
     if (p->grouped)
       dst(const_cast<void*>(p->cur_stab), 0, p->dt_io, EPI_TABLE);
@@ -736,7 +740,7 @@ bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMap
     const SlotBufs& a = p->bufs[op.a];
     const SlotBufs& b = p->bufs[op.b];
     if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + b.b_hi, p->ws + b.b_lo, p->npad,
-                      p->npad, p->grouped ? p->chunk : 0))
+                      p->npad, p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16))
       return false;
   }
   return true;

@@ -37,10 +37,16 @@ def test_invalid_arguments(n, k, radix, dtype, flags):
     assert e.value.code == C.EINVAL
 
 
-def test_fp16_not_supported_yet():
-    with pytest.raises(C.NeumannError) as e:
-        C.neumann_plan_create(64, 81, 9, C.SPLIT_FP16, 0)
-    assert e.value.code == C.ENOTSUP
+def test_fp16_plan_has_the_split_layout():
+    h = C.neumann_plan_create(64, 81, 9, C.SPLIT_FP16, 0)
+    hb = C.neumann_plan_create(64, 81, 9, C.SPLIT_BF16, 0)
+    try:
+        a, b = C.neumann_plan_info(h), C.neumann_plan_info(hb)
+        assert a["workspace_bytes"] == b["workspace_bytes"]
+        assert a["products_executed"] == b["products_executed"] == 8
+    finally:
+        C.neumann_plan_destroy(h)
+        C.neumann_plan_destroy(hb)
 
 
 def _info(n, k, radix, dtype=C.FP64, flags=0):

@@ -7,6 +7,11 @@ scheme: S_k for exact schemes, Lemma 5.7's closed form for radix 15):
   split-BF16  TOL_BF16[rho]; each operand is kept to ~2^-17 relative, so a
               product carries ~1e-5 relative error, amplified by ||S|| <= 1/(1-rho)
               across levels.
+  split-FP16  TOL_FP16[rho]; operands kept to ~2^-22 relative (x 2^8 scaling keeps
+              lo normal for |x| >= 2^-11), the same amplification. A product's
+              FP32 accumulation on the tensor cores adds ~sqrt(n) 2^-24 relative
+              (2e-6 at n = 513, 5e-6 at n = 8192), which at n = 8192 matches the
+              BF16 operand error: there both splits end near 1e-3 (rho = 0.97).
 """
 
 import numpy as np
@@ -21,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 TOL_BF16 = {0.5: 2e-4, 0.9: 1e-3, 0.97: 3e-3}
+TOL_FP16 = {0.5: 1e-5, 0.9: 5e-5, 0.97: 3e-3}
 
 
 def _nm():
@@ -30,7 +36,9 @@ def _nm():
 
 
 def _tol(dtype, rho):
-    return TOL[dtype] if dtype in TOL else TOL_BF16[rho]
+    if dtype in TOL:
+        return TOL[dtype]
+    return TOL_FP16[rho] if dtype == "split_fp16" else TOL_BF16[rho]
 
 
 def _run(A_np, k, radix, dtype, flags=0):
@@ -46,7 +54,7 @@ def _run(A_np, k, radix, dtype, flags=0):
 
 # ---------------------------------------------------------------- products
 
-@pytest.mark.parametrize("dtype,tol", [("fp64", 1e-14), ("fp32", 2e-6), ("split_bf16", 2e-5)])
+@pytest.mark.parametrize("dtype,tol", [("fp64", 1e-14), ("fp32", 2e-6), ("split_bf16", 2e-5), ("split_fp16", 5e-6)])
 @pytest.mark.parametrize("n", [1, 17, 200, 256, 300, 513])
 def test_matmul_against_fp64_reference(dtype, tol, n):
     """C = A B of each arithmetic against an FP64 product (torch on the CPU)."""
@@ -69,7 +77,7 @@ SCHEMES = [(1, 81, 0), (2, 64, 0), (2, 81, 1), (3, 27, 0), (5, 125, 0), (9, 81, 
            (15, 225, 0), (15, 3375, 0), (0, 360, 0)]
 
 
-@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16", "split_fp16"])
 @pytest.mark.parametrize("radix,k,exact", SCHEMES)
 @pytest.mark.parametrize("n", [200, 300])
 def test_scheme_parity_planted(dtype, radix, k, exact, n):
@@ -82,7 +90,7 @@ def test_scheme_parity_planted(dtype, radix, k, exact, n):
     assert CF.rel_fro(S, ref) < _tol(dtype, rho)
 
 
-@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16", "split_fp16"])
 @pytest.mark.parametrize("radix,k,exact", [(1, 81, 0), (2, 128, 0), (2, 81, 1), (9, 81, 0), (15, 225, 0)])
 def test_scheme_parity_nonsymmetric(dtype, radix, k, exact):
     """Nonsymmetric Gaussian input (||A||_2 = 0.5) against the oracle's matrix schemes."""
@@ -96,7 +104,7 @@ def test_scheme_parity_nonsymmetric(dtype, radix, k, exact):
 
 @pytest.mark.parametrize("n,k,radix", [(1, 81, 9), (1, 5, 1), (17, 1, 9), (17, 2, 1), (17, 2, 2), (17, 9, 9),
                                        (33, 15, 15), (5, 7, 2)])
-@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16", "split_fp16"])
 def test_edge_cases(n, k, radix, dtype):
     nm = _nm()
     g = G.gaussian_scaled(n, 0.5, 11)
@@ -143,6 +151,19 @@ def test_nonfinite_status_for_divergent_input():
         assert st & nm.STATUS_NONFINITE
 
 
+def test_fp16_split_overflow_is_reported():
+    """A nilpotent A (rho = 0) with an entry of 300 is outside the scaled FP16
+    range (|x| < 255): its split is flagged NONFINITE instead of silently
+    returning a wrong result; the BF16 split (FP32 exponent range) is exact here."""
+    nm = _nm()
+    A = np.zeros((16, 16))
+    A[0, 1] = 300.0
+    S, st, _ = _run(A, 81, 9, "split_fp16")
+    assert st & nm.STATUS_NONFINITE
+    S, st, _ = _run(A, 81, 9, "split_bf16")
+    assert st == 0 and CF.rel_fro(S, np.eye(16) + A) < 1e-12
+
+
 def test_timing_flag_reports_every_product():
     nm = _nm()
     pl = G.planted_symmetric(512, 0.9, 9)
@@ -151,7 +172,7 @@ def test_timing_flag_reports_every_product():
     assert len(t) == p.info["products_executed"] == 10 and all(x > 0 for x in t)
 
 
-BATCH_TOL = {"fp64": 1e-12, "fp32": 1e-5, "split_bf16": 2e-3}
+BATCH_TOL = {"fp64": 1e-12, "fp32": 1e-5, "split_bf16": 2e-3, "split_fp16": 5e-5}
 
 
 def _batch_check(bp, mats, k, radix, dtype):
@@ -166,7 +187,7 @@ def _batch_check(bp, mats, k, radix, dtype):
         assert err < BATCH_TOL[dtype], (m["n"], err)
 
 
-@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16"])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32", "split_bf16", "split_fp16"])
 @pytest.mark.parametrize("k,radix", [(81, 9), (225, 15), (64, 2), (81, 1)])
 def test_batched_grouped_matches_oracle(dtype, k, radix):
     """Grouped launches over damped-Jacobi matrices of mixed order (cfg-4 construction)."""
@@ -236,12 +257,13 @@ def test_cfg2_full(dtype, radix, k):
     assert st == 0 and CF.rel_fro(S, ref) < TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", ["split_bf16", "split_fp16"])
 @pytest.mark.parametrize("radix,k", [(15, 3375), (9, 6561)])
-def test_cfg3_full_split_bf16(radix, k):
+def test_cfg3_full_split(radix, k, dtype):
     pl = G.config_inputs(3)
     ref = EV.planted_reference(pl["V"], pl["lam"], k, radix)
-    S, st, _ = _run(pl["A"], k, radix, "split_bf16")
+    S, st, _ = _run(pl["A"], k, radix, dtype)
     assert st == 0
     err = CF.rel_fro(S, ref)
-    print(f"cfg3 radix {radix} k {k} split-bf16 rel err {err:.3e}")
-    assert err < TOL_BF16[0.97]
+    print(f"cfg3 radix {radix} k {k} {dtype} rel err {err:.3e}")
+    assert err < _tol(dtype, 0.97)
