@@ -37,6 +37,10 @@ WORKLOADS = {
     "precision-r9-bf16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_bf16", sq_k=8192),
     "precision-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096),
     "precision-r9-fp16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_fp16", sq_k=8192),
+    # cfg 5: n = 16384, planted spectrum U[-0.95, 0.95] + rank-32 nonsymmetric term of norm 0.01;
+    # the FP64 comparison (about two minutes at this size) runs only with --fp64-large
+    "large-r15-fp16-n16384-k3375": dict(cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
+                                        fp64=False),
     "plain-r9-fp32-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
     "plain-r15-fp32-n4096-k225": dict(cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
     "plain-r9-fp64-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
@@ -485,7 +489,7 @@ def run_ours(args, wl):
     # 1/64 of the FP32 rate, so this takes seconds), and the split result's
     # relative Frobenius distance from it
     fp64 = None
-    if wl["dtype"] != "fp64" and not args.no_fp64:
+    if wl["dtype"] != "fp64" and not args.no_fp64 and (wl.get("fp64", True) or args.fp64_large):
         p64 = nm.Plan(n, k, wl["radix"], "fp64")
         A64 = A.double() if A.dtype != torch.float64 else A
         S64 = torch.empty_like(A64)
@@ -593,6 +597,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison evaluation")
+    ap.add_argument("--fp64-large", action="store_true", help="run the FP64 comparison on the n = 16384 workload")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

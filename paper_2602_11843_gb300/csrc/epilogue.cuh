@@ -65,8 +65,10 @@ __device__ __forceinline__ T* dst_base(const EpiDst& ds, const EpiCtx& x, int64_
 }
 
 // The 16-bit hi/lo pair of v as raw bits (BF16, or scaled FP16; see EpiSplit).
-__device__ __forceinline__ void split_bits(float v, int fp16, unsigned short* hi, unsigned short* lo) {
-  if (fp16) {
+// kF16 is a compile-time choice: a kernel instance serves one split type.
+template <bool kF16>
+__device__ __forceinline__ void split_bits(float v, unsigned short* hi, unsigned short* lo) {
+  if (kF16) {
     const float w = v * kFp16SplitScale;
     const __half h = __float2half_rn(w);
     *hi = __half_as_ushort(h);
@@ -79,13 +81,15 @@ __device__ __forceinline__ void split_bits(float v, int fp16, unsigned short* hi
 }
 
 // An FP16 hi that overflowed (|v| * 2^8 beyond the FP16 range) is non-finite.
-__device__ __forceinline__ bool split_bad(float v, int fp16) {
-  return fp16 && !isfinite(__half2float(__float2half_rn(v * kFp16SplitScale)));
+template <bool kF16>
+__device__ __forceinline__ bool split_bad(float v) {
+  return kF16 && !(fabsf(v) * kFp16SplitScale < 65504.f);
 }
 
+template <bool kF16>
 __device__ __forceinline__ void split_store(const EpiSplit& s, const EpiCtx& x, int r, int c, float v) {
   unsigned short hi, lo;
-  split_bits(v, s.fp16, &hi, &lo);
+  split_bits<kF16>(v, &hi, &lo);
   int64_t off = x.off + (s.transposed ? (int64_t)c * s.ld + r : (int64_t)r * s.ld + c);
   reinterpret_cast<unsigned short*>(s.hi)[off] = hi;
   reinterpret_cast<unsigned short*>(s.lo)[off] = lo;
@@ -124,7 +128,7 @@ __device__ __forceinline__ void epi_padding(const EpiParams& P, const EpiCtx& x,
 // kDeferT: outputs' transposed split stores are not written; the value they
 // would split (RN_fp32 of the output) is left in tv[j] for the caller to write
 // through a shared-memory transpose (0 in the padding).
-template <typename AccT, bool kDeferT>
+template <typename AccT, bool kDeferT, bool kF16>
 __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCtx& x, int r, int c, AccT acc,
                                                  float* tv) {
   bool bad = false;
@@ -197,11 +201,11 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
     }
     // hi/lo pairs are formed from RN_fp32 of the output: FP32 keeps 24 bits, the pair 16
     for (int s = 0; s < o.nsplit; ++s) {
-      bad |= split_bad(vf, o.split[s].fp16);
+      bad |= split_bad<kF16>(vf);
       if (kDeferT && o.split[s].transposed)
         tv[j] = vf;
       else
-        split_store(o.split[s], x, r, c, vf);
+        split_store<kF16>(o.split[s], x, r, c, vf);
     }
   }
   return bad;
@@ -209,9 +213,9 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
 
 // One copy serves every call site of the GEMM kernels; P is a __grid_constant__
 // kernel parameter, so passing it by reference copies nothing.
-template <typename AccT>
+template <typename AccT, bool kF16>
 __device__ __noinline__ bool epi_element(const EpiParams& P, EpiCtx x, int r, int c, AccT acc) {
-  return epi_element_impl<AccT, false>(P, x, r, c, acc, nullptr);
+  return epi_element_impl<AccT, false, kF16>(P, x, r, c, acc, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +245,7 @@ __device__ __forceinline__ void ld_vec(const double* p, double (&v)[W]) {
 }
 
 // kWsOnly: write workspace destinations only (padding zeros never go to the caller).
-template <int W, typename V, bool kWsOnly = false>
+template <int W, typename V, bool kF16, bool kWsOnly = false>
 __device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, int c0, const V (&v)[W]) {
   for (int d = 0; d < o.ndst; ++d) {
     const EpiDst& ds = o.dst[d];
@@ -272,7 +276,7 @@ __device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, 
     const EpiSplit& sp = o.split[s];
     unsigned short hi[W], lo[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) split_bits((float)v[w], sp.fp16, &hi[w], &lo[w]);  // from RN_fp32(v)
+    for (int w = 0; w < W; ++w) split_bits<kF16>((float)v[w], &hi[w], &lo[w]);  // from RN_fp32(v)
     if (sp.transposed) {
 #pragma unroll
       for (int w = 0; w < W; ++w) {
@@ -304,38 +308,36 @@ __device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, 
 
 // Zeros for W consecutive padding elements of row r (r >= n) in every workspace
 // destination.
-template <int W>
+template <int W, bool kF16>
 __device__ __forceinline__ void epi_row_zero(const EpiParams& P, const EpiCtx& x, int r, int c0) {
   float z[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) z[w] = 0.f;
 #pragma unroll 1
-  for (int j = 0; j < P.nout; ++j) st_row<W, float, true>(P.out[j], x, r, c0, z);
+  for (int j = 0; j < P.nout; ++j) st_row<W, float, kF16, true>(P.out[j], x, r, c0, z);
 }
 
 // A scaled FP16 split of any of these values overflows.
-template <int W, typename V>
+template <int W, typename V, bool kF16>
 __device__ __forceinline__ bool fp16_overflow(const EpiOut& o, const V (&v)[W]) {
-  bool any = false;
-  for (int s = 0; s < o.nsplit; ++s) any |= o.split[s].fp16 != 0;
-  if (!any) return false;
+  if (!kF16 || o.nsplit == 0) return false;
   bool bad = false;
 #pragma unroll
   for (int w = 0; w < W; ++w) bad |= !(fabsf((float)v[w]) * kFp16SplitScale < 65504.f);
   return bad;
 }
 
-template <int W, typename AccT>
+template <int W, typename AccT, bool kF16>
 __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int r, int c0,
                                         const AccT (&acc)[W]) {
   if (r >= x.n) {
-    epi_row_zero<W>(P, x, r, c0);
+    epi_row_zero<W, kF16>(P, x, r, c0);
     return false;
   }
   if (c0 + W > x.n) {
     bool bad = false;
 #pragma unroll
-    for (int w = 0; w < W; ++w) bad |= epi_element<AccT>(P, x, r, c0 + w, acc[w]);
+    for (int w = 0; w < W; ++w) bad |= epi_element<AccT, kF16>(P, x, r, c0 + w, acc[w]);
     return bad;
   }
   float fin[kMaxIn][W];
@@ -392,8 +394,8 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, double>(o, v);
-      st_row<W, double>(o, x, r, c0, v);
+      bad |= fp16_overflow<W, double, kF16>(o, v);
+      st_row<W, double, kF16>(o, x, r, c0, v);
     } else {
       float v[W];
 #pragma unroll
@@ -408,8 +410,8 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, float>(o, v);
-      st_row<W, float>(o, x, r, c0, v);
+      bad |= fp16_overflow<W, float, kF16>(o, v);
+      st_row<W, float, kF16>(o, x, r, c0, v);
     }
   }
   return bad;
@@ -421,11 +423,11 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
 // buffer one cache line per instruction; a transposed hi/lo store is one
 // W x 2-byte run per lane. Requires W == 8 (16-byte transposed runs).
 
-template <int W>
+template <int W, bool kF16>
 __device__ __forceinline__ void st_col_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[W]) {
   unsigned short hi[W], lo[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) split_bits(v[w], sp.fp16, &hi[w], &lo[w]);
+  for (int w = 0; w < W; ++w) split_bits<kF16>(v[w], &hi[w], &lo[w]);
   if (sp.transposed) {
     uint32_t ph[W / 2], pl[W / 2];
 #pragma unroll
@@ -447,7 +449,7 @@ __device__ __forceinline__ void st_col_split(const EpiSplit& sp, const EpiCtx& x
 }
 
 // kWsOnly: padding, workspace destinations only
-template <int W, typename V, bool kWsOnly = false>
+template <int W, typename V, bool kF16, bool kWsOnly = false>
 __device__ __forceinline__ void st_col(const EpiOut& o, const EpiCtx& x, int r0, int c, const V (&v)[W]) {
   for (int d = 0; d < o.ndst; ++d) {
     const EpiDst& ds = o.dst[d];
@@ -467,11 +469,11 @@ __device__ __forceinline__ void st_col(const EpiOut& o, const EpiCtx& x, int r0,
     float vf[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) vf[w] = (float)v[w];  // pairs from RN_fp32 of the output
-    for (int s = 0; s < o.nsplit; ++s) st_col_split<W>(o.split[s], x, r0, c, vf);
+    for (int s = 0; s < o.nsplit; ++s) st_col_split<W, kF16>(o.split[s], x, r0, c, vf);
   }
 }
 
-template <int W, typename AccT>
+template <int W, typename AccT, bool kF16>
 __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int r0, int c, const AccT (&acc)[W]) {
   static_assert(W == 8, "transposed runs are 16 bytes");
   static_assert(sizeof(AccT) == 4, "FP32 accumulators (tensor-core products)");
@@ -480,13 +482,13 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
 #pragma unroll
     for (int w = 0; w < W; ++w) z[w] = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < P.nout; ++j) st_col<W, float, true>(P.out[j], x, r0, c, z);
+    for (int j = 0; j < P.nout; ++j) st_col<W, float, kF16, true>(P.out[j], x, r0, c, z);
     return false;
   }
   if (r0 + W > x.n) {  // ragged edge
     bool bad = false;
 #pragma unroll
-    for (int w = 0; w < W; ++w) bad |= epi_element<AccT>(P, x, r0 + w, c, acc[w]);
+    for (int w = 0; w < W; ++w) bad |= epi_element<AccT, kF16>(P, x, r0 + w, c, acc[w]);
     return bad;
   }
   float fin[kMaxIn][W];
@@ -533,8 +535,8 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, double>(o, v);
-      st_col<W, double>(o, x, r0, c, v);
+      bad |= fp16_overflow<W, double, kF16>(o, v);
+      st_col<W, double, kF16>(o, x, r0, c, v);
     } else {
       float v[W];
 #pragma unroll
@@ -549,8 +551,8 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, float>(o, v);
-      st_col<W, float>(o, x, r0, c, v);
+      bad |= fp16_overflow<W, float, kF16>(o, v);
+      st_col<W, float, kF16>(o, x, r0, c, v);
     }
   }
   return bad;

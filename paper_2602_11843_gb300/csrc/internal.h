@@ -51,7 +51,6 @@ struct EpiSplit {
   void* lo;
   int64_t ld;
   int transposed;
-  int fp16;
 };
 
 constexpr float kFp16SplitScale = 256.0f;  // 2^8
@@ -78,6 +77,7 @@ struct EpiParams {
   int nout;
   EpiOut out[kMaxOut];
   unsigned* status;  // device word, NEUMANN_STATUS_* bits are OR-ed in
+  int fp16;          // split stores use the scaled FP16 pair (the kernel instance is chosen on the host)
   // Batched (grouped) launches: matrix m has order mat_n[m] and occupies
   // elements [m * mat_stride, (m + 1) * mat_stride) of every workspace buffer.
   // nullptr for a single evaluation (order n, offset 0).

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
       const int c0 = n0 + h * 64 + tx * 4;
       if (r >= lim || c0 >= lim) continue;
       const T(&a4)[4] = *reinterpret_cast<const T(*)[4]>(&acc[i][4 * h]);
-      bad |= epi_row<4, T>(P, x, r, c0, a4);
+      bad |= epi_row<4, T, false>(P, x, r, c0, a4);
     }
   }
   epi_flag(P, bad);
@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
 // Row-major stores are coalesced along the warp; transposed hi/lo stores go
 // through a shared-memory tile so that they are coalesced too.
 // tiles != nullptr (grouped launch): CTA b handles tiles[b] = {matrix, tile row, tile column}.
+template <bool kF16>
 __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ tiles,
                                                      const __grid_constant__ EpiParams P) {
   __shared__ float tile[kMaxOut][32][33];
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float tv[kMaxOut];
-    bad |= epi_element_impl<float, true>(P, x, r0 + ty + 8 * q, c0 + tx, 0.f, tv);
+    bad |= epi_element_impl<float, true, kF16>(P, x, r0 + ty + 8 * q, c0 + tx, 0.f, tv);
 #pragma unroll
     for (int j = 0; j < kMaxOut; ++j) tile[j][ty + 8 * q][tx] = tv[j];
   }
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
         // lane tx writes element (r0 + tx, c0 + ty + 8q) at row c, column r of the stored transpose
         const float v = tile[j][tx][ty + 8 * q];
         unsigned short hi, lo;
-        split_bits(v, sp.fp16, &hi, &lo);
+        split_bits<kF16>(v, &hi, &lo);
         const int64_t off = x.off + (int64_t)(c0 + ty + 8 * q) * sp.ld + (r0 + tx);
         reinterpret_cast<unsigned short*>(sp.hi)[off] = hi;
         reinterpret_cast<unsigned short*>(sp.lo)[off] = lo;
@@ -218,14 +219,18 @@ cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int
 }
 
 cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles) {
+  dim3 grid;
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
-    ewise_kernel<<<ntiles, dim3(32, 8), 0, s>>>(tiles, P);
-    return cudaGetLastError();
+    grid = dim3((unsigned)ntiles);
+  } else {
+    if (P.npad <= 0 || P.npad % 32 != 0) return P.npad <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+    grid = dim3((unsigned)(P.npad / 32), (unsigned)(P.npad / 32));
   }
-  if (P.npad <= 0 || P.npad % 32 != 0) return P.npad <= 0 ? cudaSuccess : cudaErrorInvalidValue;
-  dim3 grid((unsigned)(P.npad / 32), (unsigned)(P.npad / 32));
-  ewise_kernel<<<grid, dim3(32, 8), 0, s>>>(nullptr, P);
+  if (P.fp16)
+    ewise_kernel<true><<<grid, dim3(32, 8), 0, s>>>(tiles, P);
+  else
+    ewise_kernel<false><<<grid, dim3(32, 8), 0, s>>>(tiles, P);
   return cudaGetLastError();
 }
 

@@ -140,7 +140,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 }
 
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+                                         uint32_t accumulate) {  // idesc: kIdescBf16 or kIdescF16
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
@@ -219,12 +219,13 @@ __device__ __forceinline__ void load_stage(uint32_t st, const CUtensorMap* ahi, 
   }
 }
 
-template <bool kGrouped>
+template <bool kGrouped, bool kF16>
 __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
                          int ktiles, int tiles_m, int tiles_n, const int4* __restrict__ tiles, int ntiles_grouped,
-                         uint32_t idesc, const __grid_constant__ EpiParams P) {
+                         const __grid_constant__ EpiParams P) {
+  constexpr uint32_t idesc = kF16 ? kIdescF16 : kIdescBf16;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
           float a8[8];
 #pragma unroll
           for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
-          bad |= epi_col<8, float>(P, x, r0, c, a8);
+          bad |= epi_col<8, float, kF16>(P, x, r0, c, a8);
         }
         __syncwarp();
       }
@@ -459,11 +460,14 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)EpiShape<false>::kSmem);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(tc_split_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)EpiShape<true>::kSmem);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e[4] = {
+        cudaFuncSetAttribute(tc_split_gemm_kernel<false, false>, a, (int)EpiShape<false>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<false, true>, a, (int)EpiShape<false>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<true, false>, a, (int)EpiShape<true>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<true, true>, a, (int)EpiShape<true>::kSmem)};
+    for (cudaError_t x : e)
+      if (x != cudaSuccess) attr_err = x;
   });
   if (attr_err != cudaSuccess) return attr_err;
   static int sms = 0;
@@ -475,15 +479,16 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
     const int grid = ntiles < sms ? ntiles : sms;
-    tc_split_gemm_kernel<true><<<grid, EpiShape<true>::kThreads, EpiShape<true>::kSmem, s>>>(
-        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, tiles, ntiles, maps.fp16 ? kIdescF16 : kIdescBf16, P);
+    auto k = maps.fp16 ? tc_split_gemm_kernel<true, true> : tc_split_gemm_kernel<true, false>;
+    k<<<grid, EpiShape<true>::kThreads, EpiShape<true>::kSmem, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0,
+                                                                     0, tiles, ntiles, P);
     return cudaGetLastError();
   }
   const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
-  tc_split_gemm_kernel<false><<<grid, EpiShape<false>::kThreads, EpiShape<false>::kSmem, s>>>(
-      maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, nullptr, 0,
-      maps.fp16 ? kIdescF16 : kIdescBf16, P);
+  auto k = maps.fp16 ? tc_split_gemm_kernel<false, true> : tc_split_gemm_kernel<false, false>;
+  k<<<grid, EpiShape<false>::kThreads, EpiShape<false>::kSmem, s>>>(
+      maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, nullptr, 0, P);
   return cudaGetLastError();
 }
 

@@ -685,7 +685,7 @@ EpiOut resolve_out(const neumann_plan_s* p, const OutSpec& s, const EpiIn* ins, 
   auto dst = [&](void* ptr, int64_t ld, int dt, int mode) { o.dst[o.ndst++] = EpiDst{ptr, ld, dt, mode}; };
   const int fp16 = p->dtype == NEUMANN_SPLIT_FP16;
   auto split = [&](size_t hi, size_t lo, int tr) {
-    o.split[o.nsplit++] = EpiSplit{p->ws + hi, p->ws + lo, p->npad, tr, fp16};
+    o.split[o.nsplit++] = EpiSplit{p->ws + hi, p->ws + lo, p->npad, tr};
   };
   if (fp16) {  // both operands of a tensor-core product carry 2^8
     o.acc_d = s.acc / (double)(kFp16SplitScale * kFp16SplitScale);
@@ -722,6 +722,7 @@ void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiPa
   P->n = (int)p->n;
   P->npad = (int)p->npad;
   P->status = reinterpret_cast<unsigned*>(p->ws);
+  P->fp16 = p->dtype == NEUMANN_SPLIT_FP16;
   if (p->grouped) {
     P->mat_n = p->cur_matn;
     P->mat_stride = (int64_t)p->slab;
