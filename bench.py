@@ -53,10 +53,11 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 
-# DRAM bytes per launch of the tensor-core product at n = 8192 from one ncu
-# capture (profiles/tc_split_gemm_n8192.md), valid for the kernel source whose
-# SHA-1 prefix is recorded beside it; None when no capture matches the source.
-TC_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) per launch of the tensor-core product, the mean over
+# the 16 launches of one n = 8192 radix-15 evaluation, from one ncu capture
+# (profiles/tc_split_gemm_n8192_r15_bench.md). Valid for the kernel sources
+# whose SHA-1 prefix is recorded beside it; reported as null otherwise.
+TC_TRAFFIC = {"sha1": "fad6849a14e8", "bytes_per_launch": 4.3136e9}
 
 
 def _peaks():
@@ -68,10 +69,12 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def _src_sha(name):
-    p = os.path.join(ROOT, "paper_2602_11843_gb300", "csrc", name)
-    with open(p, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+def _src_sha(*names):
+    h = hashlib.sha1()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2602_11843_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def reduce_max_ms(ms, world, device=None):
@@ -531,7 +534,7 @@ def run_ours(args, wl):
     if tc:
         flops = 3 * 2.0 * n ** 3  # three BF16 products per split product
         peak = peaks["bf16_tflops_sustained"]
-        sha = _src_sha("kernels_tc.cu")
+        sha = _src_sha("kernels_tc.cu", "epilogue.cuh")
         traffic = TC_TRAFFIC["bytes_per_launch"] if TC_TRAFFIC["sha1"] == sha and n == 8192 else None
         roof = {"bound": "tensor", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": None, "traffic": traffic,
