@@ -172,6 +172,14 @@ int neumann_last_status(neumann_plan_t plan, unsigned* status);
  * Errors: NEUMANN_EINVAL (no timing flag), NEUMANN_ECUDA. */
 int neumann_plan_timing(neumann_plan_t plan, float* ms, int cap, int* count);
 
+/* Self-test of device failure reporting: launches one thread that waits, with
+ * the same bounded-wait code the tensor-core product uses, on an mbarrier that
+ * nothing arrives on, for limit_ns nanoseconds (at most 1e9), and then sets
+ * NEUMANN_STATUS_TIMEOUT in the plan's status word (read with neumann_last_status).
+ * No kernel faults or hangs: the wait ends by itself and the context stays usable.
+ * Stream-ordered. Errors: NEUMANN_EINVAL, NEUMANN_ENOMEM, NEUMANN_ECUDA. */
+int neumann_plan_selftest_timeout(neumann_plan_t plan, uint64_t limit_ns, void* stream);
+
 /* The 28 radix-15 circuit parameters the library uses (Sec. 4.1, App. B), in
  * the order l2[3], r2[3], l3[4], r3[4], l4[5], r4[5], gamma[4]; set 0 = refined
  * on the host by minimum-norm Gauss-Newton from the printed values, 1 = as printed.

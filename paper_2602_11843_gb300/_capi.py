@@ -67,6 +67,7 @@ def _load():
         "neumann_plan_timing": (c_int, [P, POINTER(c_float), c_int, POINTER(c_int)]),
         "neumann_radix15_coefficients": (c_int, [c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double),
                                                  POINTER(c_double)]),
+        "neumann_plan_selftest_timeout": (c_int, [P, ctypes.c_uint64, c_void_p]),
         "neumann_matmul_noalloc": (c_int, [c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                            c_void_p]),
         "neumann_plan_destroy": (None, [P]),
@@ -146,6 +147,10 @@ def neumann_plan_timing(plan: int, cap: int = 4096) -> list:
     cnt = c_int(0)
     _check(_lib.neumann_plan_timing(plan, buf, cap, byref(cnt)), "neumann_plan_timing")
     return [buf[i] for i in range(min(cnt.value, cap))]
+
+
+def neumann_plan_selftest_timeout(plan: int, limit_ns: int, stream: int = 0) -> None:
+    _check(_lib.neumann_plan_selftest_timeout(plan, limit_ns, stream), "neumann_plan_selftest_timeout")
 
 
 def neumann_radix15_coefficients(coef_set: int = 0):

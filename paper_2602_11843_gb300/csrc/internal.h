@@ -116,6 +116,10 @@ bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, i
 cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,
                            const int4* tiles = nullptr, int ntiles = 0);
 
+// One thread waits (bounded by limit_ns) on an mbarrier nothing arrives on and
+// sets NEUMANN_STATUS_TIMEOUT in *status when the limit passes.
+cudaError_t launch_wait_probe(unsigned* status, uint64_t limit_ns, cudaStream_t s);
+
 // ---- radix-15 coefficients (radix15.cpp) ----
 // set 0: refined, 1: printed. Returns false if the refinement did not converge.
 bool radix15_coefficients(int set, double coef[28], double* prefix_err, double* s15, double* s16);

@@ -93,13 +93,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete; false once
+// `limit_ns` has passed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (gtimer() - t0 > kTimeoutNs) return false;
+    if (gtimer() - t0 > limit_ns) return false;
   }
 }
 
@@ -411,6 +412,17 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
   }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives on, with the product kernel's wait code and a caller-given limit, and
+// reports the expiry through the status word exactly as the product does.
+__global__ void wait_probe_kernel(unsigned* status, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(b, 0, limit_ns)) atomicOr(status, 2u);
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -452,6 +464,11 @@ bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, i
   m->fp16 = fp16;
   return make_map(&m->a_hi, a_hi, npad, ld, BM, count, fp16) && make_map(&m->a_lo, a_lo, npad, ld, BM, count, fp16) &&
          make_map(&m->b_hi, bt_hi, npad, ld, BN, count, fp16) && make_map(&m->b_lo, bt_lo, npad, ld, BN, count, fp16);
+}
+
+cudaError_t launch_wait_probe(unsigned* status, uint64_t limit_ns, cudaStream_t s) {
+  wait_probe_kernel<<<1, 1, 0, s>>>(status, limit_ns);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,

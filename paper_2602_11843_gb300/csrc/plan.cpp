@@ -1139,6 +1139,16 @@ int neumann_plan_timing(neumann_plan_t p, float* ms, int cap, int* count) {
   return NEUMANN_OK;
 }
 
+int neumann_plan_selftest_timeout(neumann_plan_t p, uint64_t limit_ns, void* stream) {
+  if (!p || limit_ns > 1000000000ull) return NEUMANN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = ensure_workspace(p, s);
+  if (rc) return rc;
+  p->last_stream = s;
+  return launch_wait_probe(reinterpret_cast<unsigned*>(p->ws), limit_ns, s) == cudaSuccess ? NEUMANN_OK
+                                                                                           : NEUMANN_ECUDA;
+}
+
 int neumann_radix15_coefficients(int set, double* coef28, double* prefix_error, double* spill15, double* spill16) {
   if ((set != 0 && set != 1) || !coef28) return NEUMANN_EINVAL;
   double e = 0, a = 0, b = 0;
