@@ -83,6 +83,8 @@ typedef enum {
 #define NEUMANN_FLAG_PRINTED_COEFFS 0x4u  /* radix 15: the three-decimal coefficients printed in App. B */
 #define NEUMANN_FLAG_TIMING 0x8u          /* record CUDA events around every product (neumann_plan_timing) */
 #define NEUMANN_FLAG_IO_FP32 0x10u        /* split dtypes: A and S are float instead of double */
+#define NEUMANN_FLAG_SINGLE_CTA 0x20u     /* split dtypes: keep every product on single-CTA 128 x 256 tiles
+                                             (by default padded orders >= 4096 use 2-CTA 256 x 256 tiles) */
 
 #define NEUMANN_MAX_LEVELS 64
 

@@ -31,6 +31,7 @@ FLAG_RESIDUAL_PAPER = 0x2
 FLAG_PRINTED_COEFFS = 0x4
 FLAG_TIMING = 0x8
 FLAG_IO_FP32 = 0x10
+FLAG_SINGLE_CTA = 0x20
 
 MAX_LEVELS = 64
 

@@ -558,6 +558,211 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
   return bad;
 }
 
+// ---------------------------------------------------------------------------
+// Chunk form for the tensor-core products: rows rbase .. rbase+31 of column c,
+// the accumulator of row rbase + i at stg[i * 33 + lane] (the warp's staged
+// 32 x 32 chunk). Interior chunks of ops the host marked `fast` (at most one
+// FP64 input, index f64_in) take a lean path: input addresses are formed once
+// per 8 rows, the identity term is applied only to the diagonal element,
+// non-finite results (and FP16 split overflow) are detected once per chunk,
+// and hi/lo pairs come from paired RN conversions (cvt.rn.bf16x2 / f16x2,
+// the same bits as two scalar conversions). Everything else (padding, ragged
+// edges, grouped row limits) goes through epi_col row group by row group.
+
+// hi/lo of (a, b) as packed pairs: low half from a, high half from b.
+template <bool kF16>
+__device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
+  if (kF16) {
+    const float wa = a * kFp16SplitScale, wb = b * kFp16SplitScale;
+    const __half2 h = __floats2half2_rn(wa, wb);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(wa - hf.x, wb - hf.y);
+    *hi = *reinterpret_cast<const uint32_t*>(&h);
+    *lo = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    *hi = *reinterpret_cast<const uint32_t*>(&h);
+    *lo = *reinterpret_cast<const uint32_t*>(&l);
+  }
+}
+
+// Split stores of 8 consecutive rows r0 .. r0+7 of column c.
+template <bool kF16>
+__device__ __forceinline__ void st8_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[8]) {
+  uint32_t ph[4], pl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], &ph[q], &pl[q]);
+  unsigned short* hi = reinterpret_cast<unsigned short*>(sp.hi) + x.off;
+  unsigned short* lo = reinterpret_cast<unsigned short*>(sp.lo) + x.off;
+  if (sp.transposed) {  // row c of the stored transpose, 8 consecutive entries: one 16-byte store each
+    const int64_t off = (int64_t)c * sp.ld + r0;
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+  } else {  // row-major: the warp's lanes write 32 consecutive entries of each row
+    const int64_t ld = sp.ld;
+    hi += (int64_t)r0 * ld + c;
+    lo += (int64_t)r0 * ld + c;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      hi[(2 * q) * ld] = (unsigned short)(ph[q] & 0xffffu);
+      hi[(2 * q + 1) * ld] = (unsigned short)(ph[q] >> 16);
+      lo[(2 * q) * ld] = (unsigned short)(pl[q] & 0xffffu);
+      lo[(2 * q + 1) * ld] = (unsigned short)(pl[q] >> 16);
+    }
+  }
+}
+
+template <bool kF16>
+__device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
+                                               int lane) {
+  const int fi = P.f64_in;  // the FP64 input, or -1
+  float chk = 0.f;          // becomes NaN once any output is non-finite
+  float amax = 0.f;         // largest |value| split to FP16
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    const int r0 = rbase + 8 * g;
+    const bool diag = (unsigned)(c - r0) < 8u;  // this lane's column holds the diagonal in these rows
+    float a8[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
+    float fin[kMaxIn][8];
+    double din[8];
+#pragma unroll
+    for (int i = 0; i < kMaxIn; ++i) {
+      if (i < P.nin && i != fi) {
+        int64_t ld;
+        const float* q = in_base<float>(P.in[i], x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) fin[i][w] = q[(int64_t)w * ld];
+      }
+    }
+    if (fi >= 0) {
+      int64_t ld;
+      const double* q = in_base<double>(P.in[fi], x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) din[w] = q[(int64_t)w * ld];
+    }
+#pragma unroll 1
+    for (int j = 0; j < P.nout; ++j) {
+      const EpiOut& o = P.out[j];
+      // the same terms in the same order as epi_col
+      float vf[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) vf[w] = o.acc_f * a8[w];
+      if (o.f64) {
+        // FP32 terms summed in FP32; the identity and the FP64 input (a partial
+        // sum Y or residual R) are added in FP64
+#pragma unroll
+        for (int i = 0; i < kMaxIn; ++i) {
+          if (i < P.nin && i != fi && o.in_f[i] != 0.f) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[i], fin[i][w], vf[w]);
+          }
+        }
+        double v[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v[w] = (double)vf[w];
+        if (diag) {
+#pragma unroll
+          for (int w = 0; w < 8; ++w)
+            if (r0 + w == c) v[w] += o.id_d;
+        }
+        if (fi >= 0 && o.in_d[fi] != 0.0) {
+#pragma unroll
+          for (int w = 0; w < 8; ++w) v[w] = fma(o.in_d[fi], din[w], v[w]);
+        }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) vf[w] = (float)v[w];
+        for (int d = 0; d < o.ndst; ++d) {
+          const EpiDst& ds = o.dst[d];
+          int64_t ld;
+          if (ds.dt == DT_F64) {
+            double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = v[w];
+          } else {
+            float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+          }
+        }
+      } else {
+        if (diag) {
+#pragma unroll
+          for (int w = 0; w < 8; ++w)
+            if (r0 + w == c) vf[w] += o.id_f;
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxIn; ++i) {
+          if (i < P.nin && o.in_f[i] != 0.f) {
+            if (i == fi) {
+#pragma unroll
+              for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[i], (float)din[w], vf[w]);
+            } else {
+#pragma unroll
+              for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[i], fin[i][w], vf[w]);
+            }
+          }
+        }
+        for (int d = 0; d < o.ndst; ++d) {
+          const EpiDst& ds = o.dst[d];
+          int64_t ld;
+          if (ds.dt == DT_F64) {
+            double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = (double)vf[w];
+          } else {
+            float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+          }
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < 8; ++w) chk = fmaf(vf[w], 0.f, chk);
+      if (o.nsplit) {
+        if (kF16) {
+#pragma unroll
+          for (int w = 0; w < 8; ++w) amax = fmaxf(amax, fabsf(vf[w]));
+        }
+        for (int s2 = 0; s2 < o.nsplit; ++s2) st8_split<kF16>(o.split[s2], x, r0, c, vf);
+      }
+    }
+  }
+  return chk != chk || (kF16 && !(amax * kFp16SplitScale < 65504.f));
+}
+
+// Boundary chunks (padding, ragged edges, grouped row limits) and ops with
+// several FP64 inputs, row group by row group. Out of line: it is rare, and
+// its registers then do not count against the lean path's.
+template <bool kF16>
+__device__ __noinline__ bool epi_chunk_generic(const EpiParams& P, EpiCtx x, int rbase, int c, const float* stg,
+                                               int lane, int lim) {
+  bool bad = false;
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    const int r0 = rbase + 8 * g;
+    if (r0 >= lim) break;
+    float a8[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
+    bad |= epi_col<8, float, kF16>(P, x, r0, c, a8);
+  }
+  return bad;
+}
+
+// The epilogue of one staged 32 x 32 chunk (rows rbase .. rbase+31, this lane's
+// column c). Rows at or beyond `lim` (a grouped tile's limit) are not written.
+template <bool kF16>
+__device__ __forceinline__ bool epi_chunk(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
+                                          int lane, int lim) {
+  if (P.fast && c < x.n && rbase + 32 <= x.n && rbase + 32 <= lim)
+    return epi_chunk_fast<kF16>(P, x, rbase, c, stg, lane);
+  return epi_chunk_generic<kF16>(P, x, rbase, c, stg, lane, lim);
+}
+
 __device__ __forceinline__ void epi_flag(const EpiParams& P, bool bad) {
   if (bad && P.status) atomicOr(P.status, 1u);
 }

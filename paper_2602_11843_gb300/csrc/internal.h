@@ -83,14 +83,21 @@ struct EpiParams {
   // nullptr for a single evaluation (order n, offset 0).
   const int* mat_n;
   int64_t mat_stride;
+  // Set by the host for ops with at most one FP64 input (f64_in, else -1):
+  // the tensor-core epilogue may take its lean path on interior chunks.
+  int fast;
+  int f64_in;
 };
 
 // Split-operand tensor maps of one tensor-core product C = A B:
 // A as (hi, lo) row-major, B as (hi, lo) stored transposed (row j of the
 // stored matrix is column j of B), both padded_n x padded_n, BF16 or FP16.
+// pair: the product runs on 2-CTA clusters (256 x 256 tiles; each CTA loads
+// 128 rows of the stored B^T, so the B maps have 128-row boxes).
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
   int fp16;
+  int pair;
 };
 
 // ---- launchers (kernels_simt.cu) ----
@@ -108,8 +115,11 @@ cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles =
 // Encode the four tensor maps over padded_n x padded_n BF16 arrays with leading
 // dimension ld; with count > 0, over count stacked padded_n x padded_n slabs
 // (3-D maps, one slab per matrix of a batch).
+// allow_pair = 0 keeps a large single product on single-CTA tiles.
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count = 0, int fp16 = 0);
+                  int count = 0, int fp16 = 0, int allow_pair = 1);
+// Whether a product of padded order npad (count = 0: single matrix) runs on CTA pairs.
+bool tc_uses_pair(int64_t npad, int count);
 // tiles == nullptr: one npad x npad product. Otherwise a grouped launch over a
 // batch (3-D maps): ntiles entries {matrix, tile row, K steps of 32, 0}; each
 // tile covers 128 rows and all 256 columns of its matrix's slab.

@@ -1,22 +1,28 @@
-// tcgen05 tensor-core product for the split-BF16 path.
+// tcgen05 tensor-core product for the split-BF16 / split-FP16 paths.
 //
-// Each operand x is stored as a pair hi = RN_bf16(x), lo = RN_bf16(x - hi), so
-// x = hi + lo to about 2^-17 relative. A product A B is formed as
+// Each operand x is stored as a pair hi = RN16(x), lo = RN16(x - hi), so
+// x = hi + lo to about 2^-17 (BF16) or 2^-22 (scaled FP16) relative. A
+// product A B is formed as
 //   Ahi Bhi + Ahi Blo + Alo Bhi
-// (the lo*lo term, ~2^-18 relative, is dropped), all three issued as
-// tcgen05.mma kind::f16 instructions into one FP32 accumulator in tensor
-// memory.
+// (the lo*lo term is dropped), all three issued as tcgen05.mma kind::f16
+// instructions into one FP32 accumulator in tensor memory.
 //
-// The kernel is persistent and warp-specialised: one CTA per SM walks the
-// 128 x 256 output tiles (tile = blockIdx.x + i * gridDim.x, grouped raster):
+// The kernel is persistent and warp-specialised. A work item is a 128 x 256
+// output tile (one CTA) or a 256 x 256 tile (a 2-CTA cluster, cta_group::2);
+// items are taken in a grouped raster, item = first + i * stride:
 //   warp 0 lane 0  TMA producer: four tiles per stage (Ahi, Alo, Bhi, Blo),
-//                  K = 32 per stage (64-byte rows, 64B swizzle), 4 stages
-//   warp 1         allocates tensor memory; lane 0 issues the MMAs: 2 K-slices
-//                  x 3 products per stage, tcgen05.commit frees the stage
-//   warps 2-5      epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//                  lanes 32 (w % 4) .. +31 = 32 rows) and the fused epilogue
+//                  K = 32 per stage (64-byte rows, 64B swizzle); 4 stages of
+//                  48 KiB (single CTA) or 6 of 32 KiB (pair: each CTA loads its
+//                  128 rows of A and 128 of the 256 columns of B)
+//   warp 1         allocates tensor memory; lane 0 (of the even CTA of a pair)
+//                  issues the MMAs: 2 K-slices x 3 products per stage, and
+//                  tcgen05.commit frees the stage (in both CTAs of a pair)
+//   warps 2-9      epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//                  lanes 32 (w % 4) .. +31 = 32 rows; two warps per lane
+//                  quarter take alternate 32-column chunks) and the fused
+//                  epilogue of epilogue.cuh
 // Two 128 x 256 FP32 accumulators (all 512 TMEM columns) alternate between
-// tiles, so the epilogue of one tile runs while the next tile's MMAs issue.
+// items, so the epilogue of one item runs while the next item's MMAs issue.
 // A is read row-major (K-major); B is read from its transpose (row j of the
 // stored array is column j of B), which makes it K-major too.
 //
@@ -33,35 +39,47 @@ namespace neumann {
 
 namespace {
 
-constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int BK = 32;  // bf16 elements per stage row = 64 bytes
-constexpr int STAGES = 4;
+constexpr int BM = 128;  // accumulator rows per CTA (TMEM lanes)
+constexpr int BN = 256;  // accumulator columns (output columns of one work item)
+constexpr int BK = 32;   // 16-bit elements per stage row = 64 bytes
 
 constexpr uint32_t A_TILE = BM * BK * 2;  // 8 KiB
-constexpr uint32_t B_TILE = BN * BK * 2;  // 16 KiB
-constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
 constexpr uint32_t STG_FLOATS = 32 * 33;  // one epilogue warp's 32 x 32 staging tile, padded
-// Epilogue warps: a single large product has long K loops that hide a 4-warp
-// epilogue; a grouped launch over small matrices has short K loops, so its
-// epilogue is the critical path and gets 8 warps (two per TMEM lane quarter).
-template <bool kGrouped>
+// Launch shapes.
+//  * single CTA (kPair = false): a CTA owns a 128 x 256 output tile and loads
+//    the full 256-row B panel per stage.
+//  * CTA pair (kPair = true): a 2-CTA cluster owns a 256 x 256 tile. Each CTA
+//    loads its own 128 rows of A and 128 of the 256 columns of B; the even CTA
+//    issues M = 256 tcgen05.mma.cta_group::2 instructions that read B from both
+//    CTAs and write each CTA's 128 rows into that CTA's tensor memory. Per
+//    unit of MMA work an SM stores and reads a third less shared memory.
+// Epilogue warps: 8, two per TMEM lane quarter taking alternate 32-column
+// chunks. The epilogue is latency-bound (a chain of dependent loads, FMAs,
+// conversions and stores per chunk), so two warps per scheduler keep it under
+// the next tile's K loop.
+template <bool kGrouped, bool kPair>
 struct EpiShape {
-  static constexpr int kWarps = kGrouped ? 8 : 4;
+  static constexpr int kWarps = 8;
   static constexpr int kThreads = 64 + 32 * kWarps;  // TMA warp, MMA warp, epilogue warps
+  static constexpr int kBRows = kPair ? BN / 2 : BN;  // rows of the stored B^T panel this CTA loads
+  static constexpr uint32_t kBTile = kBRows * BK * 2;
+  static constexpr uint32_t kStageBytes = 2 * A_TILE + 2 * kBTile;
+  static constexpr int kStages = kPair ? 6 : 4;
+  static constexpr int kTileM = kPair ? 2 * BM : BM;  // output rows of one work item
   // stages | barriers, TMEM address, abort flag (256 B) | staging tiles (+ alignment slack)
-  static constexpr uint32_t kSmem = STAGES * STAGE_BYTES + 256 + kWarps * STG_FLOATS * 4 + 1024;
+  static constexpr uint32_t kSmem = kStages * kStageBytes + 256 + kWarps * STG_FLOATS * 4 + 1024;
 };
 constexpr uint32_t ACC_COLS = BN;              // one FP32 accumulator: 128 lanes x 256 columns
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // double-buffered
-constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s; a whole launch normally takes < 20 ms
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr int64_t kPairMinN = 4096;  // padded orders from which a product runs on CTA pairs  // 2 s; a whole launch normally takes < 20 ms
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A and B both
 // BF16 (format 1 at bits 7-9 and 10-12) or both FP16 (format 0), both K-major
-// (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                ((uint32_t)(BM >> 4) << 24);
-constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24 (M = 256 for a CTA pair).
+__host__ __device__ constexpr uint32_t make_idesc(bool f16, int m) {
+  return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -140,19 +158,109 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
+// One MMA instruction D (+)= A B^T of the launch shape: cta_group::1 with
+// M = 128, or cta_group::2 with M = 256 issued by the even CTA of a pair.
+template <bool kPair>
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {  // idesc: kIdescBf16 or kIdescF16
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
+                                         uint32_t accumulate) {
+  if constexpr (kPair) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
+// Arrive on `bar` once every MMA this thread issued so far has completed. For
+// a pair, `both` arrives on the barrier at the same offset in both CTAs.
+template <bool kPair>
+__device__ __forceinline__ void umma_commit(uint32_t bar, bool both = true) {
+  if constexpr (kPair) {
+    if (both) {
+      asm volatile(
+          "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+              bar),
+          "h"((uint16_t)3)
+          : "memory");
+    } else {
+      asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                   : "memory");
+    }
+  } else {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+  }
+}
+
+template <bool kPair>
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t cols) {
+  if constexpr (kPair) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+}
+
+template <bool kPair>
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t cols) {
+  if constexpr (kPair)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+// ---- clusters (CTA pairs) ----
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Address, in the cluster's shared window, of the same offset in CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+// Every thread of both CTAs; orders earlier shared-memory writes (barrier
+// initialisation included) before later accesses from the other CTA.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on the
+// even CTA's barrier (`cluster_bar`, an address in the cluster window).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t cluster_bar, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(cluster_bar), "r"(x), "r"(y)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
@@ -203,30 +311,48 @@ __device__ __forceinline__ void tile_of(int tile, const int4* tiles, int ktiles,
   }
 }
 
-template <bool kGrouped>
+// The four operand tiles of K stage `kb` of a work item: rows `ra` of A
+// (hi, lo) and rows `rb` of the stored B^T (hi, lo), 32 deep.
+template <bool kGrouped, bool kPair>
 __device__ __forceinline__ void load_stage(uint32_t st, const CUtensorMap* ahi, const CUtensorMap* alo,
                                            const CUtensorMap* bhi, const CUtensorMap* blo, uint32_t bar, int kb,
-                                           int tm, int tn, int mat) {
-  if (kGrouped) {
-    tma_load_3d(st, ahi, bar, kb * BK, tm * BM, mat);
-    tma_load_3d(st + A_TILE, alo, bar, kb * BK, tm * BM, mat);
-    tma_load_3d(st + 2 * A_TILE, bhi, bar, kb * BK, tn * BN, mat);
-    tma_load_3d(st + 2 * A_TILE + B_TILE, blo, bar, kb * BK, tn * BN, mat);
+                                           int ra, int rb, int mat) {
+  using S = EpiShape<kGrouped, kPair>;
+  if constexpr (kGrouped) {
+    tma_load_3d(st, ahi, bar, kb * BK, ra, mat);
+    tma_load_3d(st + A_TILE, alo, bar, kb * BK, ra, mat);
+    tma_load_3d(st + 2 * A_TILE, bhi, bar, kb * BK, rb, mat);
+    tma_load_3d(st + 2 * A_TILE + S::kBTile, blo, bar, kb * BK, rb, mat);
+  } else if constexpr (kPair) {
+    tma_load_2d_pair(st, ahi, bar, kb * BK, ra);
+    tma_load_2d_pair(st + A_TILE, alo, bar, kb * BK, ra);
+    tma_load_2d_pair(st + 2 * A_TILE, bhi, bar, kb * BK, rb);
+    tma_load_2d_pair(st + 2 * A_TILE + S::kBTile, blo, bar, kb * BK, rb);
   } else {
-    tma_load_2d(st, ahi, bar, kb * BK, tm * BM);
-    tma_load_2d(st + A_TILE, alo, bar, kb * BK, tm * BM);
-    tma_load_2d(st + 2 * A_TILE, bhi, bar, kb * BK, tn * BN);
-    tma_load_2d(st + 2 * A_TILE + B_TILE, blo, bar, kb * BK, tn * BN);
+    tma_load_2d(st, ahi, bar, kb * BK, ra);
+    tma_load_2d(st + A_TILE, alo, bar, kb * BK, ra);
+    tma_load_2d(st + 2 * A_TILE, bhi, bar, kb * BK, rb);
+    tma_load_2d(st + 2 * A_TILE + S::kBTile, blo, bar, kb * BK, rb);
   }
 }
 
-template <bool kGrouped, bool kF16>
-__global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
+__device__ __forceinline__ void spin_ns(uint64_t ns) {
+  const uint64_t t0 = gtimer();
+  while (gtimer() - t0 < ns) {
+  }
+}
+
+template <bool kGrouped, bool kF16, bool kPair>
+__global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
                          int ktiles, int tiles_m, int tiles_n, const int4* __restrict__ tiles, int ntiles_grouped,
                          const __grid_constant__ EpiParams P) {
-  constexpr uint32_t idesc = kF16 ? kIdescF16 : kIdescBf16;
+  static_assert(!(kGrouped && kPair), "grouped launches use single-CTA tiles");
+  using S = EpiShape<kGrouped, kPair>;
+  constexpr int STAGES = S::kStages;
+  constexpr uint32_t STAGE_BYTES = S::kStageBytes;
+  constexpr uint32_t idesc = make_idesc(kF16, S::kTileM);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain
@@ -236,6 +362,12 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = kGrouped ? ntiles_grouped : tiles_m * tiles_n;
+  // Work items: one per CTA (single) or per cluster (pair); both CTAs of a
+  // pair walk the same items, the odd one owning rows 128 .. 255 of each.
+  const uint32_t rank = kPair ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  const int first = kPair ? (int)cluster_index() : (int)blockIdx.x;
+  const int stride = kPair ? (int)cluster_count() : (int)gridDim.x;
   const uint32_t smem_base = smem_u32(smem);
   const uint32_t bar_base = smem_u32(bars);
   auto full_bar = [&](uint32_t s) { return bar_base + 8u * s; };
@@ -251,22 +383,23 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), EpiShape<kGrouped>::kWarps);  // lane 0 of each epilogue warp
+      // lane 0 of each epilogue warp (of both CTAs for a pair; only the even CTA's is used)
+      mbar_init(tempty_bar(b), S::kWarps * (kPair ? 2 : 1));
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc<kPair>(smem_u32(tmem_slot), TMEM_COLS);
   tc_fence_before();
-  __syncthreads();
+  if constexpr (kPair)
+    cluster_sync();
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // Stage-full and accumulator-free barriers live in the even CTA of a pair.
+  const uint32_t lead_bar_base = kPair ? cluster_addr(bar_base, 0) : bar_base;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -277,9 +410,11 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_blo)) : "memory");
       uint32_t kg = 0;  // stage loads issued so far
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int tile = first; tile < ntiles && ok; tile += stride) {
         int mat, tm, tn, nk;
         tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
+        const int ra = tm * S::kTileM + (int)rank * BM;
+        const int rb = tn * BN + (int)rank * S::kBRows;
         for (int kb = 0; kb < nk; ++kb) {
           const uint32_t s = kg % STAGES;
           const uint32_t ph = (kg / STAGES) & 1u;
@@ -288,25 +423,31 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
             break;
           }
           const uint32_t st = smem_base + s * STAGE_BYTES;
-          mbar_expect_tx(full_bar(s), STAGE_BYTES);
-          load_stage<kGrouped>(st, &tm_ahi, &tm_alo, &tm_bhi, &tm_blo, full_bar(s), kb, tm, tn, mat);
+          if (leader) mbar_expect_tx(full_bar(s), STAGE_BYTES * (kPair ? 2u : 1u));
+          load_stage<kGrouped, kPair>(st, &tm_ahi, &tm_alo, &tm_bhi, &tm_blo, lead_bar_base + 8u * s, kb, ra, rb,
+                                      mat);
           ++kg;
         }
       }
       if (!ok) {
         *abort_flag = 1;
-        // drain: wait (bounded) for the last load issued into each stage
-        for (uint32_t q = (kg > STAGES ? kg - STAGES : 0); q < kg; ++q)
-          mbar_wait(full_bar(q % STAGES), (q / STAGES) & 1u);
+        if (leader) {
+          // drain: wait (bounded) for the last load issued into each stage
+          for (uint32_t q = (kg > STAGES ? kg - STAGES : 0); q < kg; ++q)
+            mbar_wait(full_bar(q % STAGES), (q / STAGES) & 1u, 10000000ull);
+        } else {
+          // this CTA's loads complete on the even CTA's barriers: give them time to land
+          spin_ns(10000000ull);
+        }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       // ---------------- MMA issuer ----------------
       uint32_t kg = 0;
       bool ok = true;
       int it = 0;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+      for (int tile = first; tile < ntiles && ok; tile += stride, ++it) {
         const uint32_t buf = it & 1;
         const uint32_t use = (uint32_t)it >> 1;
         if (it >= 2 && (!mbar_wait(tempty_bar(buf), (use - 1) & 1u) || *abort_flag)) {
@@ -331,19 +472,19 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
             const uint64_t a_hi = smem_desc(st + 32u * j);
             const uint64_t a_lo = smem_desc(st + A_TILE + 32u * j);
             const uint64_t b_hi = smem_desc(st + 2 * A_TILE + 32u * j);
-            const uint64_t b_lo = smem_desc(st + 2 * A_TILE + B_TILE + 32u * j);
-            umma_f16(d, a_hi, b_hi, idesc, (kb | j) != 0);
-            umma_f16(d, a_hi, b_lo, idesc, 1u);
-            umma_f16(d, a_lo, b_hi, idesc, 1u);
+            const uint64_t b_lo = smem_desc(st + 2 * A_TILE + S::kBTile + 32u * j);
+            umma_f16<kPair>(d, a_hi, b_hi, idesc, (kb | j) != 0);
+            umma_f16<kPair>(d, a_hi, b_lo, idesc, 1u);
+            umma_f16<kPair>(d, a_lo, b_hi, idesc, 1u);
           }
-          umma_commit(empty_bar(s));
+          umma_commit<kPair>(empty_bar(s));  // frees the stage in both CTAs of a pair
           ++kg;
         }
-        if (ok) umma_commit(tfull_bar(buf));  // accumulator `buf` holds the finished tile
+        if (ok) umma_commit<kPair>(tfull_bar(buf));  // accumulator `buf` holds the finished tile
       }
       if (!ok) *abort_flag = 1;
       // no MMA may be in flight when the tensor memory is freed
-      umma_commit(drain_bar);
+      umma_commit<kPair>(drain_bar, false);
       mbar_wait(drain_bar, 0);
     }
   } else {
@@ -351,13 +492,13 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
     // Each 32 x 32 chunk is read from TMEM one row per lane, staged in shared
     // memory, and processed one column per lane (epi_col), so that the warp's
     // global loads and stores of row-major buffers touch one line per instruction.
-    constexpr int kStep = EpiShape<kGrouped>::kWarps / 4;  // warps per TMEM lane quarter
-    const int q = warp & 3;                 // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;       // warps of one quarter take alternate column chunks
+    constexpr int kStep = S::kWarps / 4;  // warps per TMEM lane quarter
+    const int q = warp & 3;               // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;     // warps of one quarter take alternate column chunks
     float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * STG_FLOATS;
     bool bad = false;
     int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    for (int tile = first; tile < ntiles; tile += stride, ++it) {
       const uint32_t buf = it & 1;
       const uint32_t use = (uint32_t)it >> 1;
       const bool got = mbar_wait(tfull_bar(buf), use & 1u);
@@ -369,7 +510,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
       int mat, tm, tn, nk;
       tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
       const EpiCtx x = epi_ctx(P, mat);
-      const int rbase = tm * BM + q * 32;
+      const int rbase = tm * S::kTileM + (int)rank * BM + q * 32;
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
       // A grouped tile writes rows and columns below its matrix's order rounded
       // up to 32 (= nk x 32): with that K padding zero in both operands, later
@@ -384,31 +525,30 @@ __global__ void __launch_bounds__(EpiShape<kGrouped>::kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
         __syncwarp();
-        const int c = tn * BN + chunk * 32 + lane;
-#pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
-          const int r0 = rbase + 8 * g;
-          if (r0 >= lim) break;
-          float a8[8];
-#pragma unroll
-          for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
-          bad |= epi_col<8, float, kF16>(P, x, r0, c, a8);
-        }
+        bad |= epi_chunk<kF16>(P, x, rbase, tn * BN + chunk * 32 + lane, stg, lane, lim);
         __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(buf));
+      if (lane == 0) {
+        if constexpr (kPair)
+          mbar_arrive_cluster(lead_bar_base + 8u * (2 * STAGES + 2 + buf));
+        else
+          mbar_arrive(tempty_bar(buf));
+      }
     }
     epi_flag(P, bad);
   }
 
   tc_fence_before();
-  __syncthreads();
+  if constexpr (kPair)
+    cluster_sync();  // the even CTA's MMAs into this CTA's tensor memory have drained
+  else
+    __syncthreads();
   if (threadIdx.x == 0 && *abort_flag && P.status) atomicOr(P.status, 2u);
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    tmem_free<kPair>(tmem, TMEM_COLS);
   }
 }
 
@@ -458,12 +598,17 @@ bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box
 
 }  // namespace
 
+bool tc_uses_pair(int64_t npad, int count) { return count == 0 && npad >= kPairMinN; }
+
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count, int fp16) {
+                  int count, int fp16, int allow_pair) {
   if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0) return false;
   m->fp16 = fp16;
+  m->pair = allow_pair && tc_uses_pair(npad, count);
+  const uint32_t brows = m->pair ? BN / 2 : BN;
   return make_map(&m->a_hi, a_hi, npad, ld, BM, count, fp16) && make_map(&m->a_lo, a_lo, npad, ld, BM, count, fp16) &&
-         make_map(&m->b_hi, bt_hi, npad, ld, BN, count, fp16) && make_map(&m->b_lo, bt_lo, npad, ld, BN, count, fp16);
+         make_map(&m->b_hi, bt_hi, npad, ld, brows, count, fp16) &&
+         make_map(&m->b_lo, bt_lo, npad, ld, brows, count, fp16);
 }
 
 cudaError_t launch_wait_probe(unsigned* status, uint64_t limit_ns, cudaStream_t s) {
@@ -471,21 +616,65 @@ cudaError_t launch_wait_probe(unsigned* status, uint64_t limit_ns, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,
-                           const int4* tiles, int ntiles) {
-  if (npad % BN != 0) return cudaErrorInvalidValue;
+namespace {
+
+cudaError_t set_smem_attributes() {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e[4] = {
-        cudaFuncSetAttribute(tc_split_gemm_kernel<false, false>, a, (int)EpiShape<false>::kSmem),
-        cudaFuncSetAttribute(tc_split_gemm_kernel<false, true>, a, (int)EpiShape<false>::kSmem),
-        cudaFuncSetAttribute(tc_split_gemm_kernel<true, false>, a, (int)EpiShape<true>::kSmem),
-        cudaFuncSetAttribute(tc_split_gemm_kernel<true, true>, a, (int)EpiShape<true>::kSmem)};
+    cudaError_t e[6] = {
+        cudaFuncSetAttribute(tc_split_gemm_kernel<false, false, false>, a, (int)EpiShape<false, false>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<false, true, false>, a, (int)EpiShape<false, false>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<true, false, false>, a, (int)EpiShape<true, false>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<true, true, false>, a, (int)EpiShape<true, false>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<false, false, true>, a, (int)EpiShape<false, true>::kSmem),
+        cudaFuncSetAttribute(tc_split_gemm_kernel<false, true, true>, a, (int)EpiShape<false, true>::kSmem)};
     for (cudaError_t x : e)
       if (x != cudaSuccess) attr_err = x;
   });
+  return attr_err;
+}
+
+// One product on CTA pairs: as many 2-CTA clusters as can be resident at once
+// (one CTA per SM), each walking the 256 x 256 tiles.
+template <bool kF16>
+cudaError_t launch_pair(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s) {
+  using Sh = EpiShape<false, true>;
+  auto k = tc_split_gemm_kernel<false, kF16, true>;
+  const int tiles_m = (int)(npad / Sh::kTileM), tiles_n = (int)(npad / BN);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(Sh::kThreads);
+  cfg.dynamicSmemBytes = Sh::kSmem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  static int max_pairs = 0;
+  if (max_pairs == 0) {
+    cfg.gridDim = dim3(2 * tiles_m * tiles_n);
+    int nc = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, k, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nc <= 0) return cudaErrorInvalidConfiguration;
+    max_pairs = nc;
+  }
+  const int pairs = tiles_m * tiles_n < max_pairs ? tiles_m * tiles_n : max_pairs;
+  cfg.gridDim = dim3(2 * pairs);
+  return cudaLaunchKernelEx(&cfg, k, maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n,
+                            (const int4*)nullptr, 0, P);
+}
+
+}  // namespace
+
+cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,
+                           const int4* tiles, int ntiles) {
+  if (npad % BN != 0) return cudaErrorInvalidValue;
+  cudaError_t attr_err = set_smem_attributes();
   if (attr_err != cudaSuccess) return attr_err;
   static int sms = 0;
   if (sms == 0) {
@@ -496,15 +685,16 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
     const int grid = ntiles < sms ? ntiles : sms;
-    auto k = maps.fp16 ? tc_split_gemm_kernel<true, true> : tc_split_gemm_kernel<true, false>;
-    k<<<grid, EpiShape<true>::kThreads, EpiShape<true>::kSmem, s>>>(maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0,
-                                                                     0, tiles, ntiles, P);
+    auto k = maps.fp16 ? tc_split_gemm_kernel<true, true, false> : tc_split_gemm_kernel<true, false, false>;
+    k<<<grid, EpiShape<true, false>::kThreads, EpiShape<true, false>::kSmem, s>>>(
+        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, tiles, ntiles, P);
     return cudaGetLastError();
   }
+  if (maps.pair) return maps.fp16 ? launch_pair<true>(maps, npad, P, s) : launch_pair<false>(maps, npad, P, s);
   const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
-  auto k = maps.fp16 ? tc_split_gemm_kernel<false, true> : tc_split_gemm_kernel<false, false>;
-  k<<<grid, EpiShape<false>::kThreads, EpiShape<false>::kSmem, s>>>(
+  auto k = maps.fp16 ? tc_split_gemm_kernel<false, true, false> : tc_split_gemm_kernel<false, false, false>;
+  k<<<grid, EpiShape<false, false>::kThreads, EpiShape<false, false>::kSmem, s>>>(
       maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, nullptr, 0, P);
   return cudaGetLastError();
 }

@@ -84,6 +84,7 @@ EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char
   o.nsplit = 1;
   o.split[0] = EpiSplit{hi, lo, npad, transposed};
   P.status = nullptr;
+  P.f64_in = -1;
   return P;
 }
 
@@ -128,6 +129,8 @@ extern "C" int neumann_matmul_noalloc(int64_t n, const void* A, int64_t lda, con
   pc.out[0].ndst = 1;
   pc.out[0].dst[0] = EpiDst{C, ldc, DT_F64, EPI_PTR};
   pc.status = nullptr;
+  pc.fast = 1;
+  pc.f64_in = -1;
   if (launch_tc_gemm(maps, npad, pc, s) != cudaSuccess) return NEUMANN_ECUDA;
   return NEUMANN_OK;
 }

@@ -731,6 +731,15 @@ void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiPa
   for (int i = 0; i < op.nin; ++i) P->in[i] = resolve_in(p, op.in[i], u);
   P->nout = op.nout;
   for (int j = 0; j < op.nout; ++j) P->out[j] = resolve_out(p, op.out[j], P->in, op.nin, u);
+  // the tensor-core epilogue's lean path handles at most one FP64 input
+  int nf64 = 0;
+  P->f64_in = -1;
+  for (int i = 0; i < op.nin; ++i)
+    if (P->in[i].dt == DT_F64) {
+      ++nf64;
+      P->f64_in = i;
+    }
+  P->fast = nf64 <= 1;
 }
 
 bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMaps>* maps) {
@@ -741,7 +750,8 @@ bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMap
     const SlotBufs& a = p->bufs[op.a];
     const SlotBufs& b = p->bufs[op.b];
     if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + b.b_hi, p->ws + b.b_lo, p->npad,
-                      p->npad, p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16))
+                      p->npad, p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16,
+                      !(p->flags & NEUMANN_FLAG_SINGLE_CTA)))
       return false;
   }
   return true;
