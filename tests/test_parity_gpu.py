@@ -9,9 +9,10 @@ scheme: S_k for exact schemes, Lemma 5.7's closed form for radix 15):
               across levels.
   split-FP16  TOL_FP16[rho]; operands kept to ~2^-22 relative (x 2^8 scaling keeps
               lo normal for |x| >= 2^-11), the same amplification. A product's
-              FP32 accumulation on the tensor cores adds ~sqrt(n) 2^-24 relative
-              (2e-6 at n = 513, 5e-6 at n = 8192), which at n = 8192 matches the
-              BF16 operand error: there both splits end near 1e-3 (rho = 0.97).
+              FP32 accumulation on the tensor cores is biased toward zero by about
+              (3n/16)/4 ulp of the sum (one truncating update per MMA; 2e-6 at
+              n = 513, 3-5e-5 at n = 8192), which at n = 8192 exceeds both operand
+              errors: there both splits end near 1e-3 (rho = 0.97).
 """
 
 import numpy as np
