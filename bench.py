@@ -292,6 +292,8 @@ def run_batched(args, wl):
     A_all.copy_(torch.from_numpy(host).to(dt))
     As = [A_all[offs[i]:offs[i + 1]].view(n, n) for i, n in enumerate(ns)]
     outs = [S_all[offs[i]:offs[i + 1]].view(n, n) for i, n in enumerate(ns)]
+    if not args.no_autotune:
+        bp.autotune(As, outs, reps=2)  # the library's autotuner picks the matrices per pass
     bp.bind(As, outs)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -322,6 +324,7 @@ def run_batched(args, wl):
     status = bp.status()
     value = job_value(len(mats), args.steps, world, ms_max)
     info = nm.neumann_plan_info(bp.handle)
+    ck = info["batch_chunk"] or len(mats)
     # the same batch, one plan per matrix order and one evaluation (own launches) per matrix
     plans = {}
     for n in sorted(set(ns)):
@@ -386,13 +389,14 @@ def run_batched(args, wl):
         "data": "synthetic",
         "config": {"workload": args.workload, "count": len(mats), "n": "uniform in {16,...,256}", "k": wl["k"],
                    "radix": wl["radix"], "scheme": wl["dtype"], "products_per_matrix": per,
-                   "launches_per_step": info["launches"] * ((len(mats) + 2047) // 2048),
+                   "launches_per_step": info["launches"] * ((len(mats) + ck - 1) // ck),
+                   "batch_chunk": info["batch_chunk"], "autotuned": bool(info["tuned"]),
                    "l2": "inputs larger than L2 (the batch's A alone is 0.39 GB in FP32)",
                    "parallelism": f"replicas x{world}"},
         "vs_per_matrix": {"ms_per_batch": per_matrix_ms, "speedup": per_matrix_ms / (ms_max / args.steps)},
         "status": status, "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
-        "gpu_launches": args.steps * info["launches"] * ((len(mats) + 2047) // 2048),
+        "gpu_launches": args.steps * info["launches"] * ((len(mats) + ck - 1) // ck),
         "roofline": roof,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -448,10 +452,12 @@ def run_ours(args, wl):
     A = torch.tensor(A_np, dtype=io, device=dev)
     S = torch.empty_like(A)
     stream = torch.cuda.current_stream(dev)
+    if not args.no_autotune:
+        plan.autotune(A, out=S, reps=2)  # the library's autotuner picks tiles and raster
     for _ in range(args.warmup):
         plan(A, out=S)
     torch.cuda.synchronize()
-    plan.timing()  # discard warm-up records
+    plan.timing()  # discard warm-up and tuning records
     assert plan.status() == 0, "device status set during warm-up"
 
     uuid = None
@@ -571,6 +577,9 @@ def run_ours(args, wl):
         "config": {"workload": args.workload, "n": n, "k": k, "radix": wl["radix"], "scheme": wl["dtype"],
                    "products_per_step": info["products_executed"], "products_formula": info["products_formula"],
                    "l2": "inputs larger than L2 (A, S and every workspace matrix exceed 129 MB)",
+                   "tiles": None if wl["dtype"] in ("fp32", "fp64") else
+                            ("2-CTA 256x256" if info["tile_pair"] else "1-CTA 128x256"),
+                   "raster_group": info["raster_group"] or None, "autotuned": bool(info["tuned"]),
                    "parallelism": f"replicas x{world}"},
         "vs_squaring": {"k": wl["sq_k"], "ms_per_step": sq_ms, "speedup": sq_ms / (ms_max / args.steps),
                         "products_executed": sq.info["products_executed"],
@@ -599,6 +608,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default launch configuration")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison evaluation")
     ap.add_argument("--fp64-large", action="store_true", help="run the FP64 comparison on the n = 16384 workload")
     args = ap.parse_args()

@@ -101,6 +101,12 @@ typedef struct {
   int64_t launches;             /* kernel launches per neumann_eval */
   size_t workspace_bytes;       /* device workspace the plan needs */
   int64_t padded_n;             /* workspace matrices are padded_n x padded_n */
+  /* Launch configuration (set by neumann_plan_autotune*, else the defaults): */
+  int tile_pair;                /* split dtypes, single plans: 1 = products on 2-CTA 256 x 256 tiles,
+                                   0 = 1-CTA 128 x 256 tiles */
+  int raster_group;             /* split dtypes, single plans: row tiles per raster group */
+  int batch_chunk;              /* grouped batched plans (max_n <= 256): matrices per pass */
+  int tuned;                    /* 1 once tuned, by this plan or by an earlier plan of the same shape */
 } neumann_plan_info_t;
 
 /* Create a plan for S_k(A) with A n x n. Host-only: no device memory is
@@ -164,6 +170,31 @@ int neumann_eval_batched(neumann_plan_t plan, int count, const int64_t* n, const
  * bits (NEUMANN_STATUS_*) set since the previous call, then clear them.
  * Errors: NEUMANN_EINVAL, NEUMANN_ECUDA. */
 int neumann_last_status(neumann_plan_t plan, unsigned* status);
+
+/* Autotuner. Times each candidate launch configuration on the caller's input
+ * (one untimed and `reps` timed evaluations per candidate, CUDA events on the
+ * stream, median), keeps the fastest in the plan and records it for the
+ * process: plans created later with the same shape start from it (their
+ * info.tuned is 1). The evaluations write S (its final contents are those of a
+ * correct evaluation). Synchronous: returns after the last timed run.
+ *   split dtypes   candidates: {1-CTA, 2-CTA pair} tiles x raster groups {4, 8, 16}
+ *                  (pairs are skipped under NEUMANN_FLAG_SINGLE_CTA); shape key
+ *                  (padded_n, dtype)
+ *   FP64, FP32     one launch shape: marks the plan tuned and returns
+ * Arguments as neumann_eval; reps >= 1.
+ * Errors: NEUMANN_EINVAL (batched plan, bad arguments), NEUMANN_ENOMEM, NEUMANN_ECUDA. */
+int neumann_plan_autotune(neumann_plan_t plan, const void* A, int64_t lda, void* S, int64_t lds, int reps,
+                          void* stream);
+
+/* Autotuner for a batched plan: arguments as neumann_eval_batched plus reps.
+ * For a grouped plan (max_n <= 256) it times the number of matrices per pass
+ * (the plan's chunk halved down to 64, at most 6 candidates): smaller passes
+ * keep a pass's intermediate matrices in L2, larger ones fill the GPU with
+ * fewer launches. Shape key (count, max_n, k, radix, dtype). A plan with larger
+ * orders runs one single plan per order and is only marked tuned.
+ * Errors as neumann_eval_batched. */
+int neumann_plan_autotune_batched(neumann_plan_t plan, int count, const int64_t* n, const void* const* A,
+                                  void* const* S, int reps, void* stream);
 
 /* With NEUMANN_FLAG_TIMING every product launched by neumann_eval is bracketed
  * by two CUDA events on the evaluation's stream. This call synchronises on the

@@ -9,8 +9,9 @@ from __future__ import annotations
 
 from ._capi import *  # noqa: F401,F403
 from ._capi import (DTYPES, FP32, FP64, SPLIT_BF16, LIB_PATH, neumann_eval, neumann_eval_batched,  # noqa: F401
-                    neumann_last_status, neumann_plan_create, neumann_plan_create_batched,
-                    neumann_plan_destroy, neumann_plan_info, neumann_plan_matmul, neumann_plan_timing)
+                    neumann_last_status, neumann_plan_autotune, neumann_plan_autotune_batched,
+                    neumann_plan_create, neumann_plan_create_batched, neumann_plan_destroy, neumann_plan_info,
+                    neumann_plan_matmul, neumann_plan_timing)
 
 
 def _torch_dtype(dtype: int, flags: int):
@@ -54,6 +55,19 @@ class Plan:
         s = torch.cuda.current_stream(A.device) if stream is None else stream
         neumann_plan_matmul(self.handle, A.data_ptr(), B.data_ptr(), C.data_ptr(), s.cuda_stream)
         return C
+
+    def autotune(self, A, out=None, reps: int = 3, stream=None):
+        """Pick the fastest launch configuration for this plan on input A (writes `out`)."""
+        import torch
+
+        n = self.info["n"]
+        if A.device.type != "cuda" or A.dtype != self.io_dtype or A.shape != (n, n) or A.stride(1) != 1:
+            raise ValueError(f"A must be a CUDA {self.io_dtype} ({n}, {n}) tensor with unit column stride")
+        S = torch.empty((n, n), dtype=self.io_dtype, device=A.device) if out is None else out
+        s = torch.cuda.current_stream(A.device) if stream is None else stream
+        neumann_plan_autotune(self.handle, A.data_ptr(), A.stride(0), S.data_ptr(), S.stride(0), reps, s.cuda_stream)
+        self.info = neumann_plan_info(self.handle)
+        return self.info
 
     def status(self) -> int:
         return neumann_last_status(self.handle)
@@ -116,6 +130,19 @@ class BatchedPlan:
         cnt, na, aa, sa, As, _ = self._bound
         s = torch.cuda.current_stream(As[0].device) if stream is None else stream
         _check(_lib.neumann_eval_batched(self.handle, cnt, na, aa, sa, s.cuda_stream), "neumann_eval_batched")
+
+    def autotune(self, As, outs, reps: int = 3, stream=None):
+        """Pick the fastest matrices-per-pass for this batch (writes `outs`)."""
+        import torch
+
+        dt = _torch_dtype(self.dtype, self.flags)
+        for a, o in zip(As, outs):
+            if a.dtype != dt or o.dtype != dt or not a.is_contiguous() or not o.is_contiguous():
+                raise ValueError(f"inputs and outputs must be contiguous {dt}")
+        s = torch.cuda.current_stream(As[0].device) if stream is None else stream
+        neumann_plan_autotune_batched(self.handle, [a.shape[0] for a in As], [a.data_ptr() for a in As],
+                                      [o.data_ptr() for o in outs], reps, s.cuda_stream)
+        return neumann_plan_info(self.handle)
 
     def status(self) -> int:
         return neumann_last_status(self.handle)

@@ -48,6 +48,7 @@ class PlanInfo(ctypes.Structure):
         ("levels", c_int), ("level_radix", c_int * MAX_LEVELS),
         ("products_formula", c_int64), ("products_executed", c_int64), ("launches", c_int64),
         ("workspace_bytes", c_size_t), ("padded_n", c_int64),
+        ("tile_pair", c_int), ("raster_group", c_int), ("batch_chunk", c_int), ("tuned", c_int),
     ]
 
 
@@ -71,6 +72,9 @@ def _load():
         "neumann_plan_selftest_timeout": (c_int, [P, ctypes.c_uint64, c_void_p]),
         "neumann_matmul_noalloc": (c_int, [c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                            c_void_p]),
+        "neumann_plan_autotune": (c_int, [P, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p]),
+        "neumann_plan_autotune_batched": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_void_p), POINTER(c_void_p),
+                                                  c_int, c_void_p]),
         "neumann_plan_destroy": (None, [P]),
         "neumann_error_string": (ctypes.c_char_p, [c_int]),
     }
@@ -114,6 +118,8 @@ def neumann_plan_info(plan: int) -> dict:
         "levels": list(info.level_radix[: info.levels]),
         "products_formula": info.products_formula, "products_executed": info.products_executed,
         "launches": info.launches, "workspace_bytes": info.workspace_bytes, "padded_n": info.padded_n,
+        "tile_pair": info.tile_pair, "raster_group": info.raster_group, "batch_chunk": info.batch_chunk,
+        "tuned": info.tuned,
     }
 
 
@@ -135,6 +141,18 @@ def neumann_eval_batched(plan: int, n, A, S, stream: int = 0) -> None:
     aa = (c_void_p * cnt)(*A)
     sa = (c_void_p * cnt)(*S)
     _check(_lib.neumann_eval_batched(plan, cnt, na, aa, sa, stream), "neumann_eval_batched")
+
+
+def neumann_plan_autotune(plan: int, A: int, lda: int, S: int, lds: int, reps: int = 3, stream: int = 0) -> None:
+    _check(_lib.neumann_plan_autotune(plan, A, lda, S, lds, reps, stream), "neumann_plan_autotune")
+
+
+def neumann_plan_autotune_batched(plan: int, n, A, S, reps: int = 3, stream: int = 0) -> None:
+    cnt = len(n)
+    na = (c_int64 * cnt)(*n)
+    aa = (c_void_p * cnt)(*A)
+    sa = (c_void_p * cnt)(*S)
+    _check(_lib.neumann_plan_autotune_batched(plan, cnt, na, aa, sa, reps, stream), "neumann_plan_autotune_batched")
 
 
 def neumann_last_status(plan: int) -> int:

@@ -94,11 +94,15 @@ struct EpiParams {
 // stored matrix is column j of B), both padded_n x padded_n, BF16 or FP16.
 // pair: the product runs on 2-CTA clusters (256 x 256 tiles; each CTA loads
 // 128 rows of the stored B^T, so the B maps have 128-row boxes).
+// group: row tiles per group of the grouped raster of a single product.
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
   int fp16;
   int pair;
+  int group;
 };
+
+constexpr int kDefaultRasterGroup = 8;
 
 // ---- launchers (kernels_simt.cu) ----
 // tiles == nullptr: one padded npad x npad product. Otherwise a grouped launch
@@ -115,9 +119,10 @@ cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles =
 // Encode the four tensor maps over padded_n x padded_n BF16 arrays with leading
 // dimension ld; with count > 0, over count stacked padded_n x padded_n slabs
 // (3-D maps, one slab per matrix of a batch).
-// allow_pair = 0 keeps a large single product on single-CTA tiles.
+// pair_mode: -1 CTA pairs where tc_uses_pair says so, 0 never, 1 always (single
+// products only). group: row tiles per raster group (>= 1).
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count = 0, int fp16 = 0, int allow_pair = 1);
+                  int count = 0, int fp16 = 0, int pair_mode = -1, int group = kDefaultRasterGroup);
 // Whether a product of padded order npad (count = 0: single matrix) runs on CTA pairs.
 bool tc_uses_pair(int64_t npad, int count);
 // tiles == nullptr: one npad x npad product. Otherwise a grouped launch over a

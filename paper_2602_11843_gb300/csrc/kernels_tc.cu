@@ -276,12 +276,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int* tm, int* tn) {
-  constexpr int G = 8;  // row tiles per group: neighbouring CTAs share B column panels in L2
-  const int per_group = G * tiles_n;
+// Grouped raster: `group` row tiles form a group; work items run down the
+// group's rows first, so neighbouring CTAs share column panels of B in L2.
+__device__ __forceinline__ void raster(int bid, int tiles_m, int tiles_n, int group, int* tm, int* tn) {
+  const int per_group = group * tiles_n;
   const int g = bid / per_group;
-  const int first = g * G;
-  const int gs = min(tiles_m - first, G);
+  const int first = g * group;
+  const int gs = min(tiles_m - first, group);
   const int in = bid - g * per_group;
   *tm = first + in % gs;
   *tn = in / gs;
@@ -296,8 +297,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // grouped launch reads the host-built table (one 128 x 256 tile per entry,
 // K stages covering that matrix's order rounded up to 32).
 template <bool kGrouped>
-__device__ __forceinline__ void tile_of(int tile, const int4* tiles, int ktiles, int tiles_m, int tiles_n, int* mat,
-                                        int* tm, int* tn, int* nk) {
+__device__ __forceinline__ void tile_of(int tile, const int4* tiles, int ktiles, int tiles_m, int tiles_n, int group,
+                                        int* mat, int* tm, int* tn, int* nk) {
   if (kGrouped) {
     const int4 t = tiles[tile];
     *mat = t.x;
@@ -306,7 +307,7 @@ __device__ __forceinline__ void tile_of(int tile, const int4* tiles, int ktiles,
     *nk = t.z;
   } else {
     *mat = 0;
-    raster(tile, tiles_m, tiles_n, tm, tn);
+    raster(tile, tiles_m, tiles_n, group, tm, tn);
     *nk = ktiles;
   }
 }
@@ -346,8 +347,8 @@ template <bool kGrouped, bool kF16, bool kPair>
 __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
-                         int ktiles, int tiles_m, int tiles_n, const int4* __restrict__ tiles, int ntiles_grouped,
-                         const __grid_constant__ EpiParams P) {
+                         int ktiles, int tiles_m, int tiles_n, int group, const int4* __restrict__ tiles,
+                         int ntiles_grouped, const __grid_constant__ EpiParams P) {
   static_assert(!(kGrouped && kPair), "grouped launches use single-CTA tiles");
   using S = EpiShape<kGrouped, kPair>;
   constexpr int STAGES = S::kStages;
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
       bool ok = true;
       for (int tile = first; tile < ntiles && ok; tile += stride) {
         int mat, tm, tn, nk;
-        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
+        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
         const int ra = tm * S::kTileM + (int)rank * BM;
         const int rb = tn * BN + (int)rank * S::kBRows;
         for (int kb = 0; kb < nk; ++kb) {
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
         }
         tc_fence_after();
         int mat, tm, tn, nk;
-        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
+        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
         const uint32_t d = tmem + buf * ACC_COLS;
         for (int kb = 0; kb < nk; ++kb) {
           const uint32_t s = kg % STAGES;
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
       }
       tc_fence_after();
       int mat, tm, tn, nk;
-      tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, &mat, &tm, &tn, &nk);
+      tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
       const EpiCtx x = epi_ctx(P, mat);
       const int rbase = tm * S::kTileM + (int)rank * BM + q * 32;
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
@@ -601,10 +602,11 @@ bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box
 bool tc_uses_pair(int64_t npad, int count) { return count == 0 && npad >= kPairMinN; }
 
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count, int fp16, int allow_pair) {
-  if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0) return false;
+                  int count, int fp16, int pair_mode, int group) {
+  if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0 || group < 1) return false;
   m->fp16 = fp16;
-  m->pair = allow_pair && tc_uses_pair(npad, count);
+  m->pair = count == 0 && (pair_mode < 0 ? tc_uses_pair(npad, count) : pair_mode > 0);
+  m->group = group;
   const uint32_t brows = m->pair ? BN / 2 : BN;
   return make_map(&m->a_hi, a_hi, npad, ld, BM, count, fp16) && make_map(&m->a_lo, a_lo, npad, ld, BM, count, fp16) &&
          make_map(&m->b_hi, bt_hi, npad, ld, brows, count, fp16) &&
@@ -666,7 +668,7 @@ cudaError_t launch_pair(const TcMaps& maps, int64_t npad, const EpiParams& P, cu
   const int pairs = tiles_m * tiles_n < max_pairs ? tiles_m * tiles_n : max_pairs;
   cfg.gridDim = dim3(2 * pairs);
   return cudaLaunchKernelEx(&cfg, k, maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n,
-                            (const int4*)nullptr, 0, P);
+                            maps.group, (const int4*)nullptr, 0, P);
 }
 
 }  // namespace
@@ -687,7 +689,7 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
     const int grid = ntiles < sms ? ntiles : sms;
     auto k = maps.fp16 ? tc_split_gemm_kernel<true, true, false> : tc_split_gemm_kernel<true, false, false>;
     k<<<grid, EpiShape<true, false>::kThreads, EpiShape<true, false>::kSmem, s>>>(
-        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, tiles, ntiles, P);
+        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, 1, tiles, ntiles, P);
     return cudaGetLastError();
   }
   if (maps.pair) return maps.fp16 ? launch_pair<true>(maps, npad, P, s) : launch_pair<false>(maps, npad, P, s);
@@ -695,7 +697,7 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
   auto k = maps.fp16 ? tc_split_gemm_kernel<false, true, false> : tc_split_gemm_kernel<false, false, false>;
   k<<<grid, EpiShape<false, false>::kThreads, EpiShape<false, false>::kSmem, s>>>(
-      maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, nullptr, 0, P);
+      maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, maps.group, nullptr, 0, P);
   return cudaGetLastError();
 }
 

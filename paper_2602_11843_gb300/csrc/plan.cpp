@@ -18,8 +18,10 @@
 
 #include <algorithm>
 #include <map>
-#include <utility>
+#include <mutex>
 #include <new>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -143,6 +145,12 @@ struct neumann_plan_s {
   cudaStream_t last_stream = nullptr;
   std::vector<cudaEvent_t> events;
   int timed = 0;
+  // launch configuration of the tensor-core products, set by the autotuner or
+  // taken from an earlier tuning of the same shape in this process
+  int tune_pair = -1;                    // -1: CTA pairs from padded order 4096; 0 never; 1 always
+  int tune_group = kDefaultRasterGroup;  // row tiles per raster group of a single product
+  int chunk_run = 0;                     // grouped batches: matrices per pass (0: chunk)
+  bool tuned = false;
   // batched
   bool batched = false;
   int count = 0;
@@ -167,6 +175,7 @@ struct neumann_plan_s {
   char* h_tab = nullptr;
   size_t h_tab_bytes = 0;
   cudaEvent_t tab_event = nullptr;
+  int last_chunk_run = 0;
   std::vector<int64_t> last_n;
   std::vector<const void*> last_a;
   std::vector<void*> last_s;
@@ -751,7 +760,7 @@ bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMap
     const SlotBufs& b = p->bufs[op.b];
     if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + b.b_hi, p->ws + b.b_lo, p->npad,
                       p->npad, p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16,
-                      !(p->flags & NEUMANN_FLAG_SINGLE_CTA)))
+                      (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0 : p->tune_pair, p->tune_group))
       return false;
   }
   return true;
@@ -886,8 +895,10 @@ bool batch_aliases(int count, const int64_t* n, const void* const* A, void* cons
 // runs the plan's operations once per chunk.
 int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* const* A, void* const* S,
                  cudaStream_t s) {
-  const bool same = (int)p->last_n.size() == count && std::equal(n, n + count, p->last_n.begin()) &&
-                    std::equal(A, A + count, p->last_a.begin()) && std::equal(S, S + count, p->last_s.begin());
+  const int ck = p->chunk_run > 0 ? p->chunk_run : p->chunk;  // matrices per pass
+  const bool same = (int)p->last_n.size() == count && ck == p->last_chunk_run &&
+                    std::equal(n, n + count, p->last_n.begin()) && std::equal(A, A + count, p->last_a.begin()) &&
+                    std::equal(S, S + count, p->last_s.begin());
   if (!same) {
     if (batch_aliases(count, n, A, S, elem_bytes(p->dt_io))) return NEUMANN_EINVAL;
     std::vector<int> order(count);
@@ -898,8 +909,8 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     std::vector<void*> stab(count);
     std::vector<int4> tc, simt, ew;
     p->chunks.clear();
-    for (int c0 = 0; c0 < count; c0 += p->chunk) {
-      const int cn = count - c0 < p->chunk ? count - c0 : p->chunk;
+    for (int c0 = 0; c0 < count; c0 += ck) {
+      const int cn = count - c0 < ck ? count - c0 : ck;
       neumann_plan_s::Chunk ch{c0, cn, (int)tc.size(), 0, (int)simt.size(), 0, (int)ew.size(), 0};
       for (int j = 0; j < cn; ++j) {
         const int i = order[c0 + j];
@@ -959,6 +970,7 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
         cudaMemcpyAsync(ws + p->off_ew, p->h_tab + o_ew, ew.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
         cudaEventRecord(p->tab_event, s))
       return NEUMANN_ECUDA;
+    p->last_chunk_run = ck;
     p->last_n.assign(n, n + count);
     p->last_a.assign(A, A + count);
     p->last_s.assign(S, S + count);
@@ -978,6 +990,137 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     int rc = run_ops(p, p->ops, p->maps, u, s, (p->flags & NEUMANN_FLAG_TIMING) != 0);
     if (rc) return rc;
   }
+  return NEUMANN_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Launch configurations chosen by timing, kept for the process so that later
+// plans of the same shape start from them: single tensor-core products by
+// (padded order, dtype); grouped batches by (count, max order, k, radix, dtype).
+std::mutex g_tune_mu;
+std::map<std::pair<int64_t, int>, std::pair<int, int>> g_tune_single;
+std::map<std::tuple<int, int64_t, int64_t, int, int>, int> g_tune_batched;
+
+void apply_tuned(neumann_plan_s* p) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (p->batched) {
+    auto it = g_tune_batched.find(std::make_tuple(p->count, p->max_n, p->k, p->radix, p->dtype));
+    if (it != g_tune_batched.end() && it->second <= p->chunk) {
+      p->chunk_run = it->second;
+      p->tuned = true;
+    }
+  } else if (p->path == PATH_TC) {
+    auto it = g_tune_single.find(std::make_pair(p->npad, p->dtype));
+    if (it != g_tune_single.end()) {
+      p->tune_pair = it->second.first;
+      p->tune_group = it->second.second;
+      p->tuned = true;
+    }
+  }
+}
+
+// Median device time (ms) of `reps` back-to-back runs of `run` on stream s,
+// after one untimed run.
+template <typename F>
+int time_runs(F run, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  int rc = run();
+  if (rc) return rc;
+  std::vector<float> t;
+  for (int r = 0; r < reps; ++r) {
+    if (cudaEventRecord(e0, s) != cudaSuccess) return NEUMANN_ECUDA;
+    rc = run();
+    if (rc) return rc;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return NEUMANN_ECUDA;
+    float x = 0.f;
+    if (cudaEventElapsedTime(&x, e0, e1) != cudaSuccess) return NEUMANN_ECUDA;
+    t.push_back(x);
+  }
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return NEUMANN_OK;
+}
+
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok() {
+    return cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  }
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t lds, int reps, cudaStream_t s) {
+  if (p->path != PATH_TC) {  // the SIMT products have one launch shape
+    p->tuned = true;
+    return NEUMANN_OK;
+  }
+  int rc = ensure_workspace(p, s);
+  if (rc) return rc;
+  EventPair ev;
+  if (!ev.ok()) return NEUMANN_ECUDA;
+  std::vector<std::pair<int, int>> cand;
+  for (int pair = 0; pair <= 1; ++pair) {
+    if (pair && (p->flags & NEUMANN_FLAG_SINGLE_CTA)) continue;
+    for (int g : {4, 8, 16}) cand.emplace_back(pair, g);
+  }
+  float best = 0.f;
+  std::pair<int, int> pick = cand[0];
+  for (size_t i = 0; i < cand.size(); ++i) {
+    p->tune_pair = cand[i].first;
+    p->tune_group = cand[i].second;
+    if (!build_maps(p, p->ops, &p->maps) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
+    float ms = 0.f;
+    rc = time_runs([&] { return eval_one(p, A, lda, S, lds, s); }, reps, s, ev.e0, ev.e1, &ms);
+    if (rc) return rc;
+    if (i == 0 || ms < best) {
+      best = ms;
+      pick = cand[i];
+    }
+  }
+  p->tune_pair = pick.first;
+  p->tune_group = pick.second;
+  if (!build_maps(p, p->ops, &p->maps) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
+  p->timed = 0;  // tuning runs are not part of a NEUMANN_FLAG_TIMING record
+  p->tuned = true;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_single[std::make_pair(p->npad, p->dtype)] = pick;
+  return NEUMANN_OK;
+}
+
+int autotune_batched(neumann_plan_s* p, int count, const int64_t* n, const void* const* A, void* const* S, int reps,
+                     cudaStream_t s) {
+  if (!p->grouped) {  // orders above 256: one plan per order, each tuned like a single plan
+    p->tuned = true;
+    return NEUMANN_OK;
+  }
+  int rc = ensure_workspace(p, s);
+  if (rc) return rc;
+  EventPair ev;
+  if (!ev.ok()) return NEUMANN_ECUDA;
+  std::vector<int> cand;
+  for (int c = p->chunk; c >= 64 || c == p->chunk; c /= 2) {
+    cand.push_back(c);
+    if (cand.size() == 6 || c < 2) break;
+  }
+  float best = 0.f;
+  int pick = cand[0];
+  for (size_t i = 0; i < cand.size(); ++i) {
+    p->chunk_run = cand[i];
+    float ms = 0.f;
+    rc = time_runs([&] { return eval_grouped(p, count, n, A, S, s); }, reps, s, ev.e0, ev.e1, &ms);
+    if (rc) return rc;
+    if (i == 0 || ms < best) {
+      best = ms;
+      pick = cand[i];
+    }
+  }
+  p->chunk_run = pick;
+  p->timed = 0;
+  p->tuned = true;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_batched[std::make_tuple(p->count, p->max_n, p->k, p->radix, p->dtype)] = pick;
   return NEUMANN_OK;
 }
 
@@ -1002,6 +1145,7 @@ int neumann_plan_create(neumann_plan_t* out, int64_t n, int64_t k, int radix, in
     delete p;
     return rc;
   }
+  apply_tuned(p);
   *out = p;
   return NEUMANN_OK;
 }
@@ -1023,7 +1167,42 @@ int neumann_plan_info(neumann_plan_t p, neumann_plan_info_t* info) {
   info->launches = (int64_t)p->ops.size();
   info->workspace_bytes = p->ws_bytes;
   info->padded_n = p->npad;
+  if (p->path == PATH_TC && !p->grouped && !p->batched) {
+    info->tile_pair = (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0
+                      : p->tune_pair < 0                  ? (int)tc_uses_pair(p->npad, 0)
+                                                          : p->tune_pair;
+    info->raster_group = p->tune_group;
+  }
+  if (p->grouped) info->batch_chunk = p->chunk_run > 0 ? p->chunk_run : p->chunk;
+  info->tuned = p->tuned;
   return NEUMANN_OK;
+}
+
+int neumann_plan_autotune(neumann_plan_t p, const void* A, int64_t lda, void* S, int64_t lds, int reps,
+                          void* stream) {
+  if (!p || p->batched || !A || !S || lda < p->n || lds < p->n || reps < 1) return NEUMANN_EINVAL;
+  const size_t es = elem_bytes(p->dt_io);
+  if (overlap(A, ((size_t)(p->n - 1) * lda + p->n) * es, S, ((size_t)(p->n - 1) * lds + p->n) * es))
+    return NEUMANN_EINVAL;
+  try {
+    return autotune_one(p, A, lda, S, lds, reps, reinterpret_cast<cudaStream_t>(stream));
+  } catch (...) {
+    return NEUMANN_ENOMEM;
+  }
+}
+
+int neumann_plan_autotune_batched(neumann_plan_t p, int count, const int64_t* n, const void* const* A,
+                                  void* const* S, int reps, void* stream) {
+  if (!p || !p->batched || count < 1 || count > p->count || !n || !A || !S || reps < 1) return NEUMANN_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || n[i] > p->max_n || !A[i] || !S[i]) return NEUMANN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  p->last_stream = s;
+  try {
+    return autotune_batched(p, count, n, A, S, reps, s);
+  } catch (...) {
+    return NEUMANN_ENOMEM;
+  }
 }
 
 int neumann_plan_set_workspace(neumann_plan_t p, void* ws, size_t bytes) {
@@ -1086,6 +1265,7 @@ int neumann_plan_create_batched(neumann_plan_t* out, int count, int64_t max_n, i
       return NEUMANN_ENOMEM;
     }
   }
+  apply_tuned(p);
   *out = p;
   return NEUMANN_OK;
 }

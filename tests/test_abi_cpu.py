@@ -118,3 +118,39 @@ def test_batched_plan_and_empty_batch():
             C.neumann_eval_batched(h, [300], [1], [2])  # n above max_n
     finally:
         C.neumann_plan_destroy(h)
+
+
+def test_launch_configuration_defaults():
+    """Before tuning: CTA pairs from padded order 4096, raster groups of 8, one
+    pass of up to 2048 matrices for a grouped batch."""
+    assert _info(4096, 81, 9, C.SPLIT_BF16)["tile_pair"] == 1
+    assert _info(4000, 81, 9, C.SPLIT_FP16)["tile_pair"] == 1
+    assert _info(3840, 81, 9, C.SPLIT_BF16)["tile_pair"] == 0
+    assert _info(8192, 81, 9, C.SPLIT_BF16, C.FLAG_SINGLE_CTA)["tile_pair"] == 0
+    i = _info(300, 81, 9, C.SPLIT_BF16)
+    assert i["raster_group"] == 8 and i["tuned"] == 0 and i["batch_chunk"] == 0
+    assert _info(4096, 81, 9, C.FP64)["tile_pair"] == 0
+    h = C.neumann_plan_create_batched(3000, 256, 81, 9, C.SPLIT_BF16, 0)
+    try:
+        assert C.neumann_plan_info(h)["batch_chunk"] == 2048
+    finally:
+        C.neumann_plan_destroy(h)
+
+
+def test_autotune_argument_errors():
+    """Rejected before any device work."""
+    h = C.neumann_plan_create(64, 81, 9, C.SPLIT_BF16, 0)
+    hb = C.neumann_plan_create_batched(4, 64, 81, 9, C.SPLIT_BF16, 0)
+    try:
+        for args in [(h, 16, 64, 32, 64, 0), (hb, 16, 64, 32, 64, 3), (h, 16, 63, 32, 64, 3), (h, 0, 64, 32, 64, 3)]:
+            with pytest.raises(C.NeumannError) as e:
+                C.neumann_plan_autotune(*args)
+            assert e.value.code == C.EINVAL
+        for args in [(h, [64], [16], [32], 3), (hb, [65], [16], [32], 3), (hb, [64], [16], [32], 0),
+                     (hb, [64] * 5, [16] * 5, [32] * 5, 3)]:
+            with pytest.raises(C.NeumannError) as e:
+                C.neumann_plan_autotune_batched(*args)
+            assert e.value.code == C.EINVAL
+    finally:
+        C.neumann_plan_destroy(h)
+        C.neumann_plan_destroy(hb)
