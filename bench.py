@@ -362,20 +362,33 @@ def run_batched(args, wl):
     per = info["products_executed"]
     flops_one = sum(2.0 * n ** 3 for n in ns)  # one product over the batch, 2 n^3 per matrix
     mean_prod = statistics.mean(prod_ms) if prod_ms else float("nan")
-    if tc:
-        roof = {"bound": "tensor", "achieved": 3 * flops_one / (mean_prod / 1e3) / 1e12,
-                "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
-                "kernel": "tc_split_gemm_kernel (grouped)", "peak_source": f"bf16_tflops_sustained ({peak_src})",
-                "work_per_launch": "3 x sum 2 n_i^3 BF16 tensor flops"}
-    else:
-        sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        roof = {"bound": "alu", "achieved": flops_one / (mean_prod / 1e3) / 1e12,
-                "peak": 152 * 128 * 2 * sm_hz / 1e12, "unit": "TFLOP/s", "traffic": None,
-                "kernel": "simt_gemm_kernel (grouped)",
-                "peak_source": "derived: 152 SM x 128 lanes x 2 flop x max SM clock",
-                "work_per_launch": "sum 2 n_i^3 FP32 flops"}
+    # The products of orders <= 256 have little arithmetic per byte (about n / 5
+    # tensor flops per byte), so both rooflines are computed and the one that
+    # bounds the product (the longer ideal time) is reported.
+    prod_s = sum(prod_ms) / args.steps / 1e3  # product time per step
+    bytes_step = sum(n * n for n in ns) * info["product_bytes_per_element"]
+    flops_step = per * flops_one * (3 if tc else 1)
+    sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fpeak = peaks["bf16_tflops_sustained"] if tc else 152 * 128 * 2 * sm_hz / 1e12
+    hbm = {"bound": "hbm", "achieved": bytes_step / prod_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "peak_source": f"hbm_gbs ({peak_src})",
+           "work_per_launch": "algorithmic bytes: sum n_i^2 x the product's input, output and operand bytes per "
+                              f"element ({info['product_bytes_per_element']} B over the {per} products)"}
+    alu = {"bound": "tensor" if tc else "alu", "achieved": flops_step / prod_s / 1e12, "peak": fpeak,
+           "unit": "TFLOP/s",
+           "peak_source": f"bf16_tflops_sustained ({peak_src})" if tc else
+                          "derived: 152 SM x 128 lanes x 2 flop x max SM clock",
+           "work_per_launch": "3 x sum 2 n_i^3 BF16 tensor flops" if tc else "sum 2 n_i^3 FP32 flops"}
+    t_hbm = bytes_step / (hbm["peak"] * 1e9)
+    t_alu = flops_step / (alu["peak"] * 1e12)
+    roof = dict(hbm if t_hbm >= t_alu else alu)
+    other = alu if t_hbm >= t_alu else hbm
+    roof["other"] = {"bound": other["bound"], "achieved": other["achieved"], "peak": other["peak"],
+                     "unit": other["unit"], "frac": other["achieved"] / other["peak"]}
+    roof["traffic"] = None
+    roof["kernel"] = "tc_split_gemm_kernel (grouped)" if tc else "simt_gemm_kernel (grouped)"
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["effective_tflops"] = flops_one / (mean_prod / 1e3) / 1e12
+    roof["effective_tflops"] = per * flops_one / prod_s / 1e12
     roof["launches_timed"] = len(prod_ms)
     if prod_ms and per and len(prod_ms) % per == 0:
         reps = len(prod_ms) // per

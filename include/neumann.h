@@ -107,6 +107,11 @@ typedef struct {
   int raster_group;             /* split dtypes, single plans: row tiles per raster group */
   int batch_chunk;              /* grouped batched plans (max_n <= 256): matrices per pass */
   int tuned;                    /* 1 once tuned, by this plan or by an earlier plan of the same shape */
+  /* Algorithmic device-memory bytes per matrix element (x n^2 for one evaluation,
+     x sum n_i^2 for a batch): every input and output representation of every
+     launch read or written once, plus both operands of each product. */
+  int64_t bytes_per_element;          /* all launches of an evaluation */
+  int64_t product_bytes_per_element;  /* the products alone */
 } neumann_plan_info_t;
 
 /* Create a plan for S_k(A) with A n x n. Host-only: no device memory is

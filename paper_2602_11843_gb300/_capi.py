@@ -49,6 +49,7 @@ class PlanInfo(ctypes.Structure):
         ("products_formula", c_int64), ("products_executed", c_int64), ("launches", c_int64),
         ("workspace_bytes", c_size_t), ("padded_n", c_int64),
         ("tile_pair", c_int), ("raster_group", c_int), ("batch_chunk", c_int), ("tuned", c_int),
+        ("bytes_per_element", c_int64), ("product_bytes_per_element", c_int64),
     ]
 
 
@@ -119,7 +120,8 @@ def neumann_plan_info(plan: int) -> dict:
         "products_formula": info.products_formula, "products_executed": info.products_executed,
         "launches": info.launches, "workspace_bytes": info.workspace_bytes, "padded_n": info.padded_n,
         "tile_pair": info.tile_pair, "raster_group": info.raster_group, "batch_chunk": info.batch_chunk,
-        "tuned": info.tuned,
+        "tuned": info.tuned, "bytes_per_element": info.bytes_per_element,
+        "product_bytes_per_element": info.product_bytes_per_element,
     }
 
 

@@ -614,124 +614,146 @@ __device__ __forceinline__ void st8_split(const EpiSplit& sp, const EpiCtx& x, i
   }
 }
 
-template <bool kF16>
-__device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
+// The lean path proper. Rows are taken RB at a time: every input load of the
+// RB rows is issued before any output is formed, so a lane keeps RB x (inputs)
+// loads in flight; the host's input count picks RB (32 rows for one FP32
+// input, 16 for two, or one FP32 and one FP64, 8 otherwise) so that about 32
+// loads per lane are in flight whatever the op. NF: FP32 input slots (the
+// op's FP32 inputs in index order, P.f32_idx); kD: the op may have an FP64 input.
+template <bool kF16, int RB, int NF, bool kD>
+__device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
                                                int lane) {
+  static_assert(RB % 8 == 0 && 32 % RB == 0, "row batch");
   const int fi = P.f64_in;  // the FP64 input, or -1
+  const int nf = P.nf32;    // FP32 inputs (<= NF)
   float chk = 0.f;          // becomes NaN once any output is non-finite
   float amax = 0.f;         // largest |value| split to FP16
 #pragma unroll 1
-  for (int g = 0; g < 4; ++g) {
-    const int r0 = rbase + 8 * g;
-    const bool diag = (unsigned)(c - r0) < 8u;  // this lane's column holds the diagonal in these rows
-    float a8[8];
+  for (int g0 = 0; g0 < 32; g0 += RB) {
+    float fin[NF > 0 ? NF : 1][RB];
+    double din[kD ? RB : 1];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
-    float fin[kMaxIn][8];
-    double din[8];
-#pragma unroll
-    for (int i = 0; i < kMaxIn; ++i) {
-      if (i < P.nin && i != fi) {
+    for (int t = 0; t < NF; ++t) {
+      if (t < nf) {
         int64_t ld;
-        const float* q = in_base<float>(P.in[i], x, &ld) + (int64_t)r0 * ld + c;
+        const float* q = in_base<float>(P.in[P.f32_idx[t]], x, &ld) + (int64_t)(rbase + g0) * ld + c;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) fin[i][w] = q[(int64_t)w * ld];
+        for (int w = 0; w < RB; ++w) fin[t][w] = q[(int64_t)w * ld];
       }
     }
-    if (fi >= 0) {
+    if (kD && fi >= 0) {
       int64_t ld;
-      const double* q = in_base<double>(P.in[fi], x, &ld) + (int64_t)r0 * ld + c;
+      const double* q = in_base<double>(P.in[fi], x, &ld) + (int64_t)(rbase + g0) * ld + c;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) din[w] = q[(int64_t)w * ld];
+      for (int w = 0; w < RB; ++w) din[w] = q[(int64_t)w * ld];
     }
+#pragma unroll
+    for (int h = 0; h < RB; h += 8) {
+      const int r0 = rbase + g0 + h;
+      const bool diag = (unsigned)(c - r0) < 8u;  // this lane's column holds the diagonal in these rows
+      float a8[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) a8[w] = stg[(g0 + h + w) * 33 + lane];
 #pragma unroll 1
-    for (int j = 0; j < P.nout; ++j) {
-      const EpiOut& o = P.out[j];
-      // the same terms in the same order as epi_col
-      float vf[8];
+      for (int j = 0; j < P.nout; ++j) {
+        const EpiOut& o = P.out[j];
+        // the same terms in the same order as epi_col
+        float vf[8];
 #pragma unroll
-      for (int w = 0; w < 8; ++w) vf[w] = o.acc_f * a8[w];
-      if (o.f64) {
-        // FP32 terms summed in FP32; the identity and the FP64 input (a partial
-        // sum Y or residual R) are added in FP64
+        for (int w = 0; w < 8; ++w) vf[w] = o.acc_f * a8[w];
+        if (o.f64) {
+          // FP32 terms summed in FP32; the identity and the FP64 input (a partial
+          // sum Y or residual R) are added in FP64
 #pragma unroll
-        for (int i = 0; i < kMaxIn; ++i) {
-          if (i < P.nin && i != fi && o.in_f[i] != 0.f) {
+          for (int t = 0; t < NF; ++t) {
+            const float cf = t < nf ? o.in_f[P.f32_idx[t]] : 0.f;
+            if (cf != 0.f) {
 #pragma unroll
-            for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[i], fin[i][w], vf[w]);
+              for (int w = 0; w < 8; ++w) vf[w] = fmaf(cf, fin[t][h + w], vf[w]);
+            }
           }
-        }
-        double v[8];
+          double v[8];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) v[w] = (double)vf[w];
-        if (diag) {
+          for (int w = 0; w < 8; ++w) v[w] = (double)vf[w];
+          if (diag) {
 #pragma unroll
-          for (int w = 0; w < 8; ++w)
-            if (r0 + w == c) v[w] += o.id_d;
-        }
-        if (fi >= 0 && o.in_d[fi] != 0.0) {
-#pragma unroll
-          for (int w = 0; w < 8; ++w) v[w] = fma(o.in_d[fi], din[w], v[w]);
-        }
-#pragma unroll
-        for (int w = 0; w < 8; ++w) vf[w] = (float)v[w];
-        for (int d = 0; d < o.ndst; ++d) {
-          const EpiDst& ds = o.dst[d];
-          int64_t ld;
-          if (ds.dt == DT_F64) {
-            double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = v[w];
-          } else {
-            float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+            for (int w = 0; w < 8; ++w)
+              if (r0 + w == c) v[w] += o.id_d;
           }
-        }
-      } else {
-        if (diag) {
+          if (kD && fi >= 0 && o.in_d[fi] != 0.0) {
 #pragma unroll
-          for (int w = 0; w < 8; ++w)
-            if (r0 + w == c) vf[w] += o.id_f;
-        }
+            for (int w = 0; w < 8; ++w) v[w] = fma(o.in_d[fi], din[h + w], v[w]);
+          }
 #pragma unroll
-        for (int i = 0; i < kMaxIn; ++i) {
-          if (i < P.nin && o.in_f[i] != 0.f) {
-            if (i == fi) {
+          for (int w = 0; w < 8; ++w) vf[w] = (float)v[w];
+          for (int d = 0; d < o.ndst; ++d) {
+            const EpiDst& ds = o.dst[d];
+            int64_t ld;
+            if (ds.dt == DT_F64) {
+              double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
 #pragma unroll
-              for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[i], (float)din[w], vf[w]);
+              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = v[w];
             } else {
+              float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
 #pragma unroll
-              for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[i], fin[i][w], vf[w]);
+              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+            }
+          }
+        } else {
+          if (diag) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+              if (r0 + w == c) vf[w] += o.id_f;
+          }
+          // FP32 inputs in index order, then an FP64 input rounded to FP32 (no
+          // op of the schedules pairs an FP64 input with an FP32-only output)
+#pragma unroll
+          for (int t = 0; t < NF; ++t) {
+            const float cf = t < nf ? o.in_f[P.f32_idx[t]] : 0.f;
+            if (cf != 0.f) {
+#pragma unroll
+              for (int w = 0; w < 8; ++w) vf[w] = fmaf(cf, fin[t][h + w], vf[w]);
+            }
+          }
+          if (kD && fi >= 0 && o.in_f[fi] != 0.f) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[fi], (float)din[h + w], vf[w]);
+          }
+          for (int d = 0; d < o.ndst; ++d) {
+            const EpiDst& ds = o.dst[d];
+            int64_t ld;
+            if (ds.dt == DT_F64) {
+              double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = (double)vf[w];
+            } else {
+              float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+#pragma unroll
+              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
             }
           }
         }
-        for (int d = 0; d < o.ndst; ++d) {
-          const EpiDst& ds = o.dst[d];
-          int64_t ld;
-          if (ds.dt == DT_F64) {
-            double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = (double)vf[w];
-          } else {
-            float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+        for (int w = 0; w < 8; ++w) chk = fmaf(vf[w], 0.f, chk);
+        if (o.nsplit) {
+          if (kF16) {
 #pragma unroll
-            for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+            for (int w = 0; w < 8; ++w) amax = fmaxf(amax, fabsf(vf[w]));
           }
+          for (int s2 = 0; s2 < o.nsplit; ++s2) st8_split<kF16>(o.split[s2], x, r0, c, vf);
         }
-      }
-#pragma unroll
-      for (int w = 0; w < 8; ++w) chk = fmaf(vf[w], 0.f, chk);
-      if (o.nsplit) {
-        if (kF16) {
-#pragma unroll
-          for (int w = 0; w < 8; ++w) amax = fmaxf(amax, fabsf(vf[w]));
-        }
-        for (int s2 = 0; s2 < o.nsplit; ++s2) st8_split<kF16>(o.split[s2], x, r0, c, vf);
       }
     }
   }
   return chk != chk || (kF16 && !(amax * kFp16SplitScale < 65504.f));
+}
+
+template <bool kF16>
+__device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
+                                               int lane) {
+  if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane);
+  if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane);
+  return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane);
 }
 
 // Boundary chunks (padding, ragged edges, grouped row limits) and ops with

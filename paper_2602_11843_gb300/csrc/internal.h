@@ -85,8 +85,11 @@ struct EpiParams {
   int64_t mat_stride;
   // Set by the host for ops with at most one FP64 input (f64_in, else -1):
   // the tensor-core epilogue may take its lean path on interior chunks.
+  // f32_idx[0 .. nf32-1]: the FP32 inputs in index order.
   int fast;
   int f64_in;
+  int nf32;
+  int f32_idx[kMaxIn];
 };
 
 // Split-operand tensor maps of one tensor-core product C = A B:

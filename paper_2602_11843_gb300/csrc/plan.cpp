@@ -743,12 +743,45 @@ void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiPa
   // the tensor-core epilogue's lean path handles at most one FP64 input
   int nf64 = 0;
   P->f64_in = -1;
-  for (int i = 0; i < op.nin; ++i)
+  P->nf32 = 0;
+  for (int i = 0; i < op.nin; ++i) {
     if (P->in[i].dt == DT_F64) {
       ++nf64;
       P->f64_in = i;
+    } else {
+      P->f32_idx[P->nf32++] = i;
     }
+  }
   P->fast = nf64 <= 1;
+}
+
+// Algorithmic device-memory bytes of one op per matrix element: each input
+// and each output representation read or written once, plus the two operands
+// of a product (hi/lo pairs on the tensor-core path). Mirrors resolve_in /
+// resolve_out.
+int64_t op_bytes(const neumann_plan_s* p, const Op& op) {
+  const int64_t io = elem_bytes(p->dt_io);
+  const int64_t w = p->path == PATH_F64 ? 8 : 4;
+  int64_t b = 0;
+  for (int i = 0; i < op.nin; ++i) {
+    const InRef& r = op.in[i];
+    b += r.slot == SL_USER_A || r.slot == SL_USER_B ? io : (r.rep & REP_F64) ? 8 : w;
+  }
+  for (int j = 0; j < op.nout; ++j) {
+    const OutSpec& o = op.out[j];
+    if (o.slot == SL_USER_S) {
+      b += io;
+    } else if (p->path == PATH_F64) {
+      b += 8;
+    } else if (p->path == PATH_F32) {
+      b += ((o.reps & (REP_W | REP_OPA | REP_OPB)) ? 4 : 0) + ((o.reps & REP_F64) ? 8 : 0);
+    } else {
+      b += ((o.reps & REP_W) ? 4 : 0) + ((o.reps & REP_F64) ? 8 : 0) + ((o.reps & REP_OPA) ? 4 : 0) +
+           ((o.reps & REP_OPB) ? 4 : 0);
+    }
+  }
+  if (op.kind == OP_GEMM) b += p->path == PATH_TC ? 8 : 2 * w;
+  return b;
 }
 
 bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMaps>* maps) {
@@ -1175,6 +1208,11 @@ int neumann_plan_info(neumann_plan_t p, neumann_plan_info_t* info) {
   }
   if (p->grouped) info->batch_chunk = p->chunk_run > 0 ? p->chunk_run : p->chunk;
   info->tuned = p->tuned;
+  for (const Op& op : p->ops) {
+    const int64_t b = op_bytes(p, op);
+    info->bytes_per_element += b;
+    if (op.kind == OP_GEMM) info->product_bytes_per_element += b;
+  }
   return NEUMANN_OK;
 }
 

@@ -154,3 +154,17 @@ def test_autotune_argument_errors():
     finally:
         C.neumann_plan_destroy(h)
         C.neumann_plan_destroy(hb)
+
+
+def test_algorithmic_bytes_per_element():
+    """The plan's byte count per matrix element grows with the work: more levels
+    move more bytes, the products are most of them, and FP64 moves the most."""
+    b9 = _info(512, 81, 9, C.SPLIT_BF16)
+    b9x = _info(512, 729, 9, C.SPLIT_BF16)
+    assert 0 < b9["product_bytes_per_element"] < b9["bytes_per_element"]
+    assert b9x["bytes_per_element"] > b9["bytes_per_element"]
+    # per product, between the bare operands (8 B of hi/lo pairs) and operands plus
+    # four inputs and four outputs in every representation
+    per = b9["product_bytes_per_element"] / b9["products_executed"]
+    assert 8 < per < 8 + 4 * 8 + 4 * 20
+    assert _info(512, 81, 9, C.FP64)["bytes_per_element"] > _info(512, 81, 9, C.FP32)["bytes_per_element"]
