@@ -7,6 +7,8 @@
 // matrices are padded to a multiple of 256 in both dimensions and every
 // epilogue rewrites the padding with zeros, so the main loop has no bounds
 // checks.
+#include <mutex>
+
 #include "epilogue.cuh"
 
 namespace neumann {
@@ -29,12 +31,15 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
 // (tm, tn) over `ktiles` K steps. Otherwise (grouped launch over a batch) CTA b
 // computes tiles[b] = {matrix, tm, tn, K steps}; every operand and workspace
 // buffer then holds matrix m at element offset m * P.mat_stride.
+// FP32 keeps its running sums in shared memory (see below), so two CTAs fit
+// per SM; FP64 is bound by the FP64 pipe and keeps them in registers.
 template <typename T>
-__global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B,
-                                                        int64_t ld, int ktiles, const int4* __restrict__ tiles,
-                                                        const __grid_constant__ EpiParams P) {
+__global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
+    simt_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, int64_t ld, int ktiles,
+                     const int4* __restrict__ tiles, const __grid_constant__ EpiParams P) {
   __shared__ __align__(16) T As[2][BK][BM + 4];
   __shared__ __align__(16) T Bs[2][BK][BN];
+  extern __shared__ float acc_smem[];  // FP32: running sums, [64][TPB] (element e of thread t at e * TPB + t)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   int mat = 0, tm = blockIdx.y, tn = blockIdx.x;
@@ -65,15 +70,23 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
   __syncthreads();
 
   // FP32: two-level accumulation. Products are summed into `part` for 64
-  // consecutive k and then added to `acc`, so each rounding error grows with
-  // sqrt(64) + sqrt(K/64) instead of sqrt(K) (K = 4096: 16 vs 64 units).
+  // consecutive k and then added to the running sum, so each rounding error
+  // grows with sqrt(64) + sqrt(K/64) instead of sqrt(K) (K = 4096: 16 vs 64
+  // units). The running sums live in shared memory (touched once per 64 k),
+  // which keeps the kernel within 128 registers.
   constexpr bool kTwoLevel = sizeof(T) == 4;
   constexpr int kFlush = 64 / BK;  // k tiles per partial sum
-  T acc[8][8], part[8][8];
+  T acc[kTwoLevel ? 1 : 8][kTwoLevel ? 1 : 8], part[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = part[i][j] = T(0);
+    for (int j = 0; j < 8; ++j) {
+      part[i][j] = T(0);
+      if constexpr (kTwoLevel)
+        acc_smem[(i * 8 + j) * TPB + tid] = 0.f;
+      else
+        acc[i][j] = T(0);
+    }
 
   for (int kt = 0; kt < ktiles; ++kt) {
     const int cur = kt & 1;
@@ -102,20 +115,22 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          if (kTwoLevel)
+          if constexpr (kTwoLevel)
             part[i][j] = fma(a[i], b[j], part[i][j]);
           else
             acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
     }
-    if (kTwoLevel && ((kt + 1) % kFlush == 0 || !more)) {
+    if constexpr (kTwoLevel) {
+      if ((kt + 1) % kFlush == 0 || !more) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          acc[i][j] += part[i][j];
-          part[i][j] = T(0);
-        }
+          for (int j = 0; j < 8; ++j) {
+            acc_smem[(i * 8 + j) * TPB + tid] += part[i][j];
+            part[i][j] = T(0);
+          }
+      }
     }
     if (more) {
 #pragma unroll
@@ -138,7 +153,14 @@ __global__ void __launch_bounds__(TPB) simt_gemm_kernel(const T* __restrict__ A,
     for (int h = 0; h < 2; ++h) {
       const int c0 = n0 + h * 64 + tx * 4;
       if (r >= lim || c0 >= lim) continue;
-      const T(&a4)[4] = *reinterpret_cast<const T(*)[4]>(&acc[i][4 * h]);
+      T a4[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if constexpr (kTwoLevel)
+          a4[j] = acc_smem[(i * 8 + 4 * h + j) * TPB + tid];
+        else
+          a4[j] = acc[i][4 * h + j];
+      }
       bad |= epi_row<4, T, false>(P, x, r, c0, a4);
     }
   }
@@ -196,12 +218,22 @@ template <typename T>
 cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const int4* tiles, int ntiles,
                         const EpiParams& P, cudaStream_t s) {
   if (npad % BM != 0 || npad % BN != 0 || ld < npad) return cudaErrorInvalidValue;
+  // FP32: 64 running sums per thread in dynamic shared memory (64 KB)
+  constexpr size_t dyn = sizeof(T) == 4 ? 64 * TPB * sizeof(float) : 0;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  if (dyn) {
+    std::call_once(once, [] {
+      attr = cudaFuncSetAttribute(simt_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    });
+    if (attr != cudaSuccess) return attr;
+  }
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
-    simt_gemm_kernel<T><<<ntiles, TPB, 0, s>>>(A, B, ld, 0, tiles, P);
+    simt_gemm_kernel<T><<<ntiles, TPB, dyn, s>>>(A, B, ld, 0, tiles, P);
   } else {
     dim3 grid((unsigned)(npad / BN), (unsigned)(npad / BM));
-    simt_gemm_kernel<T><<<grid, TPB, 0, s>>>(A, B, ld, (int)(npad / BK), nullptr, P);
+    simt_gemm_kernel<T><<<grid, TPB, dyn, s>>>(A, B, ld, (int)(npad / BK), nullptr, P);
   }
   return cudaGetLastError();
 }

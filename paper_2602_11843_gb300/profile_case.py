@@ -2,9 +2,11 @@
 
   python -m paper_2602_11843_gb300.profile_case matmul N REPS   split-BF16 product C = A B
   python -m paper_2602_11843_gb300.profile_case r15 N REPS      radix-15, k = 3375, split-BF16
+  python -m paper_2602_11843_gb300.profile_case batched N REPS  512 matrices of order N, radix 9,
+                                                                k = 81, split-BF16, one grouped pass
 
 Inputs are drawn on the device (no host copies): A, B ~ N(0, 1) for the
-product; for r15 a symmetric A with spectral radius about 0.45. Prints the
+product; for r15 and batched symmetric matrices with spectral radius about 0.45. Prints the
 plan's device status at the end; exits non-zero if it is not 0.
 """
 
@@ -34,6 +36,14 @@ def main(argv):
         S = torch.empty_like(A)
         for _ in range(reps):
             p(A, out=S)
+    elif mode == "batched":
+        count = 512
+        X = torch.randn((count, n, n), dtype=torch.float64, device="cuda", generator=g)
+        As = list((X + X.transpose(1, 2)) * (0.45 / (2.0 * n ** 0.5)))
+        outs = [torch.empty_like(a) for a in As]
+        p = nm.BatchedPlan(count, n, 81, 9, "split_bf16")
+        for _ in range(reps):
+            p(As, outs)
     else:
         raise SystemExit(f"unknown case {mode}")
     torch.cuda.synchronize()
