@@ -36,6 +36,10 @@ WORKLOADS = {
     "precision-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096),
     "precision-r9-bf16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_bf16", sq_k=8192),
     "precision-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096),
+    "precise-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
+                                         precise=True),
+    "precise-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096,
+                                         precise=True),
     "precision-r9-fp16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_fp16", sq_k=8192),
     # cfg 5: n = 16384, planted spectrum U[-0.95, 0.95] + rank-32 nonsymmetric term of norm 0.01;
     # the FP64 comparison (about two minutes at this size) runs only with --fp64-large
@@ -460,7 +464,8 @@ def run_ours(args, wl):
     inp = make_input(wl, rank)
     A_np = np.asarray(inp["A"], dtype=np.float64)
     n, k = wl["n"], wl["k"]
-    plan = nm.Plan(n, k, wl["radix"], wl["dtype"], nm.FLAG_TIMING)
+    pflags = nm.FLAG_PRECISE_ACC if wl.get("precise") else 0
+    plan = nm.Plan(n, k, wl["radix"], wl["dtype"], nm.FLAG_TIMING | pflags)
     io = plan.io_dtype
     A = torch.tensor(A_np, dtype=io, device=dev)
     S = torch.empty_like(A)
@@ -495,7 +500,7 @@ def run_ours(args, wl):
     value = job_value(1, args.steps, world, ms_max)
 
     # repeated squaring on the same input and arithmetic (the paper's binary comparator)
-    sq = nm.Plan(n, wl["sq_k"], 2, wl["dtype"])
+    sq = nm.Plan(n, wl["sq_k"], 2, wl["dtype"], pflags)
     for _ in range(args.warmup):
         sq(A, out=S)
     torch.cuda.synchronize()
@@ -585,12 +590,14 @@ def run_ours(args, wl):
         "dtype": {"split_bf16": "bf16", "split_fp16": "f16", "fp32": "f32", "fp64": "f64"}[wl["dtype"]],
         "precision": {"split_bf16": "hi+lo BF16 operands, 3 products, FP32 accumulate, FP64 Y and R",
                       "split_fp16": "hi+lo FP16 operands of x*2^8, 3 products, FP32 accumulate, FP64 Y and R",
-                      "fp32": "FP32 products, FP64 Y and R", "fp64": "FP64"}[wl["dtype"]],
+                      "fp32": "FP32 products, FP64 Y and R", "fp64": "FP64"}[wl["dtype"]]
+                     + ("; K accumulated in chunks of 512 summed with round-to-nearest" if pflags else ""),
         "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "k": k, "radix": wl["radix"], "scheme": wl["dtype"],
                    "products_per_step": info["products_executed"], "products_formula": info["products_formula"],
                    "l2": "inputs larger than L2 (A, S and every workspace matrix exceed 129 MB)",
                    "tiles": None if wl["dtype"] in ("fp32", "fp64") else
+                            "2-CTA 256x128, chunked accumulation" if pflags else
                             ("2-CTA 256x256" if info["tile_pair"] else "1-CTA 128x256"),
                    "raster_group": info["raster_group"] or None, "autotuned": bool(info["tuned"]),
                    "parallelism": f"replicas x{world}"},

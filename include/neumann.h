@@ -85,6 +85,12 @@ typedef enum {
 #define NEUMANN_FLAG_IO_FP32 0x10u        /* split dtypes: A and S are float instead of double */
 #define NEUMANN_FLAG_SINGLE_CTA 0x20u     /* split dtypes: keep every product on single-CTA 128 x 256 tiles
                                              (by default padded orders >= 4096 use 2-CTA 256 x 256 tiles) */
+#define NEUMANN_FLAG_PRECISE_ACC 0x40u    /* split dtypes: products accumulate K in chunks of 512, each chunk
+                                             added to the running FP32 sum with round-to-nearest. The tensor
+                                             cores' accumulator rounds every update toward zero, a bias of about
+                                             (3K/16)/4 ulp over a K-long sum; chunking bounds the truncated chain
+                                             to 96 updates. 2-CTA 256 x 128 tiles; slower. Single plans only
+                                             (a grouped batch's K is at most 256) */
 
 #define NEUMANN_MAX_LEVELS 64
 

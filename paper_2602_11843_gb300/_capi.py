@@ -32,6 +32,7 @@ FLAG_PRINTED_COEFFS = 0x4
 FLAG_TIMING = 0x8
 FLAG_IO_FP32 = 0x10
 FLAG_SINGLE_CTA = 0x20
+FLAG_PRECISE_ACC = 0x40
 
 MAX_LEVELS = 64
 

@@ -98,11 +98,14 @@ struct EpiParams {
 // pair: the product runs on 2-CTA clusters (256 x 256 tiles; each CTA loads
 // 128 rows of the stored B^T, so the B maps have 128-row boxes).
 // group: row tiles per group of the grouped raster of a single product.
+// precise: K accumulated in chunks summed with round-to-nearest (256 x 128
+// tiles on CTA pairs; the B maps have 64-row boxes).
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
   int fp16;
   int pair;
   int group;
+  int precise;
 };
 
 constexpr int kDefaultRasterGroup = 8;
@@ -125,7 +128,8 @@ cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles =
 // pair_mode: -1 CTA pairs where tc_uses_pair says so, 0 never, 1 always (single
 // products only). group: row tiles per raster group (>= 1).
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count = 0, int fp16 = 0, int pair_mode = -1, int group = kDefaultRasterGroup);
+                  int count = 0, int fp16 = 0, int pair_mode = -1, int group = kDefaultRasterGroup,
+                  int precise = 0);
 // Whether a product of padded order npad (count = 0: single matrix) runs on CTA pairs.
 bool tc_uses_pair(int64_t npad, int count);
 // tiles == nullptr: one npad x npad product. Otherwise a grouped launch over a

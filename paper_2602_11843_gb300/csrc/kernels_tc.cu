@@ -553,6 +553,301 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Precise accumulation (NEUMANN_FLAG_PRECISE_ACC). The tensor cores' FP32
+// accumulator rounds each MMA update toward zero; over the 3K/16 updates of a
+// long K loop that leaves a bias of about (3K/16)/4 ulp of the sum, which at
+// K = 8192 is larger than the operand split error. Here K is taken in chunks
+// of 512: chunk 0 of a tile accumulates in TMEM region S, every later chunk in
+// a fresh region X, and drain warps add X into S with round-to-nearest FP32
+// adds, so the truncated chain is 96 updates long whatever K is.
+//   tile      256 x 128 on a CTA pair (cta_group::2, M = 256, N = 128); each
+//             CTA loads its 128 rows of A and 64 of the 128 rows of the stored B^T
+//   TMEM      X0 [0,128), X1 [128,256): chunk accumulators, alternating by chunk;
+//             S0 [256,384), S1 [384,512): tile sums, alternating by tile
+//   warps     0 TMA; 1 MMA (even CTA); 2-5 drain (one per TMEM lane quarter);
+//             6-7 idle; 8-15 epilogue (two per lane quarter), as in the main kernel
+//   registers the TMA / MMA / drain warpgroups give back registers
+//             (setmaxnreg 56) to the two epilogue warpgroups (200):
+//             2 x 128 x 56 + 2 x 128 x 200 = 65536 = 512 threads x 128 at launch
+constexpr int PQ_N = 128;                                // tile columns
+constexpr int PQ_BROWS = PQ_N / 2;                       // stored B^T rows per CTA
+constexpr uint32_t PQ_BTILE = PQ_BROWS * BK * 2;         // 4 KiB
+constexpr uint32_t PQ_STAGE = 2 * A_TILE + 2 * PQ_BTILE;  // 24 KiB
+constexpr int PQ_STAGES = 8;
+constexpr int PQ_KC = 16;  // 32-deep stages per K chunk (512)
+constexpr int PQ_THREADS = 512;
+constexpr int PQ_EPI_WARPS = 8;
+constexpr uint32_t PQ_SMEM = PQ_STAGES * PQ_STAGE + 256 + PQ_EPI_WARPS * STG_FLOATS * 4 + 1024;
+constexpr uint32_t PQ_X = 0, PQ_S = 256;  // TMEM column bases
+
+__host__ __device__ constexpr uint32_t make_idesc_mn(bool f16, int m, int n) {
+  return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+template <bool kF16>
+__global__ void __launch_bounds__(PQ_THREADS, 1)
+    tc_precise_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
+                      const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
+                      int ktiles, int tiles_m, int tiles_n, int group, const __grid_constant__ EpiParams P) {
+  constexpr uint32_t idesc = make_idesc_mn(kF16, 2 * BM, PQ_N);
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // barriers: full[8], empty[8], xfull[2], xempty[2], sfull[2], sempty[2], drain
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + PQ_STAGES * PQ_STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * PQ_STAGES + 9);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = tiles_m * tiles_n;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int first = (int)cluster_index(), stride = (int)cluster_count();
+  const int nchunks = (ktiles + PQ_KC - 1) / PQ_KC;
+  const uint32_t smem_base = smem_u32(smem);
+  const uint32_t bar_base = smem_u32(bars);
+  auto full_bar = [&](uint32_t i) { return bar_base + 8u * i; };
+  auto empty_bar = [&](uint32_t i) { return bar_base + 8u * (PQ_STAGES + i); };
+  auto xfull_bar = [&](uint32_t b) { return bar_base + 8u * (2 * PQ_STAGES + b); };
+  auto xempty_bar = [&](uint32_t b) { return bar_base + 8u * (2 * PQ_STAGES + 2 + b); };
+  auto sfull_bar = [&](uint32_t b) { return bar_base + 8u * (2 * PQ_STAGES + 4 + b); };
+  auto sempty_bar = [&](uint32_t b) { return bar_base + 8u * (2 * PQ_STAGES + 6 + b); };
+  const uint32_t drain_bar = bar_base + 8u * (2 * PQ_STAGES + 8);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < PQ_STAGES; ++i) {
+      mbar_init(full_bar(i), 1);
+      mbar_init(empty_bar(i), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(xfull_bar(b), 1);
+      mbar_init(xempty_bar(b), 4 * 2);  // the drain warps of both CTAs (the even CTA's is used)
+      // the MMA commit, and this CTA's drain warps when there is anything to drain
+      mbar_init(sfull_bar(b), nchunks > 1 ? 1 + 4 : 1);
+      mbar_init(sempty_bar(b), PQ_EPI_WARPS * 2);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc<true>(smem_u32(tmem_slot), TMEM_COLS);
+  tc_fence_before();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lead_bar_base = cluster_addr(bar_base, 0);
+
+  if (warp >= 8) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 200;" ::: "memory");
+    // ---------------- epilogue (warps 8 .. 15) ----------------
+    const int q = warp & 3;
+    const int half = (warp - 8) >> 2;
+    float* stg = reinterpret_cast<float*>(smem + PQ_STAGES * PQ_STAGE + 256) + (warp - 8) * STG_FLOATS;
+    bool bad = false;
+    int it = 0;
+    for (int tile = first; tile < ntiles; tile += stride, ++it) {
+      const uint32_t sb = it & 1;
+      const uint32_t su = (uint32_t)it >> 1;
+      const bool got = mbar_wait(sfull_bar(sb), su & 1u);
+      if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      int tm, tn;
+      raster(tile, tiles_m, tiles_n, group, &tm, &tn);
+      const EpiCtx x = epi_ctx(P, 0);
+      const int rbase = tm * 2 * BM + (int)rank * BM + q * 32;
+      const uint32_t taddr = tmem + PQ_S + sb * PQ_N + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int chunk = half; chunk < PQ_N / 32; chunk += 2) {
+        uint32_t v[32];
+        __syncwarp();
+        tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = __uint_as_float(v[i]);
+        __syncwarp();
+        bad |= epi_chunk<kF16>(P, x, rbase, tn * PQ_N + chunk * 32 + lane, stg, lane, 1 << 30);
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(lead_bar_base + 8u * (2 * PQ_STAGES + 6 + sb));
+    }
+    epi_flag(P, bad);
+  } else {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      uint32_t kg = 0;
+      bool ok = true;
+      for (int tile = first; tile < ntiles && ok; tile += stride) {
+        int tm, tn;
+        raster(tile, tiles_m, tiles_n, group, &tm, &tn);
+        const int ra = tm * 2 * BM + (int)rank * BM;
+        const int rb = tn * PQ_N + (int)rank * PQ_BROWS;
+        for (int kb = 0; kb < ktiles; ++kb) {
+          const uint32_t st = kg % PQ_STAGES;
+          const uint32_t ph = (kg / PQ_STAGES) & 1u;
+          if (kg >= PQ_STAGES && (!mbar_wait(empty_bar(st), ph ^ 1u) || *abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = smem_base + st * PQ_STAGE;
+          if (leader) mbar_expect_tx(full_bar(st), 2 * PQ_STAGE);
+          const uint32_t fb = lead_bar_base + 8u * st;
+          tma_load_2d_pair(sa, &tm_ahi, fb, kb * BK, ra);
+          tma_load_2d_pair(sa + A_TILE, &tm_alo, fb, kb * BK, ra);
+          tma_load_2d_pair(sa + 2 * A_TILE, &tm_bhi, fb, kb * BK, rb);
+          tma_load_2d_pair(sa + 2 * A_TILE + PQ_BTILE, &tm_blo, fb, kb * BK, rb);
+          ++kg;
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (leader) {
+          for (uint32_t q = (kg > PQ_STAGES ? kg - PQ_STAGES : 0); q < kg; ++q)
+            mbar_wait(full_bar(q % PQ_STAGES), (q / PQ_STAGES) & 1u, 10000000ull);
+        } else {
+          spin_ns(10000000ull);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      // ---------------- MMA issuer ----------------
+      uint32_t kg = 0, cc = 0;
+      bool ok = true;
+      int it = 0;
+      for (int tile = first; tile < ntiles && ok; tile += stride, ++it) {
+        const uint32_t sb = it & 1;
+        const uint32_t su = (uint32_t)it >> 1;
+        if (it >= 2 && (!mbar_wait(sempty_bar(sb), (su - 1) & 1u) || *abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int j = 0; j < nchunks && ok; ++j) {
+          uint32_t d = tmem + PQ_S + sb * PQ_N;  // chunk 0 accumulates in the tile sum itself
+          uint32_t xb = 0;
+          if (j > 0) {
+            xb = cc & 1;
+            const uint32_t xu = cc >> 1;
+            if (cc >= 2 && (!mbar_wait(xempty_bar(xb), (xu - 1) & 1u) || *abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            d = tmem + PQ_X + xb * PQ_N;
+          }
+          const int k1 = min(ktiles, (j + 1) * PQ_KC);
+          for (int kb = j * PQ_KC; kb < k1; ++kb) {
+            const uint32_t st = kg % PQ_STAGES;
+            const uint32_t ph = (kg / PQ_STAGES) & 1u;
+            if (!mbar_wait(full_bar(st), ph) || *abort_flag) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_base + st * PQ_STAGE;
+#pragma unroll
+            for (int q = 0; q < BK / 16; ++q) {
+              const uint64_t a_hi = smem_desc(sa + 32u * q);
+              const uint64_t a_lo = smem_desc(sa + A_TILE + 32u * q);
+              const uint64_t b_hi = smem_desc(sa + 2 * A_TILE + 32u * q);
+              const uint64_t b_lo = smem_desc(sa + 2 * A_TILE + PQ_BTILE + 32u * q);
+              umma_f16<true>(d, a_hi, b_hi, idesc, (kb != j * PQ_KC || q != 0) ? 1u : 0u);
+              umma_f16<true>(d, a_hi, b_lo, idesc, 1u);
+              umma_f16<true>(d, a_lo, b_hi, idesc, 1u);
+            }
+            umma_commit<true>(empty_bar(st));
+            ++kg;
+          }
+          if (ok && j > 0) {
+            umma_commit<true>(xfull_bar(xb));  // chunk j is in X[xb] in both CTAs
+            ++cc;
+          }
+        }
+        if (ok) umma_commit<true>(sfull_bar(sb));  // every MMA of the tile has completed
+      }
+      if (!ok) *abort_flag = 1;
+      umma_commit<true>(drain_bar, false);
+      mbar_wait(drain_bar, 0);
+    }
+  } else if (warp < 6) {
+    // ---------------- drain: S += X, FP32 round to nearest ----------------
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    uint32_t cc = 0;
+    int it = 0;
+    bool ok = true;
+    for (int tile = first; tile < ntiles && ok; tile += stride, ++it) {
+      const uint32_t sb = it & 1;
+      for (int j = 1; j < nchunks; ++j) {
+        const uint32_t xb = cc & 1;
+        const bool got = mbar_wait(xfull_bar(xb), (cc >> 1) & 1u);
+        if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t xa = tmem + lane_off + PQ_X + xb * PQ_N;
+        const uint32_t sa = tmem + lane_off + PQ_S + sb * PQ_N;
+#pragma unroll 1
+        for (int piece = 0; piece < PQ_N / 16; ++piece) {
+          uint32_t xv[16], sv[16];
+          tmem_ld16(xa + piece * 16, xv);
+          tmem_ld16(sa + piece * 16, sv);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int i = 0; i < 16; ++i) sv[i] = __float_as_uint(__uint_as_float(sv[i]) + __uint_as_float(xv[i]));
+          tmem_st16(sa + piece * 16, sv);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(lead_bar_base + 8u * (2 * PQ_STAGES + 2 + xb));
+        ++cc;
+      }
+      if (!ok) break;
+      if (nchunks > 1) {  // with one chunk the tile sum is the MMA's own result
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(sfull_bar(sb));
+      }
+    }
+  }
+  }
+
+  tc_fence_before();
+  cluster_sync();
+  if (threadIdx.x == 0 && *abort_flag && P.status) atomicOr(P.status, 2u);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_free<true>(tmem, TMEM_COLS);
+  }
+}
+
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing
 // arrives on, with the product kernel's wait code and a caller-given limit, and
 // reports the expiry through the status word exactly as the product does.
@@ -602,12 +897,13 @@ bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box
 bool tc_uses_pair(int64_t npad, int count) { return count == 0 && npad >= kPairMinN; }
 
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count, int fp16, int pair_mode, int group) {
+                  int count, int fp16, int pair_mode, int group, int precise) {
   if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0 || group < 1) return false;
   m->fp16 = fp16;
-  m->pair = count == 0 && (pair_mode < 0 ? tc_uses_pair(npad, count) : pair_mode > 0);
+  m->precise = precise && count == 0;
+  m->pair = count == 0 && (m->precise || (pair_mode < 0 ? tc_uses_pair(npad, count) : pair_mode > 0));
   m->group = group;
-  const uint32_t brows = m->pair ? BN / 2 : BN;
+  const uint32_t brows = m->precise ? PQ_BROWS : m->pair ? BN / 2 : BN;
   return make_map(&m->a_hi, a_hi, npad, ld, BM, count, fp16) && make_map(&m->a_lo, a_lo, npad, ld, BM, count, fp16) &&
          make_map(&m->b_hi, bt_hi, npad, ld, brows, count, fp16) &&
          make_map(&m->b_lo, bt_lo, npad, ld, brows, count, fp16);
@@ -671,6 +967,42 @@ cudaError_t launch_pair(const TcMaps& maps, int64_t npad, const EpiParams& P, cu
                             maps.group, (const int4*)nullptr, 0, P);
 }
 
+template <bool kF16>
+cudaError_t launch_precise(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s) {
+  auto k = tc_precise_kernel<kF16>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PQ_SMEM);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  const int tiles_m = (int)(npad / (2 * BM)), tiles_n = (int)(npad / PQ_N);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(PQ_THREADS);
+  cfg.dynamicSmemBytes = PQ_SMEM;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  static int max_pairs = 0;
+  if (max_pairs == 0) {
+    cfg.gridDim = dim3(2 * tiles_m * tiles_n);
+    int nc = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, k, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nc <= 0) return cudaErrorInvalidConfiguration;
+    max_pairs = nc;
+  }
+  const int pairs = tiles_m * tiles_n < max_pairs ? tiles_m * tiles_n : max_pairs;
+  cfg.gridDim = dim3(2 * pairs);
+  return cudaLaunchKernelEx(&cfg, k, maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n,
+                            maps.group, P);
+}
+
 }  // namespace
 
 cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s,
@@ -692,6 +1024,8 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
         maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, 1, tiles, ntiles, P);
     return cudaGetLastError();
   }
+  if (maps.precise)
+    return maps.fp16 ? launch_precise<true>(maps, npad, P, s) : launch_precise<false>(maps, npad, P, s);
   if (maps.pair) return maps.fp16 ? launch_pair<true>(maps, npad, P, s) : launch_pair<false>(maps, npad, P, s);
   const int tiles_m = (int)(npad / BM), tiles_n = (int)(npad / BN);
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;

@@ -793,7 +793,8 @@ bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMap
     const SlotBufs& b = p->bufs[op.b];
     if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + b.b_hi, p->ws + b.b_lo, p->npad,
                       p->npad, p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16,
-                      (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0 : p->tune_pair, p->tune_group))
+                      (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0 : p->tune_pair, p->tune_group,
+                      (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0))
       return false;
   }
   return true;
@@ -1034,6 +1035,12 @@ std::mutex g_tune_mu;
 std::map<std::pair<int64_t, int>, std::pair<int, int>> g_tune_single;
 std::map<std::tuple<int, int64_t, int64_t, int, int>, int> g_tune_batched;
 
+// Single products are keyed by padded order and dtype; precise-accumulation
+// plans run another kernel and are keyed apart.
+std::pair<int64_t, int> tune_key(const neumann_plan_s* p) {
+  return std::make_pair(p->npad, p->dtype + ((p->flags & NEUMANN_FLAG_PRECISE_ACC) ? 16 : 0));
+}
+
 void apply_tuned(neumann_plan_s* p) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (p->batched) {
@@ -1043,7 +1050,7 @@ void apply_tuned(neumann_plan_s* p) {
       p->tuned = true;
     }
   } else if (p->path == PATH_TC) {
-    auto it = g_tune_single.find(std::make_pair(p->npad, p->dtype));
+    auto it = g_tune_single.find(tune_key(p));
     if (it != g_tune_single.end()) {
       p->tune_pair = it->second.first;
       p->tune_group = it->second.second;
@@ -1094,8 +1101,9 @@ int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t
   EventPair ev;
   if (!ev.ok()) return NEUMANN_ECUDA;
   std::vector<std::pair<int, int>> cand;
-  for (int pair = 0; pair <= 1; ++pair) {
-    if (pair && (p->flags & NEUMANN_FLAG_SINGLE_CTA)) continue;
+  const bool precise = (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0;  // always CTA pairs
+  for (int pair = precise ? 1 : 0; pair <= 1; ++pair) {
+    if (pair && (p->flags & NEUMANN_FLAG_SINGLE_CTA) && !precise) continue;
     for (int g : {4, 8, 16}) cand.emplace_back(pair, g);
   }
   float best = 0.f;
@@ -1118,7 +1126,7 @@ int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t
   p->timed = 0;  // tuning runs are not part of a NEUMANN_FLAG_TIMING record
   p->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_single[std::make_pair(p->npad, p->dtype)] = pick;
+  g_tune_single[tune_key(p)] = pick;
   return NEUMANN_OK;
 }
 
@@ -1201,9 +1209,10 @@ int neumann_plan_info(neumann_plan_t p, neumann_plan_info_t* info) {
   info->workspace_bytes = p->ws_bytes;
   info->padded_n = p->npad;
   if (p->path == PATH_TC && !p->grouped && !p->batched) {
-    info->tile_pair = (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0
-                      : p->tune_pair < 0                  ? (int)tc_uses_pair(p->npad, 0)
-                                                          : p->tune_pair;
+    info->tile_pair = (p->flags & NEUMANN_FLAG_PRECISE_ACC) ? 1
+                      : (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0
+                      : p->tune_pair < 0                     ? (int)tc_uses_pair(p->npad, 0)
+                                                             : p->tune_pair;
     info->raster_group = p->tune_group;
   }
   if (p->grouped) info->batch_chunk = p->chunk_run > 0 ? p->chunk_run : p->chunk;
