@@ -45,6 +45,8 @@ WORKLOADS = {
     # the FP64 comparison (about two minutes at this size) runs only with --fp64-large
     "large-r15-fp16-n16384-k3375": dict(cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
                                         fp64=False),
+    "large-precise-r15-fp16-n16384-k3375": dict(cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16",
+                                                sq_k=4096, fp64=False, precise=True),
     "plain-r9-fp32-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
     "plain-r15-fp32-n4096-k225": dict(cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
     "plain-r9-fp64-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
@@ -530,7 +532,22 @@ def run_ours(args, wl):
         diff = float(torch.linalg.norm(S.double() - S64) / torch.linalg.norm(S64))
         fp64 = {"ms_per_step": fp64_ms, "speedup": fp64_ms / (ms_max / args.steps), "rel_fro_vs_fp64": diff,
                 "products": p64.info["products_executed"]}
+        if "probes" in inp:  # cfg 5: the split result on the 64 probe vectors, against the FP64 path's
+            X = torch.tensor(inp["probes"], dtype=torch.float64, device=dev)
+            SX64 = S64 @ X
+            fp64["probe_rel_err_vs_fp64"] = float(torch.linalg.norm(S.double() @ X - SX64) / torch.linalg.norm(SX64))
         del p64, A64, S64
+
+    # cfg 5: the telescoping property on the probes, (I - A) S_k X = X - A^k X with
+    # A^k X ~ 0 (rho(A)^k ~ 0.95^3375): relative residual || (I - A)(S X) - X || / || X ||
+    probes = None
+    if "probes" in inp:
+        plan(A, out=S)
+        torch.cuda.synchronize()
+        X = torch.tensor(inp["probes"], dtype=torch.float64, device=dev)
+        SX = S.double() @ X
+        resid = SX - A.double() @ SX - X
+        probes = {"count": X.shape[1], "telescoping_residual": float(torch.linalg.norm(resid) / torch.linalg.norm(X))}
 
     # end to end through the C ABI: pinned host A in, host S out, every step
     A_host = torch.tensor(A_np, dtype=io).pin_memory()
@@ -605,6 +622,7 @@ def run_ours(args, wl):
                         "products_executed": sq.info["products_executed"],
                         "formula_ratio": sq.info["products_formula"] / info["products_formula"]},
         "vs_fp64": fp64,
+        "probes": probes,
         "status": status,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": A_host.numel() * A_host.element_size(),
