@@ -549,24 +549,24 @@ def run_ours(args, wl):
         resid = SX - A.double() @ SX - X
         probes = {"count": X.shape[1], "telescoping_residual": float(torch.linalg.norm(resid) / torch.linalg.norm(X))}
 
-    # end to end through the C ABI: pinned host A in, host S out, every step
+    # end to end through the C ABI's host-buffer call (neumann_eval_host): every
+    # step copies pinned host A in and the result S out; the library overlaps one
+    # step's copies with the neighbouring steps' evaluations. Host wall clock
+    # from the first call to the last result in host memory.
     A_host = torch.tensor(A_np, dtype=io).pin_memory()
     S_host = torch.empty_like(A_host).pin_memory()
     for _ in range(max(1, args.warmup)):
-        A.copy_(A_host, non_blocking=True)
-        plan(A, out=S)
-        S_host.copy_(S, non_blocking=True)
+        plan.eval_host(A_host, out=S_host)
+    plan.host_wait()
     torch.cuda.synchronize()
     plan.timing()
     barrier()
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        A.copy_(A_host, non_blocking=True)
-        plan(A, out=S)
-        S_host.copy_(S, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_value = job_value(1, args.steps, world, reduce_max_ms(e0.elapsed_time(e1), world, dev))
+        plan.eval_host(A_host, out=S_host)
+    plan.host_wait()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    e2e_value = job_value(1, args.steps, world, reduce_max_ms(e2e_ms, world, dev))
     plan.timing()
 
     peaks, peak_src = _peaks()

@@ -157,6 +157,26 @@ int neumann_plan_set_workspace(neumann_plan_t plan, void* workspace, size_t byte
  * Errors: NEUMANN_EINVAL, NEUMANN_ENOMEM, NEUMANN_ECUDA. */
 int neumann_eval(neumann_plan_t plan, const void* A, int64_t lda, void* S, int64_t lds, void* stream);
 
+/* S <- S_k(A) for matrices in HOST memory: the call copies A into one of two
+ * plan-owned device staging sets on the plan's input copy stream, evaluates on
+ * `stream`, and copies the result to S on the plan's output copy stream. It
+ * returns once that work is enqueued. Consecutive calls alternate between the
+ * two sets, so one call's copy-in and the previous call's copy-out run while an
+ * evaluation runs.
+ *   A, S  host, n x n row-major with leading dimensions lda, lds >= n, element type
+ *         as in neumann_eval. Pinned memory (cudaHostAlloc / cudaHostRegister) gives
+ *         asynchronous copies; pageable memory is copied synchronously by the driver.
+ *         A must stay unchanged and S unread until neumann_plan_host_wait returns.
+ * The first call allocates the staging sets (4 n^2 elements) and the streams.
+ * Errors: NEUMANN_EINVAL (batched plan, bad arguments, A and S overlap),
+ * NEUMANN_ENOMEM, NEUMANN_ECUDA. */
+int neumann_eval_host(neumann_plan_t plan, const void* A, int64_t lda, void* S, int64_t lds, void* stream);
+
+/* Block until every copy issued by neumann_eval_host on this plan has completed
+ * (results in host memory, inputs no longer read). Errors: NEUMANN_EINVAL,
+ * NEUMANN_ECUDA. */
+int neumann_plan_host_wait(neumann_plan_t plan);
+
 /* C <- A B in the plan's arithmetic (the product every scheme step uses), for
  * n x n row-major device matrices with leading dimension n, element type as in
  * neumann_eval. Uses the plan's workspace for split operands. Stream-ordered.

@@ -9,7 +9,8 @@ from __future__ import annotations
 
 from ._capi import *  # noqa: F401,F403
 from ._capi import (DTYPES, FP32, FP64, SPLIT_BF16, LIB_PATH, neumann_eval, neumann_eval_batched,  # noqa: F401
-                    neumann_last_status, neumann_plan_autotune, neumann_plan_autotune_batched,
+                    neumann_eval_host, neumann_last_status, neumann_plan_autotune,
+                    neumann_plan_autotune_batched, neumann_plan_host_wait,
                     neumann_plan_create, neumann_plan_create_batched, neumann_plan_destroy, neumann_plan_info,
                     neumann_plan_matmul, neumann_plan_timing)
 
@@ -47,6 +48,22 @@ class Plan:
         s = torch.cuda.current_stream(A.device) if stream is None else stream
         neumann_eval(self.handle, A.data_ptr(), A.stride(0), S.data_ptr(), S.stride(0), s.cuda_stream)
         return S
+
+    def eval_host(self, A, out=None, stream=None):
+        """S_k(A) for a CPU tensor A (pinned for asynchronous copies). Returns the
+        CPU result tensor; it is complete after `host_wait()`."""
+        import torch
+
+        n = self.info["n"]
+        if A.device.type != "cpu" or A.dtype != self.io_dtype or A.shape != (n, n) or A.stride(1) != 1:
+            raise ValueError(f"A must be a CPU {self.io_dtype} ({n}, {n}) tensor with unit column stride")
+        S = torch.empty((n, n), dtype=self.io_dtype, pin_memory=A.is_pinned()) if out is None else out
+        s = torch.cuda.current_stream() if stream is None else stream
+        neumann_eval_host(self.handle, A.data_ptr(), A.stride(0), S.data_ptr(), S.stride(0), s.cuda_stream)
+        return S
+
+    def host_wait(self):
+        neumann_plan_host_wait(self.handle)
 
     def matmul(self, A, B, out=None, stream=None):
         import torch

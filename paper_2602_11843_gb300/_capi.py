@@ -65,6 +65,8 @@ def _load():
         "neumann_plan_set_workspace": (c_int, [P, c_void_p, c_size_t]),
         "neumann_eval": (c_int, [P, c_void_p, c_int64, c_void_p, c_int64, c_void_p]),
         "neumann_plan_matmul": (c_int, [P, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "neumann_eval_host": (c_int, [P, c_void_p, c_int64, c_void_p, c_int64, c_void_p]),
+        "neumann_plan_host_wait": (c_int, [P]),
         "neumann_plan_create_batched": (c_int, [POINTER(c_void_p), c_int, c_int64, c_int64, c_int, c_int, c_uint32]),
         "neumann_eval_batched": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_void_p), POINTER(c_void_p), c_void_p]),
         "neumann_last_status": (c_int, [P, POINTER(c_uint32)]),
@@ -132,6 +134,14 @@ def neumann_plan_set_workspace(plan: int, ptr: int, nbytes: int) -> None:
 
 def neumann_eval(plan: int, A: int, lda: int, S: int, lds: int, stream: int = 0) -> None:
     _check(_lib.neumann_eval(plan, A, lda, S, lds, stream), "neumann_eval")
+
+
+def neumann_eval_host(plan: int, A: int, lda: int, S: int, lds: int, stream: int = 0) -> None:
+    _check(_lib.neumann_eval_host(plan, A, lda, S, lds, stream), "neumann_eval_host")
+
+
+def neumann_plan_host_wait(plan: int) -> None:
+    _check(_lib.neumann_plan_host_wait(plan), "neumann_plan_host_wait")
 
 
 def neumann_plan_matmul(plan: int, A: int, B: int, C: int, stream: int = 0) -> None:

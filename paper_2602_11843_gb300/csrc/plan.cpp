@@ -144,6 +144,17 @@ struct neumann_plan_s {
   double c15[28];
   cudaStream_t last_stream = nullptr;
   std::vector<cudaEvent_t> events;
+  // neumann_eval_host: two sets of device staging buffers, an input and an
+  // output copy stream, and per set the events that order copy-in, evaluation
+  // and copy-out (set i % 2 serves call i)
+  struct HostStage {
+    char* a = nullptr;
+    char* s = nullptr;
+    cudaEvent_t in = nullptr, done = nullptr, out = nullptr;
+    bool used = false;
+  } host[2];
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  int64_t host_calls = 0;
   int timed = 0;
   // launch configuration of the tensor-core products, set by the autotuner or
   // taken from an earlier tuning of the same shape in this process
@@ -1277,6 +1288,64 @@ int neumann_eval(neumann_plan_t p, const void* A, int64_t lda, void* S, int64_t 
   }
 }
 
+int neumann_eval_host(neumann_plan_t p, const void* A, int64_t lda, void* S, int64_t lds, void* stream) {
+  if (!p || p->batched || !A || !S || lda < p->n || lds < p->n) return NEUMANN_EINVAL;
+  const size_t es = elem_bytes(p->dt_io);
+  const size_t row = (size_t)p->n * es, mat = row * (size_t)p->n;
+  if (overlap(A, ((size_t)(p->n - 1) * lda) * es + row, S, ((size_t)(p->n - 1) * lds) * es + row))
+    return NEUMANN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  try {
+    if (!p->cs_in) {
+      if (cudaStreamCreateWithFlags(&p->cs_in, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&p->cs_out, cudaStreamNonBlocking) != cudaSuccess)
+        return NEUMANN_ECUDA;
+    }
+    neumann_plan_s::HostStage& h = p->host[p->host_calls & 1];
+    if (!h.a) {
+      if (cudaMalloc(&h.a, mat) != cudaSuccess || cudaMalloc(&h.s, mat) != cudaSuccess) {
+        cudaGetLastError();
+        return NEUMANN_ENOMEM;
+      }
+      if (cudaEventCreateWithFlags(&h.in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h.out, cudaEventDisableTiming) != cudaSuccess)
+        return NEUMANN_ECUDA;
+    }
+    // copy in once this set's previous evaluation has consumed its input
+    if (h.used && cudaStreamWaitEvent(p->cs_in, h.done, 0) != cudaSuccess) return NEUMANN_ECUDA;
+    if (cudaMemcpy2DAsync(h.a, row, A, (size_t)lda * es, row, (size_t)p->n, cudaMemcpyHostToDevice, p->cs_in) !=
+            cudaSuccess ||
+        cudaEventRecord(h.in, p->cs_in) != cudaSuccess)
+      return NEUMANN_ECUDA;
+    // evaluate on the caller's stream once the input is in and this set's
+    // previous result has been copied out
+    if (cudaStreamWaitEvent(s, h.in, 0) != cudaSuccess) return NEUMANN_ECUDA;
+    if (h.used && cudaStreamWaitEvent(s, h.out, 0) != cudaSuccess) return NEUMANN_ECUDA;
+    int rc = eval_one(p, h.a, p->n, h.s, p->n, s);
+    if (rc) return rc;
+    if (cudaEventRecord(h.done, s) != cudaSuccess) return NEUMANN_ECUDA;
+    // copy out while the caller's stream moves on
+    if (cudaStreamWaitEvent(p->cs_out, h.done, 0) != cudaSuccess ||
+        cudaMemcpy2DAsync(S, (size_t)lds * es, h.s, row, row, (size_t)p->n, cudaMemcpyDeviceToHost, p->cs_out) !=
+            cudaSuccess ||
+        cudaEventRecord(h.out, p->cs_out) != cudaSuccess)
+      return NEUMANN_ECUDA;
+    h.used = true;
+    ++p->host_calls;
+  } catch (...) {
+    return NEUMANN_ENOMEM;
+  }
+  return NEUMANN_OK;
+}
+
+int neumann_plan_host_wait(neumann_plan_t p) {
+  if (!p) return NEUMANN_EINVAL;
+  if (p->cs_in && cudaStreamSynchronize(p->cs_in) != cudaSuccess) return NEUMANN_ECUDA;
+  if (p->cs_out && cudaStreamSynchronize(p->cs_out) != cudaSuccess) return NEUMANN_ECUDA;
+  return NEUMANN_OK;
+}
+
 int neumann_plan_matmul(neumann_plan_t p, const void* A, const void* B, void* C, void* stream) {
   if (!p || p->batched || !A || !B || !C) return NEUMANN_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1403,6 +1472,16 @@ void neumann_plan_destroy(neumann_plan_t p) {
     neumann_plan_destroy(kv.second);
   }
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->cs_in) cudaStreamSynchronize(p->cs_in);
+  if (p->cs_out) cudaStreamSynchronize(p->cs_out);
+  for (auto& h : p->host) {
+    if (h.a) cudaFree(h.a);
+    if (h.s) cudaFree(h.s);
+    for (cudaEvent_t e : {h.in, h.done, h.out})
+      if (e) cudaEventDestroy(e);
+  }
+  if (p->cs_in) cudaStreamDestroy(p->cs_in);
+  if (p->cs_out) cudaStreamDestroy(p->cs_out);
   if (p->tab_event) cudaEventDestroy(p->tab_event);
   if (p->h_tab) cudaFreeHost(p->h_tab);
   if (p->ws_owned) cudaFree(p->ws);

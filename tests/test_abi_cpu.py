@@ -168,3 +168,17 @@ def test_algorithmic_bytes_per_element():
     per = b9["product_bytes_per_element"] / b9["products_executed"]
     assert 8 < per < 8 + 4 * 8 + 4 * 20
     assert _info(512, 81, 9, C.FP64)["bytes_per_element"] > _info(512, 81, 9, C.FP32)["bytes_per_element"]
+
+
+def test_eval_host_argument_errors():
+    h = C.neumann_plan_create(64, 81, 9, C.SPLIT_BF16, 0)
+    hb = C.neumann_plan_create_batched(4, 64, 81, 9, C.SPLIT_BF16, 0)
+    try:
+        for args in [(hb, 16, 64, 32, 64), (h, 16, 63, 32, 64), (h, 16, 64, 0, 64), (h, 0, 64, 32, 64),
+                     (h, 4096, 64, 4096 + 8 * 64, 64)]:  # the last pair overlaps
+            with pytest.raises(C.NeumannError) as e:
+                C.neumann_eval_host(*args)
+            assert e.value.code == C.EINVAL
+    finally:
+        C.neumann_plan_destroy(h)
+        C.neumann_plan_destroy(hb)
