@@ -57,14 +57,20 @@ constexpr uint32_t STG_FLOATS = 32 * 33;  // one epilogue warp's 32 x 32 staging
 // chunks. The epilogue is latency-bound (a chain of dependent loads, FMAs,
 // conversions and stores per chunk), so two warps per scheduler keep it under
 // the next tile's K loop.
+// A grouped launch (matrices of order <= 256: K loops of at most 8 stages) is
+// bound by its epilogue alone, so it runs 20 warps: warpgroup 0 holds the TMA
+// and MMA warps (and two idle ones) and gives registers back (setmaxnreg 24)
+// to four warpgroups of epilogue warps (112 each): 128 x 24 + 512 x 112 =
+// 60416 <= 61440 = 640 threads x 96 at launch.
 template <bool kGrouped, bool kPair>
 struct EpiShape {
-  static constexpr int kWarps = 8;
-  static constexpr int kThreads = 64 + 32 * kWarps;  // TMA warp, MMA warp, epilogue warps
+  static constexpr int kWarps = kGrouped ? 16 : 8;
+  static constexpr int kEpiFirst = kGrouped ? 4 : 2;                  // first epilogue warp
+  static constexpr int kThreads = 32 * (kEpiFirst + kWarps);         // TMA warp, MMA warp, (idle,) epilogue
   static constexpr int kBRows = kPair ? BN / 2 : BN;  // rows of the stored B^T panel this CTA loads
   static constexpr uint32_t kBTile = kBRows * BK * 2;
   static constexpr uint32_t kStageBytes = 2 * A_TILE + 2 * kBTile;
-  static constexpr int kStages = kPair ? 6 : 4;
+  static constexpr int kStages = kPair ? 6 : kGrouped ? 3 : 4;
   static constexpr int kTileM = kPair ? 2 * BM : BM;  // output rows of one work item
   // stages | barriers, TMEM address, abort flag (256 B) | staging tiles (+ alignment slack)
   static constexpr uint32_t kSmem = kStages * kStageBytes + 256 + kWarps * STG_FLOATS * 4 + 1024;
@@ -401,7 +407,60 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   // Stage-full and accumulator-free barriers live in the even CTA of a pair.
   const uint32_t lead_bar_base = kPair ? cluster_addr(bar_base, 0) : bar_base;
-
+  if (warp >= S::kEpiFirst) {
+    if constexpr (kGrouped) asm volatile("setmaxnreg.inc.sync.aligned.u32 112;" ::: "memory");
+    // ---------------- epilogue (warps kEpiFirst .. kEpiFirst + kWarps) ----------------
+    // Each 32 x 32 chunk is read from TMEM one row per lane, staged in shared
+    // memory, and processed one column per lane (epi_col), so that the warp's
+    // global loads and stores of row-major buffers touch one line per instruction.
+    constexpr int kStep = S::kWarps / 4;          // warps per TMEM lane quarter
+    const int q = warp & 3;                       // TMEM lane quarter this warp may access
+    const int half = (warp - S::kEpiFirst) >> 2;  // warps of one quarter take turns at column chunks
+    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - S::kEpiFirst) * STG_FLOATS;
+    bool bad = false;
+    int it = 0;
+    for (int tile = first; tile < ntiles; tile += stride, ++it) {
+      const uint32_t buf = it & 1;
+      const uint32_t use = (uint32_t)it >> 1;
+      const bool got = mbar_wait(tfull_bar(buf), use & 1u);
+      if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      int mat, tm, tn, nk;
+      tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
+      const EpiCtx x = epi_ctx(P, mat);
+      const int rbase = tm * S::kTileM + (int)rank * BM + q * 32;
+      const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
+      // A grouped tile writes rows and columns below its matrix's order rounded
+      // up to 32 (= nk x 32): with that K padding zero in both operands, later
+      // rows and columns only feed accumulator entries every consumer discards.
+      const int nchunks = kGrouped ? nk : BN / 32;
+      const int lim = kGrouped ? nk * 32 : (1 << 30);
+#pragma unroll 1
+      for (int chunk = half; chunk < nchunks; chunk += kStep) {
+        uint32_t v[32];
+        __syncwarp();
+        tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        bad |= epi_chunk<kF16>(P, x, rbase, tn * BN + chunk * 32 + lane, stg, lane, lim);
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if constexpr (kPair)
+          mbar_arrive_cluster(lead_bar_base + 8u * (2 * STAGES + 2 + buf));
+        else
+          mbar_arrive(tempty_bar(buf));
+      }
+    }
+    epi_flag(P, bad);
+  } else {
+    if constexpr (kGrouped) asm volatile("setmaxnreg.dec.sync.aligned.u32 24;" ::: "memory");
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
@@ -488,57 +547,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
       umma_commit<kPair>(drain_bar, false);
       mbar_wait(drain_bar, 0);
     }
-  } else {
-    // ---------------- epilogue (warps 2 .. 2 + kWarps) ----------------
-    // Each 32 x 32 chunk is read from TMEM one row per lane, staged in shared
-    // memory, and processed one column per lane (epi_col), so that the warp's
-    // global loads and stores of row-major buffers touch one line per instruction.
-    constexpr int kStep = S::kWarps / 4;  // warps per TMEM lane quarter
-    const int q = warp & 3;               // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;     // warps of one quarter take alternate column chunks
-    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * STG_FLOATS;
-    bool bad = false;
-    int it = 0;
-    for (int tile = first; tile < ntiles; tile += stride, ++it) {
-      const uint32_t buf = it & 1;
-      const uint32_t use = (uint32_t)it >> 1;
-      const bool got = mbar_wait(tfull_bar(buf), use & 1u);
-      if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      int mat, tm, tn, nk;
-      tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
-      const EpiCtx x = epi_ctx(P, mat);
-      const int rbase = tm * S::kTileM + (int)rank * BM + q * 32;
-      const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
-      // A grouped tile writes rows and columns below its matrix's order rounded
-      // up to 32 (= nk x 32): with that K padding zero in both operands, later
-      // rows and columns only feed accumulator entries every consumer discards.
-      const int nchunks = kGrouped ? nk : BN / 32;
-      const int lim = kGrouped ? nk * 32 : (1 << 30);
-#pragma unroll 1
-      for (int chunk = half; chunk < nchunks; chunk += kStep) {
-        uint32_t v[32];
-        __syncwarp();
-        tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
-        __syncwarp();
-        bad |= epi_chunk<kF16>(P, x, rbase, tn * BN + chunk * 32 + lane, stg, lane, lim);
-        __syncwarp();
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        if constexpr (kPair)
-          mbar_arrive_cluster(lead_bar_base + 8u * (2 * STAGES + 2 + buf));
-        else
-          mbar_arrive(tempty_bar(buf));
-      }
-    }
-    epi_flag(P, bad);
+  }
   }
 
   tc_fence_before();
