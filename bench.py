@@ -344,24 +344,21 @@ def run_batched(args, wl):
     e1.record(stream)
     torch.cuda.synchronize()
     per_matrix_ms = e0.elapsed_time(e1)
-    # end to end: host inputs in, host results out, every step
+    # end to end through the C ABI's packed host-batch call (neumann_eval_batched_host):
+    # every step copies the pinned packed batch in and the results out; the library
+    # overlaps the copies with the neighbouring steps' evaluations. Host wall clock
+    # from the first call to the last result in host memory.
     A_host = A_all.cpu().pin_memory()
     S_host = torch.empty_like(A_host).pin_memory()
     h2d = A_host.numel() * A_host.element_size()
-
-    def e2e_step():
-        A_all.copy_(A_host, non_blocking=True)
-        bp.launch()
-        S_host.copy_(S_all, non_blocking=True)
-
-    e2e_step()
+    bp.eval_host(ns, A_host, S_host)
+    bp.host_wait()
     torch.cuda.synchronize()
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_value = job_value(len(mats), args.steps, world, reduce_max_ms(e0.elapsed_time(e1), world, dev))
+        bp.eval_host(ns, A_host, S_host)
+    bp.host_wait()
+    e2e_value = job_value(len(mats), args.steps, world, reduce_max_ms((time.perf_counter() - t0) * 1e3, world, dev))
     nm.neumann_plan_timing(bp.handle, 1 << 16)
     peaks, peak_src = _peaks()
     tc = wl["dtype"].startswith("split")

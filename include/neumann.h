@@ -172,7 +172,21 @@ int neumann_eval(neumann_plan_t plan, const void* A, int64_t lda, void* S, int64
  * NEUMANN_ENOMEM, NEUMANN_ECUDA. */
 int neumann_eval_host(neumann_plan_t plan, const void* A, int64_t lda, void* S, int64_t lds, void* stream);
 
-/* Block until every copy issued by neumann_eval_host on this plan has completed
+/* S_i <- S_k(A_i), i < count, for a batch PACKED in host memory: matrix i
+ * (n_i x n_i, row-major, leading dimension n_i) starts at element
+ * sum_{j<i} n_j^2 of A and of S. The call copies the packed batch into one
+ * plan-owned device staging pair on the plan's input copy stream, evaluates it
+ * on `stream` (as neumann_eval_batched), and copies the results out on the
+ * plan's output copy stream; it returns once that work is enqueued. The next
+ * call's copy-in waits only for the last step that reads A, and its first write
+ * of S only for this call's copy-out, so copies overlap evaluations.
+ * Host buffers as in neumann_eval_host (pinned for asynchronous copies; stable
+ * until neumann_plan_host_wait). The staging pair grows to the largest batch
+ * seen (2 x sum n_i^2 elements). Errors as neumann_eval_batched. */
+int neumann_eval_batched_host(neumann_plan_t plan, int count, const int64_t* n, const void* A, void* S,
+                              void* stream);
+
+/* Block until every copy issued by neumann_eval_host / neumann_eval_batched_host on this plan has completed
  * (results in host memory, inputs no longer read). Errors: NEUMANN_EINVAL,
  * NEUMANN_ECUDA. */
 int neumann_plan_host_wait(neumann_plan_t plan);

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 from ._capi import *  # noqa: F401,F403
 from ._capi import (DTYPES, FP32, FP64, SPLIT_BF16, LIB_PATH, neumann_eval, neumann_eval_batched,  # noqa: F401
-                    neumann_eval_host, neumann_last_status, neumann_plan_autotune,
+                    neumann_eval_batched_host, neumann_eval_host, neumann_last_status, neumann_plan_autotune,
                     neumann_plan_autotune_batched, neumann_plan_host_wait,
                     neumann_plan_create, neumann_plan_create_batched, neumann_plan_destroy, neumann_plan_info,
                     neumann_plan_matmul, neumann_plan_timing)
@@ -147,6 +147,22 @@ class BatchedPlan:
         cnt, na, aa, sa, As, _ = self._bound
         s = torch.cuda.current_stream(As[0].device) if stream is None else stream
         _check(_lib.neumann_eval_batched(self.handle, cnt, na, aa, sa, s.cuda_stream), "neumann_eval_batched")
+
+    def eval_host(self, ns, A, S, stream=None):
+        """The batch packed in the CPU tensors A and S (matrix i at element
+        sum_{j<i} n_j^2; pinned for asynchronous copies); complete after host_wait()."""
+        import torch
+
+        dt = _torch_dtype(self.dtype, self.flags)
+        total = sum(int(n) * int(n) for n in ns)
+        for t in (A, S):
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or t.numel() < total:
+                raise ValueError(f"A and S must be contiguous CPU {dt} tensors of at least {total} elements")
+        s = torch.cuda.current_stream() if stream is None else stream
+        neumann_eval_batched_host(self.handle, [int(n) for n in ns], A.data_ptr(), S.data_ptr(), s.cuda_stream)
+
+    def host_wait(self):
+        neumann_plan_host_wait(self.handle)
 
     def autotune(self, As, outs, reps: int = 3, stream=None):
         """Pick the fastest matrices-per-pass for this batch (writes `outs`)."""

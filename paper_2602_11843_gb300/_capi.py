@@ -67,6 +67,7 @@ def _load():
         "neumann_plan_matmul": (c_int, [P, c_void_p, c_void_p, c_void_p, c_void_p]),
         "neumann_eval_host": (c_int, [P, c_void_p, c_int64, c_void_p, c_int64, c_void_p]),
         "neumann_plan_host_wait": (c_int, [P]),
+        "neumann_eval_batched_host": (c_int, [P, c_int, POINTER(c_int64), c_void_p, c_void_p, c_void_p]),
         "neumann_plan_create_batched": (c_int, [POINTER(c_void_p), c_int, c_int64, c_int64, c_int, c_int, c_uint32]),
         "neumann_eval_batched": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_void_p), POINTER(c_void_p), c_void_p]),
         "neumann_last_status": (c_int, [P, POINTER(c_uint32)]),
@@ -138,6 +139,12 @@ def neumann_eval(plan: int, A: int, lda: int, S: int, lds: int, stream: int = 0)
 
 def neumann_eval_host(plan: int, A: int, lda: int, S: int, lds: int, stream: int = 0) -> None:
     _check(_lib.neumann_eval_host(plan, A, lda, S, lds, stream), "neumann_eval_host")
+
+
+def neumann_eval_batched_host(plan: int, n, A: int, S: int, stream: int = 0) -> None:
+    cnt = len(n)
+    na = (c_int64 * cnt)(*n)
+    _check(_lib.neumann_eval_batched_host(plan, cnt, na, A, S, stream), "neumann_eval_batched_host")
 
 
 def neumann_plan_host_wait(plan: int) -> None:

@@ -155,6 +155,17 @@ struct neumann_plan_s {
   } host[2];
   cudaStream_t cs_in = nullptr, cs_out = nullptr;
   int64_t host_calls = 0;
+  // neumann_eval_batched_host: one packed staging pair (stable device pointers,
+  // so the grouped tile tables stay cached). Within an evaluation, `a_free` is
+  // recorded after the last op that reads A and the first op that writes S
+  // waits for `s_free` (the previous call's copy-out).
+  char* pk_a = nullptr;
+  char* pk_s = nullptr;
+  size_t pk_bytes = 0;
+  cudaEvent_t pk_in = nullptr, pk_a_free = nullptr, pk_done = nullptr, pk_s_free = nullptr;
+  bool pk_used = false;
+  cudaEvent_t hook_after_a = nullptr;  // record after the last A-reading op (set during one run_ops)
+  cudaEvent_t hook_before_s = nullptr;  // wait before the first S-writing op
   int timed = 0;
   // launch configuration of the tensor-core products, set by the autotuner or
   // taken from an earlier tuning of the same shape in this process
@@ -856,9 +867,21 @@ int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcM
       p->events.push_back(e);
     }
   }
+  // the last op reading the caller's A and the first writing the caller's S
+  int a_last = -1, s_first = -1;
+  if (p->hook_after_a || p->hook_before_s) {
+    for (int i = 0; i < (int)ops.size(); ++i) {
+      for (int j = 0; j < ops[i].nin; ++j)
+        if (ops[i].in[j].slot == SL_USER_A) a_last = i;
+      for (int j = 0; j < ops[i].nout; ++j)
+        if (ops[i].out[j].slot == SL_USER_S && s_first < 0) s_first = i;
+    }
+  }
   for (size_t i = 0; i < ops.size(); ++i) {
     const Op& op = ops[i];
     make_params(p, op, u, &P);
+    if (p->hook_before_s && (int)i == s_first && cudaStreamWaitEvent(s, p->hook_before_s, 0) != cudaSuccess)
+      return NEUMANN_ECUDA;
     cudaError_t err;
     const int4* ew = p->grouped ? p->cur_ew : nullptr;
     const int4* st = p->grouped ? p->cur_simt : nullptr;
@@ -882,6 +905,8 @@ int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcM
       ++gi;
     }
     if (err != cudaSuccess) return NEUMANN_ECUDA;
+    if (p->hook_after_a && (int)i == a_last && cudaEventRecord(p->hook_after_a, s) != cudaSuccess)
+      return NEUMANN_ECUDA;
   }
   if (timing) p->timed = gi;
   return NEUMANN_OK;
@@ -1021,7 +1046,12 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     p->last_s.assign(S, S + count);
   }
   char* ws = p->ws;
-  for (const neumann_plan_s::Chunk& ch : p->chunks) {
+  cudaEvent_t after_a = p->hook_after_a, before_s = p->hook_before_s;
+  for (size_t ci = 0; ci < p->chunks.size(); ++ci) {
+    const neumann_plan_s::Chunk& ch = p->chunks[ci];
+    // S is first written by the first chunk; A is last read by the last chunk
+    p->hook_before_s = ci == 0 ? before_s : nullptr;
+    p->hook_after_a = ci + 1 == p->chunks.size() ? after_a : nullptr;
     p->cur_matn = reinterpret_cast<const int*>(ws + p->off_matn) + ch.first;
     p->cur_atab = reinterpret_cast<const void* const*>(ws + p->off_atab) + ch.first;
     p->cur_stab = reinterpret_cast<void* const*>(ws + p->off_stab) + ch.first;
@@ -1033,8 +1063,12 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     p->n_ew = ch.new_;
     UserPtrs u{nullptr, 0, nullptr, nullptr, 0};
     int rc = run_ops(p, p->ops, p->maps, u, s, (p->flags & NEUMANN_FLAG_TIMING) != 0);
-    if (rc) return rc;
+    if (rc) {
+      p->hook_after_a = p->hook_before_s = nullptr;
+      return rc;
+    }
   }
+  p->hook_after_a = p->hook_before_s = nullptr;
   return NEUMANN_OK;
 }
 
@@ -1339,6 +1373,85 @@ int neumann_eval_host(neumann_plan_t p, const void* A, int64_t lda, void* S, int
   return NEUMANN_OK;
 }
 
+int neumann_eval_batched_host(neumann_plan_t p, int count, const int64_t* n, const void* A, void* S,
+                              void* stream) {
+  if (!p || !p->batched || count < 0 || count > p->count) return NEUMANN_EINVAL;
+  if (count == 0) return NEUMANN_OK;
+  if (!n || !A || !S) return NEUMANN_EINVAL;
+  const size_t es = elem_bytes(p->dt_io);
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || n[i] > p->max_n) return NEUMANN_EINVAL;
+    total += (size_t)n[i] * (size_t)n[i];
+  }
+  const size_t bytes = total * es;
+  if (overlap(A, bytes, S, bytes)) return NEUMANN_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  try {
+    if (!p->cs_in) {
+      if (cudaStreamCreateWithFlags(&p->cs_in, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&p->cs_out, cudaStreamNonBlocking) != cudaSuccess)
+        return NEUMANN_ECUDA;
+    }
+    if (!p->pk_in) {
+      for (cudaEvent_t* e : {&p->pk_in, &p->pk_a_free, &p->pk_done, &p->pk_s_free})
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return NEUMANN_ECUDA;
+    }
+    if (bytes > p->pk_bytes) {  // grow the staging pair once nothing uses it
+      if (p->pk_used && (cudaStreamSynchronize(p->cs_in) != cudaSuccess ||
+                         cudaStreamSynchronize(p->cs_out) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
+        return NEUMANN_ECUDA;
+      if (p->pk_a) cudaFree(p->pk_a);
+      if (p->pk_s) cudaFree(p->pk_s);
+      p->pk_a = p->pk_s = nullptr;
+      p->pk_bytes = 0;
+      p->pk_used = false;
+      if (cudaMalloc(&p->pk_a, bytes) != cudaSuccess || cudaMalloc(&p->pk_s, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return NEUMANN_ENOMEM;
+      }
+      p->pk_bytes = bytes;
+    }
+    std::vector<const void*> ad(count);
+    std::vector<void*> sd(count);
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+      ad[i] = p->pk_a + off * es;
+      sd[i] = p->pk_s + off * es;
+      off += (size_t)n[i] * (size_t)n[i];
+    }
+    // copy in once the previous evaluation has read its last A
+    if (p->pk_used && cudaStreamWaitEvent(p->cs_in, p->pk_a_free, 0) != cudaSuccess) return NEUMANN_ECUDA;
+    if (cudaMemcpyAsync(p->pk_a, A, bytes, cudaMemcpyHostToDevice, p->cs_in) != cudaSuccess ||
+        cudaEventRecord(p->pk_in, p->cs_in) != cudaSuccess || cudaStreamWaitEvent(s, p->pk_in, 0) != cudaSuccess)
+      return NEUMANN_ECUDA;
+    int rc = ensure_workspace(p, s);
+    if (rc) return rc;
+    p->last_stream = s;
+    p->hook_after_a = p->pk_a_free;
+    p->hook_before_s = p->pk_used ? p->pk_s_free : nullptr;
+    if (p->grouped) {
+      rc = eval_grouped(p, count, n, ad.data(), sd.data(), s);
+    } else {  // orders above 256: plain per-matrix evaluation, then the same copy-out
+      p->hook_after_a = p->hook_before_s = nullptr;
+      if (p->pk_used && cudaStreamWaitEvent(s, p->pk_s_free, 0) != cudaSuccess) return NEUMANN_ECUDA;
+      rc = neumann_eval_batched(p, count, n, ad.data(), sd.data(), stream);
+      if (!rc && cudaEventRecord(p->pk_a_free, s) != cudaSuccess) rc = NEUMANN_ECUDA;
+    }
+    p->hook_after_a = p->hook_before_s = nullptr;
+    if (rc) return rc;
+    // copy out while the caller's stream moves on
+    if (cudaEventRecord(p->pk_done, s) != cudaSuccess || cudaStreamWaitEvent(p->cs_out, p->pk_done, 0) != cudaSuccess ||
+        cudaMemcpyAsync(S, p->pk_s, bytes, cudaMemcpyDeviceToHost, p->cs_out) != cudaSuccess ||
+        cudaEventRecord(p->pk_s_free, p->cs_out) != cudaSuccess)
+      return NEUMANN_ECUDA;
+    p->pk_used = true;
+  } catch (...) {
+    return NEUMANN_ENOMEM;
+  }
+  return NEUMANN_OK;
+}
+
 int neumann_plan_host_wait(neumann_plan_t p) {
   if (!p) return NEUMANN_EINVAL;
   if (p->cs_in && cudaStreamSynchronize(p->cs_in) != cudaSuccess) return NEUMANN_ECUDA;
@@ -1480,6 +1593,10 @@ void neumann_plan_destroy(neumann_plan_t p) {
     for (cudaEvent_t e : {h.in, h.done, h.out})
       if (e) cudaEventDestroy(e);
   }
+  if (p->pk_a) cudaFree(p->pk_a);
+  if (p->pk_s) cudaFree(p->pk_s);
+  for (cudaEvent_t e : {p->pk_in, p->pk_a_free, p->pk_done, p->pk_s_free})
+    if (e) cudaEventDestroy(e);
   if (p->cs_in) cudaStreamDestroy(p->cs_in);
   if (p->cs_out) cudaStreamDestroy(p->cs_out);
   if (p->tab_event) cudaEventDestroy(p->tab_event);

@@ -49,3 +49,34 @@ def test_eval_host_leading_dimensions():
     ref = p(A.contiguous().cuda()).cpu()
     torch.cuda.synchronize()
     assert torch.equal(S, ref) and torch.all(Sbig[:, n:] == 5.0)
+
+
+@pytest.mark.parametrize("dtype", ["split_bf16", "fp32"])
+def test_eval_batched_host_packed(dtype):
+    """Three back-to-back packed batches (different contents) before one wait,
+    against the device batched call on the same matrices."""
+    import paper_2602_11843_gb300 as nm
+    from workloads import generators as G
+
+    ns = [16, 48, 128, 200, 256, 33, 1]
+    bp = nm.BatchedPlan(len(ns), 256, 81, 9, dtype)
+    dt = torch.float32 if dtype == "fp32" else torch.float64
+    total = sum(n * n for n in ns)
+    batches = []
+    for b in range(3):
+        mats = [G.gaussian_scaled(n, 0.5, 500 + 10 * b + i)["A"] for i, n in enumerate(ns)]
+        A = torch.cat([torch.tensor(m, dtype=dt).reshape(-1) for m in mats]).pin_memory()
+        S = torch.empty(total, dtype=dt).pin_memory()
+        batches.append((mats, A, S))
+    for _, A, S in batches:
+        bp.eval_host(ns, A, S)
+    bp.host_wait()
+    assert bp.status() == 0
+    for mats, A, S in batches:
+        As = [torch.tensor(m, dtype=dt, device="cuda") for m in mats]
+        ref = bp(As)
+        torch.cuda.synchronize()
+        off = 0
+        for n, r in zip(ns, ref):
+            assert torch.equal(S[off:off + n * n].view(n, n), r.cpu())
+            off += n * n
