@@ -63,7 +63,7 @@ DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 # the 16 launches of one n = 8192 radix-15 evaluation, from one ncu capture
 # (profiles/tc_split_gemm_n8192_r15_bench.md). Valid for the kernel sources
 # whose SHA-1 prefix is recorded beside it; reported as null otherwise.
-TC_TRAFFIC = {"sha1": "e423d4ac8da0", "bytes_per_launch": 5.0947e9}
+TC_TRAFFIC = {"sha1": "8a2af775a17e", "bytes_per_launch": 4.6036e9}
 
 
 def _peaks():
