@@ -67,6 +67,31 @@ def planted_symmetric(n: int, rho: float, seed: int, n_reflectors: int = 8) -> d
     return {"kind": "planted", "n": n, "A": M, "V": V, "lam": lam, "rho": rho, "seed": seed}
 
 
+def planted_spectrum(lam: np.ndarray, seed: int, n_reflectors: int = 8) -> dict:
+    """Symmetric A = Q diag(lam) Q^T for given eigenvalues, Q = H_1 ... H_r
+    (the construction of planted_symmetric with a prescribed spectrum)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    n = lam.shape[0]
+    (rv,) = _rngs(seed, 1)
+    V = rv.standard_normal((n_reflectors, n))
+    M = np.diag(lam)
+    for i in reversed(range(n_reflectors)):
+        _apply_reflector_both_sides(M, V[i])
+    M = 0.5 * (M + M.T)
+    return {"kind": "planted", "n": n, "A": M, "V": V, "lam": lam, "seed": seed}
+
+
+def convergence_spd(d: int = 64, kappa: float = 1e4, seed: int = 6400) -> dict:
+    """The convergence problem of the numerical validation: I - A symmetric
+    positive definite with eigenvalues geometrically spaced in [1/kappa, 1]
+    (condition number kappa), i.e. A with eigenvalues 1 - sigma_i,
+    sigma_i = kappa^(-i/(d-1)), so rho(A) = 1 - 1/kappa."""
+    sigma = kappa ** (-np.arange(d) / (d - 1))
+    out = planted_spectrum(1.0 - sigma, seed)
+    out["kappa"] = kappa
+    return out
+
+
 def planted_perturbed(n: int, rho: float, seed: int, rank: int = 32, pert_norm: float = 0.01,
                       n_probes: int = 64, n_reflectors: int = 8) -> dict:
     """Planted symmetric spectrum plus a nonsymmetric rank-`rank` term of 2-norm `pert_norm`.
