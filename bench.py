@@ -40,6 +40,12 @@ WORKLOADS = {
                                          precise=True),
     "precise-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096,
                                          precise=True),
+    # the same symmetric input through NEUMANN_FLAG_SYMMETRIC: products compute the tiles on or
+    # above the diagonal only, so the roofline counts that work, not 2 n^3
+    "symmetric-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096,
+                                           symmetric=True),
+    "symmetric-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
+                                           symmetric=True),
     "precision-r9-fp16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_fp16", sq_k=8192),
     # cfg 5: n = 16384, planted spectrum U[-0.95, 0.95] + rank-32 nonsymmetric term of norm 0.01;
     # the FP64 comparison (about two minutes at this size) runs only with --fp64-large
@@ -463,7 +469,7 @@ def run_ours(args, wl):
     inp = make_input(wl, rank)
     A_np = np.asarray(inp["A"], dtype=np.float64)
     n, k = wl["n"], wl["k"]
-    pflags = nm.FLAG_PRECISE_ACC if wl.get("precise") else 0
+    pflags = (nm.FLAG_PRECISE_ACC if wl.get("precise") else 0) | (nm.FLAG_SYMMETRIC if wl.get("symmetric") else 0)
     plan = nm.Plan(n, k, wl["radix"], wl["dtype"], nm.FLAG_TIMING | pflags)
     io = plan.io_dtype
     A = torch.tensor(A_np, dtype=io, device=dev)
@@ -571,13 +577,19 @@ def run_ours(args, wl):
     mean_prod_ms = statistics.mean(prod_ms) if prod_ms else float("nan")
     if tc:
         flops = 3 * 2.0 * n ** 3  # three BF16 products per split product
+        work = "3 x 2n^3 BF16 tensor flops"
+        if wl.get("symmetric"):  # the 256 x 256 tiles on or above the diagonal only
+            t = info["padded_n"] // 256
+            flops = 3 * 2.0 * info["padded_n"] * 256 * 256 * (t * (t + 1) // 2)
+            work = "3 x 2 x padded_n x 256^2 x (tiles on or above the diagonal) BF16 tensor flops"
         peak = peaks["bf16_tflops_sustained"]
         sha = _src_sha("kernels_tc.cu", "epilogue.cuh")
-        traffic = TC_TRAFFIC["bytes_per_launch"] if TC_TRAFFIC["sha1"] == sha and n == 8192 else None
+        traffic = (TC_TRAFFIC["bytes_per_launch"] if TC_TRAFFIC["sha1"] == sha and n == 8192 and not pflags
+                   else None)
         roof = {"bound": "tensor", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": None, "traffic": traffic,
                 "kernel": "tc_split_gemm_kernel", "peak_source": f"bf16_tflops_sustained ({peak_src})",
-                "work_per_launch": "3 x 2n^3 BF16 tensor flops", "launches_timed": len(prod_ms)}
+                "work_per_launch": work, "launches_timed": len(prod_ms)}
     else:
         flops = 2.0 * n ** 3
         # CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes (x 2 flop) at the
@@ -611,6 +623,7 @@ def run_ours(args, wl):
                    "products_per_step": info["products_executed"], "products_formula": info["products_formula"],
                    "l2": "inputs larger than L2 (A, S and every workspace matrix exceed 129 MB)",
                    "tiles": None if wl["dtype"] in ("fp32", "fp64") else
+                            "2-CTA 256x256, upper triangle mirrored" if wl.get("symmetric") else
                             "2-CTA 256x128, chunked accumulation" if pflags else
                             ("2-CTA 256x256" if info["tile_pair"] else "1-CTA 128x256"),
                    "raster_group": info["raster_group"] or None, "autotuned": bool(info["tuned"]),

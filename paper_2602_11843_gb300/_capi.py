@@ -33,6 +33,7 @@ FLAG_TIMING = 0x8
 FLAG_IO_FP32 = 0x10
 FLAG_SINGLE_CTA = 0x20
 FLAG_PRECISE_ACC = 0x40
+FLAG_SYMMETRIC = 0x80
 
 MAX_LEVELS = 64
 

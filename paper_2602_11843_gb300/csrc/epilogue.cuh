@@ -620,9 +620,106 @@ __device__ __forceinline__ void st8_split(const EpiSplit& sp, const EpiCtx& x, i
 // input, 16 for two, or one FP32 and one FP64, 8 otherwise) so that about 32
 // loads per lane are in flight whatever the op. NF: FP32 input slots (the
 // op's FP32 inputs in index order, P.f32_idx); kD: the op may have an FP64 input.
+// Symmetric products: a tile above the diagonal also writes its transpose.
+// The run (r0 .. r0+7, c) lands at (c, r0 .. r0+7), 8 consecutive entries of
+// row c: vector stores into workspace buffers (leading dimension npad, r0 a
+// multiple of 8), scalar stores into a caller's matrix.
+__device__ __forceinline__ void st8_mirror_dst(const EpiOut& o, const EpiCtx& x, int r0, int c, const float (&vf)[8],
+                                               const double* v) {
+  for (int d = 0; d < o.ndst; ++d) {
+    const EpiDst& ds = o.dst[d];
+    int64_t ld;
+    if (ds.dt == DT_F64) {
+      double* q = dst_base<double>(ds, x, &ld) + (int64_t)c * ld + r0;
+      double t[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t[w] = v ? v[w] : (double)vf[w];
+      if (ds.mode == EPI_WS) {
+#pragma unroll
+        for (int w = 0; w < 8; w += 2) *reinterpret_cast<double2*>(q + w) = make_double2(t[w], t[w + 1]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) q[w] = t[w];
+      }
+    } else {
+      float* q = dst_base<float>(ds, x, &ld) + (int64_t)c * ld + r0;
+      if (ds.mode == EPI_WS) {
+        *reinterpret_cast<float4*>(q) = make_float4(vf[0], vf[1], vf[2], vf[3]);
+        *reinterpret_cast<float4*>(q + 4) = make_float4(vf[4], vf[5], vf[6], vf[7]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) q[w] = vf[w];
+      }
+    }
+  }
+}
+
+// The mirrored run of a row-major split (symmetric plans store no transposed
+// splits): hi/lo of (c, r0 .. r0+7), one 16-byte store each.
+template <bool kF16>
+__device__ __forceinline__ void st8_split_mirror(const EpiSplit& sp, const EpiCtx& x, int r0, int c,
+                                                 const float (&v)[8]) {
+  uint32_t ph[4], pl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], &ph[q], &pl[q]);
+  const int64_t off = x.off + (int64_t)c * sp.ld + r0;
+  *reinterpret_cast<uint4*>(reinterpret_cast<unsigned short*>(sp.hi) + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+  *reinterpret_cast<uint4*>(reinterpret_cast<unsigned short*>(sp.lo) + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+}
+
+// A chunk on the diagonal of a symmetric product: the element (r, c) of the
+// run r = r0 .. r0+7 is written at its place when r <= c and at (c, r) too
+// when r < c, so that the result is exactly symmetric.
+__device__ __forceinline__ void st8_dst_diag(const EpiOut& o, const EpiCtx& x, int r0, int c, const float (&vf)[8],
+                                             const double* v) {
+  for (int d = 0; d < o.ndst; ++d) {
+    const EpiDst& ds = o.dst[d];
+    int64_t ld;
+    if (ds.dt == DT_F64) {
+      double* q = dst_base<double>(ds, x, &ld);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const double t = v ? v[w] : (double)vf[w];
+        if (r0 + w <= c) q[(int64_t)(r0 + w) * ld + c] = t;
+        if (r0 + w < c) q[(int64_t)c * ld + r0 + w] = t;
+      }
+    } else {
+      float* q = dst_base<float>(ds, x, &ld);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        if (r0 + w <= c) q[(int64_t)(r0 + w) * ld + c] = vf[w];
+        if (r0 + w < c) q[(int64_t)c * ld + r0 + w] = vf[w];
+      }
+    }
+  }
+}
+
+template <bool kF16>
+__device__ __forceinline__ void st8_split_diag(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[8]) {
+  uint32_t ph[4], pl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], &ph[q], &pl[q]);
+  unsigned short* hi = reinterpret_cast<unsigned short*>(sp.hi) + x.off;
+  unsigned short* lo = reinterpret_cast<unsigned short*>(sp.lo) + x.off;
+  const int64_t ld = sp.ld;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const unsigned short h = (unsigned short)(w & 1 ? ph[w / 2] >> 16 : ph[w / 2] & 0xffffu);
+    const unsigned short l = (unsigned short)(w & 1 ? pl[w / 2] >> 16 : pl[w / 2] & 0xffffu);
+    if (r0 + w <= c) {
+      hi[(int64_t)(r0 + w) * ld + c] = h;
+      lo[(int64_t)(r0 + w) * ld + c] = l;
+    }
+    if (r0 + w < c) {
+      hi[(int64_t)c * ld + r0 + w] = h;
+      lo[(int64_t)c * ld + r0 + w] = l;
+    }
+  }
+}
+
 template <bool kF16, int RB, int NF, bool kD>
 __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                               int lane) {
+                                               int lane, int sym) {
   static_assert(RB % 8 == 0 && 32 % RB == 0, "row batch");
   const int fi = P.f64_in;  // the FP64 input, or -1
   const int nf = P.nf32;    // FP32 inputs (<= NF)
@@ -686,18 +783,23 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
           }
 #pragma unroll
           for (int w = 0; w < 8; ++w) vf[w] = (float)v[w];
-          for (int d = 0; d < o.ndst; ++d) {
-            const EpiDst& ds = o.dst[d];
-            int64_t ld;
-            if (ds.dt == DT_F64) {
-              double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
+          if (sym == 2) {
+            st8_dst_diag(o, x, r0, c, vf, v);
+          } else {
+            for (int d = 0; d < o.ndst; ++d) {
+              const EpiDst& ds = o.dst[d];
+              int64_t ld;
+              if (ds.dt == DT_F64) {
+                double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
 #pragma unroll
-              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = v[w];
-            } else {
-              float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = v[w];
+              } else {
+                float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
 #pragma unroll
-              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+              }
             }
+            if (sym == 1) st8_mirror_dst(o, x, r0, c, vf, v);
           }
         } else {
           if (diag) {
@@ -719,18 +821,23 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
 #pragma unroll
             for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[fi], (float)din[h + w], vf[w]);
           }
-          for (int d = 0; d < o.ndst; ++d) {
-            const EpiDst& ds = o.dst[d];
-            int64_t ld;
-            if (ds.dt == DT_F64) {
-              double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
+          if (sym == 2) {
+            st8_dst_diag(o, x, r0, c, vf, nullptr);
+          } else {
+            for (int d = 0; d < o.ndst; ++d) {
+              const EpiDst& ds = o.dst[d];
+              int64_t ld;
+              if (ds.dt == DT_F64) {
+                double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
 #pragma unroll
-              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = (double)vf[w];
-            } else {
-              float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = (double)vf[w];
+              } else {
+                float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
 #pragma unroll
-              for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+              }
             }
+            if (sym == 1) st8_mirror_dst(o, x, r0, c, vf, nullptr);
           }
         }
 #pragma unroll
@@ -740,7 +847,14 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
 #pragma unroll
             for (int w = 0; w < 8; ++w) amax = fmaxf(amax, fabsf(vf[w]));
           }
-          for (int s2 = 0; s2 < o.nsplit; ++s2) st8_split<kF16>(o.split[s2], x, r0, c, vf);
+          for (int s2 = 0; s2 < o.nsplit; ++s2) {
+            if (sym == 2) {
+              st8_split_diag<kF16>(o.split[s2], x, r0, c, vf);
+            } else {
+              st8_split<kF16>(o.split[s2], x, r0, c, vf);
+              if (sym == 1) st8_split_mirror<kF16>(o.split[s2], x, r0, c, vf);
+            }
+          }
         }
       }
     }
@@ -750,10 +864,10 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
 
 template <bool kF16>
 __device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                               int lane) {
-  if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane);
-  if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane);
-  return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane);
+                                               int lane, int sym = 0) {
+  if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane, sym);
+  if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane, sym);
+  return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane, sym);
 }
 
 // Boundary chunks (padding, ragged edges, grouped row limits) and ops with
@@ -761,7 +875,7 @@ __device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx&
 // its registers then do not count against the lean path's.
 template <bool kF16>
 __device__ __noinline__ bool epi_chunk_generic(const EpiParams& P, EpiCtx x, int rbase, int c, const float* stg,
-                                               int lane, int lim) {
+                                               int lane, int lim, bool mirror) {
   bool bad = false;
 #pragma unroll 1
   for (int g = 0; g < 4; ++g) {
@@ -771,18 +885,42 @@ __device__ __noinline__ bool epi_chunk_generic(const EpiParams& P, EpiCtx x, int
 #pragma unroll
     for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
     bad |= epi_col<8, float, kF16>(P, x, r0, c, a8);
+    if (mirror) {  // the transposed element of a symmetric result, one at a time
+#pragma unroll 1
+      for (int w = 0; w < 8; ++w) bad |= epi_element<float, kF16>(P, x, c, r0 + w, a8[w]);
+    }
   }
   return bad;
 }
 
 // The epilogue of one staged 32 x 32 chunk (rows rbase .. rbase+31, this lane's
 // column c). Rows at or beyond `lim` (a grouped tile's limit) are not written.
+// A chunk on the diagonal of a symmetric product: each element on or above
+// the diagonal is written at its place, and those above it at the transpose
+// too, so that the result is exactly symmetric.
+template <bool kF16>
+__device__ __noinline__ bool epi_chunk_diag(const EpiParams& P, EpiCtx x, int rbase, int c, const float* stg,
+                                            int lane) {
+  bool bad = false;
+#pragma unroll 1
+  for (int i = 0; i < 32; ++i) {
+    const int r = rbase + i;
+    const float a = stg[i * 33 + lane];
+    if (r <= c) bad |= epi_element<float, kF16>(P, x, r, c, a);
+    if (r < c) bad |= epi_element<float, kF16>(P, x, c, r, a);
+  }
+  return bad;
+}
+
+// Symmetric products: sym = 0 for a chunk of a general product, 1 for a chunk
+// above the diagonal (also writes its transpose), 2 for a chunk on it.
 template <bool kF16>
 __device__ __forceinline__ bool epi_chunk(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                          int lane, int lim) {
+                                          int lane, int lim, int sym = 0) {
   if (P.fast && c < x.n && rbase + 32 <= x.n && rbase + 32 <= lim)
-    return epi_chunk_fast<kF16>(P, x, rbase, c, stg, lane);
-  return epi_chunk_generic<kF16>(P, x, rbase, c, stg, lane, lim);
+    return epi_chunk_fast<kF16>(P, x, rbase, c, stg, lane, sym);
+  if (sym == 2) return epi_chunk_diag<kF16>(P, x, rbase, c, stg, lane);
+  return epi_chunk_generic<kF16>(P, x, rbase, c, stg, lane, lim, sym == 1);
 }
 
 __device__ __forceinline__ void epi_flag(const EpiParams& P, bool bad) {

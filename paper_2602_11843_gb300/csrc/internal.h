@@ -100,12 +100,17 @@ struct EpiParams {
 // group: row tiles per group of the grouped raster of a single product.
 // precise: K accumulated in chunks summed with round-to-nearest (256 x 128
 // tiles on CTA pairs; the B maps have 64-row boxes).
+// sym: a symmetric product (pairs only): the device list of the nsym tiles
+// (tile row, tile column) on or above the diagonal; the tiles above it also
+// write their transpose.
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
   int fp16;
   int pair;
   int group;
   int precise;
+  const int2* sym;
+  int nsym;
 };
 
 constexpr int kDefaultRasterGroup = 8;

@@ -304,8 +304,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // K stages covering that matrix's order rounded up to 32).
 template <bool kGrouped>
 __device__ __forceinline__ void tile_of(int tile, const int4* tiles, int ktiles, int tiles_m, int tiles_n, int group,
-                                        int* mat, int* tm, int* tn, int* nk) {
-  if (kGrouped) {
+                                        int* mat, int* tm, int* tn, int* nk, const int2* sym = nullptr) {
+  if (!kGrouped && sym) {  // a symmetric product: the host's list of tiles on or above the diagonal
+    const int2 t = sym[tile];
+    *mat = 0;
+    *tm = t.x;
+    *tn = t.y;
+    *nk = ktiles;
+  } else if (kGrouped) {
     const int4 t = tiles[tile];
     *mat = t.x;
     *tm = t.y;
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
                          int ktiles, int tiles_m, int tiles_n, int group, const int4* __restrict__ tiles,
-                         int ntiles_grouped, const __grid_constant__ EpiParams P) {
+                         int ntiles_grouped, const int2* __restrict__ sym, const __grid_constant__ EpiParams P) {
   static_assert(!(kGrouped && kPair), "grouped launches use single-CTA tiles");
   using S = EpiShape<kGrouped, kPair>;
   constexpr int STAGES = S::kStages;
@@ -368,7 +374,8 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = kGrouped ? ntiles_grouped : tiles_m * tiles_n;
+  // a symmetric product runs only the ntiles_grouped tiles listed in `sym`
+  const int ntiles = (kGrouped || sym) ? ntiles_grouped : tiles_m * tiles_n;
   // Work items: one per CTA (single) or per cluster (pair); both CTAs of a
   // pair walk the same items, the odd one owning rows 128 .. 255 of each.
   const uint32_t rank = kPair ? cluster_rank() : 0u;
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
       }
       tc_fence_after();
       int mat, tm, tn, nk;
-      tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
+      tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk, sym);
       const EpiCtx x = epi_ctx(P, mat);
       const int rbase = tm * S::kTileM + (int)rank * BM + q * 32;
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
@@ -438,15 +445,20 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
       // rows and columns only feed accumulator entries every consumer discards.
       const int nchunks = kGrouped ? nk : BN / 32;
       const int lim = kGrouped ? nk * 32 : (1 << 30);
+      // symmetric product: chunks below the diagonal are left to their transpose
+      const int cdiag = kGrouped ? 0 : tn * BN - rbase;  // first column of the tile minus this warp's first row
 #pragma unroll 1
       for (int chunk = half; chunk < nchunks; chunk += kStep) {
+        const int rel = cdiag + chunk * 32;  // this chunk's first column minus its first row
+        if (sym && rel < 0) continue;        // below the diagonal
+        const int symc = !sym ? 0 : rel > 0 ? 1 : 2;
         uint32_t v[32];
         __syncwarp();
         tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
         __syncwarp();
-        bad |= epi_chunk<kF16>(P, x, rbase, tn * BN + chunk * 32 + lane, stg, lane, lim);
+        bad |= epi_chunk<kF16>(P, x, rbase, tn * BN + chunk * 32 + lane, stg, lane, lim, symc);
         __syncwarp();
       }
       tc_fence_before();
@@ -472,7 +484,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
       bool ok = true;
       for (int tile = first; tile < ntiles && ok; tile += stride) {
         int mat, tm, tn, nk;
-        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
+        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk, sym);
         const int ra = tm * S::kTileM + (int)rank * BM;
         const int rb = tn * BN + (int)rank * S::kBRows;
         for (int kb = 0; kb < nk; ++kb) {
@@ -516,7 +528,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
         }
         tc_fence_after();
         int mat, tm, tn, nk;
-        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk);
+        tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk, sym);
         const uint32_t d = tmem + buf * ACC_COLS;
         for (int kb = 0; kb < nk; ++kb) {
           const uint32_t s = kg % STAGES;
@@ -910,6 +922,8 @@ bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, i
   if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0 || group < 1) return false;
   m->fp16 = fp16;
   m->precise = precise && count == 0;
+  m->sym = nullptr;  // set by the caller for a symmetric product on pairs
+  m->nsym = 0;
   m->pair = count == 0 && (m->precise || (pair_mode < 0 ? tc_uses_pair(npad, count) : pair_mode > 0));
   m->group = group;
   const uint32_t brows = m->precise ? PQ_BROWS : m->pair ? BN / 2 : BN;
@@ -970,10 +984,11 @@ cudaError_t launch_pair(const TcMaps& maps, int64_t npad, const EpiParams& P, cu
     if (nc <= 0) return cudaErrorInvalidConfiguration;
     max_pairs = nc;
   }
-  const int pairs = tiles_m * tiles_n < max_pairs ? tiles_m * tiles_n : max_pairs;
+  const int work = maps.sym ? maps.nsym : tiles_m * tiles_n;
+  const int pairs = work < max_pairs ? work : max_pairs;
   cfg.gridDim = dim3(2 * pairs);
   return cudaLaunchKernelEx(&cfg, k, maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n,
-                            maps.group, (const int4*)nullptr, 0, P);
+                            maps.group, (const int4*)nullptr, maps.nsym, maps.sym, P);
 }
 
 template <bool kF16>
@@ -1030,7 +1045,7 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
     const int grid = ntiles < sms ? ntiles : sms;
     auto k = maps.fp16 ? tc_split_gemm_kernel<true, true, false> : tc_split_gemm_kernel<true, false, false>;
     k<<<grid, EpiShape<true, false>::kThreads, EpiShape<true, false>::kSmem, s>>>(
-        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, 1, tiles, ntiles, P);
+        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, 1, tiles, ntiles, (const int2*)nullptr, P);
     return cudaGetLastError();
   }
   if (maps.precise)
@@ -1040,7 +1055,8 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   const int grid = tiles_m * tiles_n < sms ? tiles_m * tiles_n : sms;
   auto k = maps.fp16 ? tc_split_gemm_kernel<false, true, false> : tc_split_gemm_kernel<false, false, false>;
   k<<<grid, EpiShape<false, false>::kThreads, EpiShape<false, false>::kSmem, s>>>(
-      maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, maps.group, nullptr, 0, P);
+      maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, maps.group, nullptr, 0,
+      (const int2*)nullptr, P);
   return cudaGetLastError();
 }
 

@@ -169,6 +169,11 @@ struct neumann_plan_s {
   int timed = 0;
   // launch configuration of the tensor-core products, set by the autotuner or
   // taken from an earlier tuning of the same shape in this process
+  // NEUMANN_FLAG_SYMMETRIC on a split single plan: the scheme's products run
+  // only the tiles on or above the diagonal (list at off_sym, nsym entries)
+  bool sym = false;
+  size_t off_sym = 0;
+  int nsym = 0;
   int tune_pair = -1;                    // -1: CTA pairs from padded order 4096; 0 never; 1 always
   int tune_group = kDefaultRasterGroup;  // row tiles per raster group of a single product
   int chunk_run = 0;                     // grouped batches: matrices per pass (0: chunk)
@@ -515,11 +520,13 @@ struct Sched {
 
 // ---------------------------------------------------------------- layout
 
-void note_reps(neumann_plan_s* p, const std::vector<Op>& ops) {
+// sym: every matrix of the scheme is symmetric, so a product's right operand
+// is read from its row-major pair (B^T = B).
+void note_reps(neumann_plan_s* p, const std::vector<Op>& ops, bool sym = false) {
   for (const Op& op : ops) {
     if (op.kind == OP_GEMM) {
       p->reps[op.a] |= REP_OPA;
-      p->reps[op.b] |= REP_OPB;
+      p->reps[op.b] |= sym ? REP_OPA : REP_OPB;
     }
     for (int i = 0; i < op.nin; ++i)
       if (op.in[i].slot >= 0) p->reps[op.in[i].slot] |= op.in[i].rep;
@@ -547,6 +554,11 @@ void layout(neumann_plan_s* p) {
     p->off_tc = take(c * tiles_per * sizeof(int4));
     p->off_simt = take(c * tiles_per * sizeof(int4));
     p->off_ew = take(c * (size_t)(p->npad / 32) * (size_t)(p->npad / 32) * sizeof(int4));
+  }
+  if (p->sym) {
+    const int t = (int)(p->npad / 256);
+    p->nsym = t * (t + 1) / 2;
+    p->off_sym = take((size_t)p->nsym * sizeof(int2));
   }
   for (int s = 0; s < SL_N; ++s) {
     SlotBufs& b = p->bufs[s];
@@ -590,8 +602,13 @@ int build(neumann_plan_s* p) {
     sc.levels();
   }
   sc.matmul();
+  if (p->sym) {  // symmetric matrices: the transposed pairs equal the row-major ones
+    for (Op& op : p->ops)
+      for (int j = 0; j < op.nout; ++j)
+        if (op.out[j].reps & REP_OPB) op.out[j].reps = (op.out[j].reps & ~REP_OPB) | REP_OPA;
+  }
   memset(p->reps, 0, sizeof(p->reps));
-  note_reps(p, p->ops);
+  note_reps(p, p->ops, p->sym);
   note_reps(p, p->mm_ops);
   layout(p);
   return NEUMANN_OK;
@@ -650,6 +667,8 @@ int init_plan(neumann_plan_s* p, int64_t n, int64_t k, int radix, int dtype, uin
   p->npad = (n + 255) / 256 * 256;
   p->path = dtype == NEUMANN_FP64 ? PATH_F64 : dtype == NEUMANN_FP32 ? PATH_F32 : PATH_TC;
   p->dt_io = (dtype == NEUMANN_FP32 || (p->path == PATH_TC && (flags & NEUMANN_FLAG_IO_FP32))) ? DT_F32 : DT_F64;
+  if ((flags & NEUMANN_FLAG_SYMMETRIC) && (flags & NEUMANN_FLAG_PRECISE_ACC)) return NEUMANN_ENOTSUP;
+  p->sym = (flags & NEUMANN_FLAG_SYMMETRIC) && p->path == PATH_TC;
   int rc = validate_and_levels(p);
   if (rc) return rc;
   if (radix == 15 || radix == 0) {
@@ -806,27 +825,53 @@ int64_t op_bytes(const neumann_plan_s* p, const Op& op) {
   return b;
 }
 
-bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMaps>* maps) {
+// sym: the ops are the scheme's products of a symmetric plan (right operands
+// read from their row-major pairs, only the tiles on or above the diagonal).
+bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMaps>* maps, bool sym = false) {
   maps->assign(ops.size(), TcMaps());
   for (size_t i = 0; i < ops.size(); ++i) {
     const Op& op = ops[i];
     if (op.kind != OP_GEMM) continue;
     const SlotBufs& a = p->bufs[op.a];
     const SlotBufs& b = p->bufs[op.b];
-    if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + b.b_hi, p->ws + b.b_lo, p->npad,
-                      p->npad, p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16,
-                      (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0 : p->tune_pair, p->tune_group,
+    const size_t bhi = sym ? b.a_hi : b.b_hi, blo = sym ? b.a_lo : b.b_lo;
+    if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + bhi, p->ws + blo, p->npad, p->npad,
+                      p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16,
+                      sym ? 1 : (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0 : p->tune_pair, p->tune_group,
                       (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0))
       return false;
+    if (sym) {
+      (*maps)[i].sym = reinterpret_cast<const int2*>(p->ws + p->off_sym);
+      (*maps)[i].nsym = p->nsym;
+    }
   }
   return true;
+}
+
+// The tiles on or above the diagonal of a symmetric product, in groups of 8
+// tile rows; within a group column by column, so that neighbouring clusters
+// share panels in L2.
+std::vector<int2> sym_tiles(int t) {
+  std::vector<int2> v;
+  v.reserve((size_t)t * (t + 1) / 2);
+  for (int g0 = 0; g0 < t; g0 += kDefaultRasterGroup) {
+    const int g1 = std::min(t, g0 + kDefaultRasterGroup);
+    for (int tn = g0; tn < t; ++tn)
+      for (int tm = g0; tm < g1 && tm <= tn; ++tm) v.push_back(make_int2(tm, tn));
+  }
+  return v;
 }
 
 int attach(neumann_plan_s* p, void* ws) {
   p->ws = reinterpret_cast<char*>(ws);
   p->maps_ready = false;
+  if (p->sym) {
+    const std::vector<int2> t = sym_tiles((int)(p->npad / 256));
+    if (cudaMemcpy(p->ws + p->off_sym, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return NEUMANN_ECUDA;
+  }
   if (p->path == PATH_TC) {
-    if (!build_maps(p, p->ops, &p->maps) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
+    if (!build_maps(p, p->ops, &p->maps, p->sym) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
   }
   p->maps_ready = true;
   return NEUMANN_OK;
@@ -1083,7 +1128,7 @@ std::map<std::tuple<int, int64_t, int64_t, int, int>, int> g_tune_batched;
 // Single products are keyed by padded order and dtype; precise-accumulation
 // plans run another kernel and are keyed apart.
 std::pair<int64_t, int> tune_key(const neumann_plan_s* p) {
-  return std::make_pair(p->npad, p->dtype + ((p->flags & NEUMANN_FLAG_PRECISE_ACC) ? 16 : 0));
+  return std::make_pair(p->npad, p->dtype + ((p->flags & NEUMANN_FLAG_PRECISE_ACC) ? 16 : 0) + (p->sym ? 32 : 0));
 }
 
 void apply_tuned(neumann_plan_s* p) {
@@ -1146,7 +1191,7 @@ int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t
   EventPair ev;
   if (!ev.ok()) return NEUMANN_ECUDA;
   std::vector<std::pair<int, int>> cand;
-  const bool precise = (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0;  // always CTA pairs
+  const bool precise = (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0 || p->sym;  // always CTA pairs
   for (int pair = precise ? 1 : 0; pair <= 1; ++pair) {
     if (pair && (p->flags & NEUMANN_FLAG_SINGLE_CTA) && !precise) continue;
     for (int g : {4, 8, 16}) cand.emplace_back(pair, g);
@@ -1156,7 +1201,7 @@ int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t
   for (size_t i = 0; i < cand.size(); ++i) {
     p->tune_pair = cand[i].first;
     p->tune_group = cand[i].second;
-    if (!build_maps(p, p->ops, &p->maps) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
+    if (!build_maps(p, p->ops, &p->maps, p->sym) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
     float ms = 0.f;
     rc = time_runs([&] { return eval_one(p, A, lda, S, lds, s); }, reps, s, ev.e0, ev.e1, &ms);
     if (rc) return rc;
@@ -1167,7 +1212,7 @@ int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t
   }
   p->tune_pair = pick.first;
   p->tune_group = pick.second;
-  if (!build_maps(p, p->ops, &p->maps) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
+  if (!build_maps(p, p->ops, &p->maps, p->sym) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
   p->timed = 0;  // tuning runs are not part of a NEUMANN_FLAG_TIMING record
   p->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1254,7 +1299,7 @@ int neumann_plan_info(neumann_plan_t p, neumann_plan_info_t* info) {
   info->workspace_bytes = p->ws_bytes;
   info->padded_n = p->npad;
   if (p->path == PATH_TC && !p->grouped && !p->batched) {
-    info->tile_pair = (p->flags & NEUMANN_FLAG_PRECISE_ACC) ? 1
+    info->tile_pair = ((p->flags & NEUMANN_FLAG_PRECISE_ACC) || p->sym) ? 1
                       : (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0
                       : p->tune_pair < 0                     ? (int)tc_uses_pair(p->npad, 0)
                                                              : p->tune_pair;
@@ -1477,8 +1522,11 @@ int neumann_plan_create_batched(neumann_plan_t* out, int count, int64_t max_n, i
   *out = nullptr;
   if (count < 0) return NEUMANN_EINVAL;
   neumann_plan_t p = nullptr;
-  int rc = neumann_plan_create(&p, max_n, k, radix, dtype, flags);
+  // a grouped pass over orders <= 256 has no symmetric path (its products run whole slabs)
+  const bool grouped = max_n <= kGroupedMaxN && count > 0;
+  int rc = neumann_plan_create(&p, max_n, k, radix, dtype, grouped ? (flags & ~NEUMANN_FLAG_SYMMETRIC) : flags);
   if (rc) return rc;
+  p->flags = flags;
   p->batched = true;
   p->count = count;
   p->max_n = max_n;
