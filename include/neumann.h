@@ -85,14 +85,14 @@ typedef enum {
 #define NEUMANN_FLAG_IO_FP32 0x10u        /* split dtypes: A and S are float instead of double */
 #define NEUMANN_FLAG_SINGLE_CTA 0x20u     /* split dtypes: keep every product on single-CTA 128 x 256 tiles
                                              (by default padded orders >= 4096 use 2-CTA 256 x 256 tiles) */
-#define NEUMANN_FLAG_SYMMETRIC 0x80u      /* split dtypes, single plans: A is symmetric, so is every matrix of the
-                                             scheme (each is a polynomial in A): products compute only the
-                                             256 x 256 tiles on or above the diagonal and write their
-                                             transposes, and right operands are read from the row-major hi/lo
-                                             pairs. About half the tensor work. A must be symmetric (the result
-                                             is otherwise unspecified); exactly symmetric S. Not with
-                                             NEUMANN_FLAG_PRECISE_ACC; ignored by FP64/FP32 plans and grouped
-                                             batches */
+#define NEUMANN_FLAG_SYMMETRIC 0x80u      /* single plans: A is symmetric, so is every matrix of the scheme (each
+                                             is a polynomial in A): products compute only the tiles on or above
+                                             the diagonal (256 x 256 CTA pairs for split dtypes, 128 x 128 for
+                                             FP64/FP32) and write their transposes; split right operands are
+                                             read from the row-major hi/lo pairs. About half the product work.
+                                             A must be symmetric (the result is otherwise unspecified); S is
+                                             exactly symmetric. Not with NEUMANN_FLAG_PRECISE_ACC; ignored by
+                                             grouped batches */
 #define NEUMANN_FLAG_PRECISE_ACC 0x40u    /* split dtypes: products accumulate K in chunks of 512, each chunk
                                              added to the running FP32 sum with round-to-nearest. The tensor
                                              cores' accumulator rounds every update toward zero, a bias of about

@@ -118,10 +118,12 @@ constexpr int kDefaultRasterGroup = 8;
 // ---- launchers (kernels_simt.cu) ----
 // tiles == nullptr: one padded npad x npad product. Otherwise a grouped launch
 // over a batch: ntiles entries {matrix, tile row, tile column, K steps of 8}.
+// sym (single products only): the product is symmetric; only the 128 x 128
+// tiles on or above the diagonal run, writing their transposes too.
 cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad, const int4* tiles,
-                                 int ntiles, const EpiParams& P, cudaStream_t s);
+                                 int ntiles, const EpiParams& P, cudaStream_t s, bool sym = false);
 cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad, const int4* tiles,
-                                 int ntiles, const EpiParams& P, cudaStream_t s);
+                                 int ntiles, const EpiParams& P, cudaStream_t s, bool sym = false);
 // Element-wise epilogue with acc = 0: over the npad x npad elements, or (grouped)
 // over ntiles 32 x 32 tiles {matrix, tile row, tile column}.
 cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles = nullptr, int ntiles = 0);

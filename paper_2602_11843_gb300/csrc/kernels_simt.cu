@@ -36,13 +36,25 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
 template <typename T>
 __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
     simt_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, int64_t ld, int ktiles,
-                     const int4* __restrict__ tiles, const __grid_constant__ EpiParams P) {
+                     const int4* __restrict__ tiles, int sym, const __grid_constant__ EpiParams P) {
   __shared__ __align__(16) T As[2][BK][BM + 4];
   __shared__ __align__(16) T Bs[2][BK][BN];
   extern __shared__ float acc_smem[];  // FP32: running sums, [64][TPB] (element e of thread t at e * TPB + t)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   int mat = 0, tm = blockIdx.y, tn = blockIdx.x;
+  if (sym) {
+    // a symmetric product (every matrix of the scheme is a polynomial in the
+    // symmetric A): block b takes the b-th tile on or above the diagonal, row
+    // by row; `sym` is the number of tile rows
+    int t = blockIdx.x;
+    tm = 0;
+    while (t >= sym - tm) {
+      t -= sym - tm;
+      ++tm;
+    }
+    tn = tm + t;
+  }
   if (tiles) {
     const int4 t = tiles[blockIdx.x];
     mat = t.x;
@@ -161,7 +173,19 @@ __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
         else
           a4[j] = acc[i][4 * h + j];
       }
-      bad |= epi_row<4, T, false>(P, x, r, c0, a4);
+      if (!sym) {
+        bad |= epi_row<4, T, false>(P, x, r, c0, a4);
+      } else if (tm != tn) {  // above the diagonal: this run, then its transpose
+        bad |= epi_row<4, T, false>(P, x, r, c0, a4);
+#pragma unroll 1
+        for (int j = 0; j < 4; ++j) bad |= epi_element<T, false>(P, x, c0 + j, r, a4[j]);
+      } else {  // on the diagonal tile: r <= c at its place, r < c at the transpose too
+#pragma unroll 1
+        for (int j = 0; j < 4; ++j) {
+          if (r <= c0 + j) bad |= epi_element<T, false>(P, x, r, c0 + j, a4[j]);
+          if (r < c0 + j) bad |= epi_element<T, false>(P, x, c0 + j, r, a4[j]);
+        }
+      }
     }
   }
   epi_flag(P, bad);
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
 
 template <typename T>
 cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const int4* tiles, int ntiles,
-                        const EpiParams& P, cudaStream_t s) {
+                        const EpiParams& P, cudaStream_t s, bool sym) {
   if (npad % BM != 0 || npad % BN != 0 || ld < npad) return cudaErrorInvalidValue;
   // FP32: 64 running sums per thread in dynamic shared memory (64 KB)
   constexpr size_t dyn = sizeof(T) == 4 ? 64 * TPB * sizeof(float) : 0;
@@ -230,10 +254,13 @@ cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const 
   }
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
-    simt_gemm_kernel<T><<<ntiles, TPB, dyn, s>>>(A, B, ld, 0, tiles, P);
+    simt_gemm_kernel<T><<<ntiles, TPB, dyn, s>>>(A, B, ld, 0, tiles, 0, P);
+  } else if (sym) {
+    const int t = (int)(npad / BM);
+    simt_gemm_kernel<T><<<t * (t + 1) / 2, TPB, dyn, s>>>(A, B, ld, (int)(npad / BK), nullptr, t, P);
   } else {
     dim3 grid((unsigned)(npad / BN), (unsigned)(npad / BM));
-    simt_gemm_kernel<T><<<grid, TPB, dyn, s>>>(A, B, ld, (int)(npad / BK), nullptr, P);
+    simt_gemm_kernel<T><<<grid, TPB, dyn, s>>>(A, B, ld, (int)(npad / BK), nullptr, 0, P);
   }
   return cudaGetLastError();
 }
@@ -241,13 +268,13 @@ cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const 
 }  // namespace
 
 cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad, const int4* tiles,
-                                 int ntiles, const EpiParams& P, cudaStream_t s) {
-  return launch_simt<double>(A, B, ld, npad, tiles, ntiles, P, s);
+                                 int ntiles, const EpiParams& P, cudaStream_t s, bool sym) {
+  return launch_simt<double>(A, B, ld, npad, tiles, ntiles, P, s, sym);
 }
 
 cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad, const int4* tiles,
-                                 int ntiles, const EpiParams& P, cudaStream_t s) {
-  return launch_simt<float>(A, B, ld, npad, tiles, ntiles, P, s);
+                                 int ntiles, const EpiParams& P, cudaStream_t s, bool sym) {
+  return launch_simt<float>(A, B, ld, npad, tiles, ntiles, P, s, sym);
 }
 
 cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles) {

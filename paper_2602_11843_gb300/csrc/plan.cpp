@@ -555,7 +555,7 @@ void layout(neumann_plan_s* p) {
     p->off_simt = take(c * tiles_per * sizeof(int4));
     p->off_ew = take(c * (size_t)(p->npad / 32) * (size_t)(p->npad / 32) * sizeof(int4));
   }
-  if (p->sym) {
+  if (p->sym && p->path == PATH_TC) {
     const int t = (int)(p->npad / 256);
     p->nsym = t * (t + 1) / 2;
     p->off_sym = take((size_t)p->nsym * sizeof(int2));
@@ -668,7 +668,7 @@ int init_plan(neumann_plan_s* p, int64_t n, int64_t k, int radix, int dtype, uin
   p->path = dtype == NEUMANN_FP64 ? PATH_F64 : dtype == NEUMANN_FP32 ? PATH_F32 : PATH_TC;
   p->dt_io = (dtype == NEUMANN_FP32 || (p->path == PATH_TC && (flags & NEUMANN_FLAG_IO_FP32))) ? DT_F32 : DT_F64;
   if ((flags & NEUMANN_FLAG_SYMMETRIC) && (flags & NEUMANN_FLAG_PRECISE_ACC)) return NEUMANN_ENOTSUP;
-  p->sym = (flags & NEUMANN_FLAG_SYMMETRIC) && p->path == PATH_TC;
+  p->sym = (flags & NEUMANN_FLAG_SYMMETRIC) != 0;
   int rc = validate_and_levels(p);
   if (rc) return rc;
   if (radix == 15 || radix == 0) {
@@ -865,7 +865,7 @@ std::vector<int2> sym_tiles(int t) {
 int attach(neumann_plan_s* p, void* ws) {
   p->ws = reinterpret_cast<char*>(ws);
   p->maps_ready = false;
-  if (p->sym) {
+  if (p->sym && p->path == PATH_TC) {
     const std::vector<int2> t = sym_tiles((int)(p->npad / 256));
     if (cudaMemcpy(p->ws + p->off_sym, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
       return NEUMANN_ECUDA;
@@ -935,14 +935,16 @@ int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcM
       err = launch_ewise(P, s, ew, p->n_ew);
     } else {
       if (timing) cudaEventRecord(p->events[2 * gi], s);
+      // the scheme's products of a symmetric plan (not the general product call)
+      const bool sym = p->sym && &ops == &p->ops;
       if (p->path == PATH_F64) {
         err = launch_simt_gemm_f64(reinterpret_cast<const double*>(p->ws + p->bufs[op.a].w),
                                    reinterpret_cast<const double*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, st,
-                                   p->n_simt, P, s);
+                                   p->n_simt, P, s, sym);
       } else if (p->path == PATH_F32) {
         err = launch_simt_gemm_f32(reinterpret_cast<const float*>(p->ws + p->bufs[op.a].w),
                                    reinterpret_cast<const float*>(p->ws + p->bufs[op.b].w), p->npad, p->npad, st,
-                                   p->n_simt, P, s);
+                                   p->n_simt, P, s, sym);
       } else {
         err = launch_tc_gemm(maps[i], p->npad, P, s, tt, p->n_tc);
       }

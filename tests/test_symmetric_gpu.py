@@ -1,6 +1,7 @@
 """GPU checks of NEUMANN_FLAG_SYMMETRIC: for symmetric A every matrix of the
 scheme is a polynomial in A and so symmetric; the products compute only the
-256 x 256 tiles on or above the diagonal and write their transposes.
+tiles on or above the diagonal (256 x 256 CTA pairs for the split dtypes,
+128 x 128 SIMT tiles for FP64 / FP32) and write their transposes.
 
 Checked against the closed form at orders with ragged tiles and at full
 tiles, for exact symmetry of S, against the general path, with a strided
@@ -51,6 +52,24 @@ def test_symmetric_matches_closed_form(dtype, n, radix, k):
     print(f"n={n} radix {radix} k {k} {dtype}: symmetric {e_sym:.3e} general {e_gen:.3e}")
     assert torch.equal(S_sym, S_sym.T)
     assert e_sym < TOL[dtype] and e_sym < 2 * e_gen + 1e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("n,radix,k", [(300, 9, 81), (1000, 15, 225), (1024, 2, 256)])
+def test_symmetric_simt_paths(dtype, tol, n, radix, k):
+    """FP64 and FP32: 128 x 128 SIMT tiles on or above the diagonal."""
+    nm = _nm()
+    pl = G.config_inputs(2, n=n)
+    ref = EV.planted_reference(pl["V"], pl["lam"], k, radix)
+    p = nm.Plan(n, k, radix, dtype, nm.FLAG_SYMMETRIC)
+    A = torch.tensor(pl["A"], dtype=p.io_dtype, device="cuda")
+    S = p(A)
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    assert torch.equal(S, S.T)
+    err = CF.rel_fro(S.double().cpu().numpy(), ref)
+    print(f"n={n} radix {radix} k {k} {dtype} symmetric: {err:.3e}")
+    assert err < tol
 
 
 def test_symmetric_strided_output():
