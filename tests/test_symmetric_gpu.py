@@ -128,3 +128,28 @@ def test_symmetric_cfg3_full(dtype):
     err = CF.rel_fro(S.cpu().numpy(), ref)
     print(f"cfg3 symmetric {dtype} rel err {err:.3e}")
     assert torch.equal(S, S.T) and err < 3e-3
+
+
+@pytest.mark.parametrize("dtype", ["split_bf16", "fp64"])
+@pytest.mark.parametrize("radix,k,extra", [(1, 81, 0), (2, 64, 0), (2, 81, "exact"), (3, 27, 0), (5, 125, 0),
+                                           (0, 360, 0), (9, 81, "paper"), (15, 225, "printed"),
+                                           (9, 729, "io32")])
+def test_symmetric_every_scheme(dtype, radix, k, extra):
+    """Every scheme and the flags that change the ops (exact-k binary, the
+    paper-form residual, printed radix-15 coefficients, FP32 input/output)."""
+    nm = _nm()
+    flags = nm.FLAG_SYMMETRIC | {0: 0, "exact": nm.FLAG_EXACT_K, "paper": nm.FLAG_RESIDUAL_PAPER,
+                                 "printed": nm.FLAG_PRINTED_COEFFS, "io32": nm.FLAG_IO_FP32}[extra]
+    if extra == "io32" and dtype == "fp64":
+        flags &= ~nm.FLAG_IO_FP32
+    pl = G.config_inputs(2, n=300)
+    coef = "printed" if extra == "printed" else "refined"
+    ref = EV.planted_reference(pl["V"], pl["lam"], k, radix, coef15=coef)
+    p = nm.Plan(300, k, radix, dtype, flags)
+    A = torch.tensor(pl["A"], dtype=p.io_dtype, device="cuda")
+    S = p(A)
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    assert torch.equal(S, S.T)
+    err = CF.rel_fro(S.double().cpu().numpy(), ref)
+    assert err < (1e-12 if dtype == "fp64" else 1e-3), err
