@@ -111,6 +111,7 @@ struct TcMaps {
   int precise;
   const int2* sym;
   int nsym;
+  int b_mn;  // B is read MN-major from its row-major pair (bt_* are then row-major arrays of B)
 };
 
 constexpr int kDefaultRasterGroup = 8;
@@ -136,7 +137,7 @@ cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles =
 // products only). group: row tiles per raster group (>= 1).
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
                   int count = 0, int fp16 = 0, int pair_mode = -1, int group = kDefaultRasterGroup,
-                  int precise = 0);
+                  int precise = 0, int b_mn = 0);
 // Whether a product of padded order npad (count = 0: single matrix) runs on CTA pairs.
 bool tc_uses_pair(int64_t npad, int count);
 // tiles == nullptr: one npad x npad product. Otherwise a grouped launch over a

@@ -164,6 +164,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
+// MN-major operand tile (B read from its row-major hi/lo pair, B^T never
+// stored): strips of 32 columns (64-byte rows, 64B swizzle) of 32 K rows each,
+// strip after strip. Leading byte offset: from one 32-column strip to the
+// next along N (2048); stride byte offset: from one 8-row K group to the next
+// (512).
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(2048 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // One MMA instruction D (+)= A B^T of the launch shape: cta_group::1 with
 // M = 128, or cta_group::2 with M = 256 issued by the even CTA of a pair.
 template <bool kPair>
@@ -258,6 +273,24 @@ __device__ __forceinline__ void cluster_sync() {
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z,
+                                            int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, uint32_t cluster_bar, int x,
+                                                 int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(cluster_bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
 // TMA load into this CTA's shared memory whose completion is counted on the
 // even CTA's barrier (`cluster_bar`, an address in the cluster window).
 __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t cluster_bar, int x,
@@ -327,25 +360,43 @@ __device__ __forceinline__ void tile_of(int tile, const int4* tiles, int ktiles,
 // The four operand tiles of K stage `kb` of a work item: rows `ra` of A
 // (hi, lo) and rows `rb` of the stored B^T (hi, lo), 32 deep.
 template <bool kGrouped, bool kPair>
+// bmn: B is read MN-major from its row-major pair (columns rb .. of rows
+// kb*32 ..) as 32-column strips; otherwise K-major from the stored B^T (rows rb ..).
 __device__ __forceinline__ void load_stage(uint32_t st, const CUtensorMap* ahi, const CUtensorMap* alo,
                                            const CUtensorMap* bhi, const CUtensorMap* blo, uint32_t bar, int kb,
-                                           int ra, int rb, int mat) {
+                                           int ra, int rb, int mat, bool bmn) {
   using S = EpiShape<kGrouped, kPair>;
+  const uint32_t sb = st + 2 * A_TILE;
   if constexpr (kGrouped) {
     tma_load_3d(st, ahi, bar, kb * BK, ra, mat);
     tma_load_3d(st + A_TILE, alo, bar, kb * BK, ra, mat);
-    tma_load_3d(st + 2 * A_TILE, bhi, bar, kb * BK, rb, mat);
-    tma_load_3d(st + 2 * A_TILE + S::kBTile, blo, bar, kb * BK, rb, mat);
+    if (bmn) {
+      tma_load_4d(sb, bhi, bar, 0, kb * BK, rb / 32, mat);
+      tma_load_4d(sb + S::kBTile, blo, bar, 0, kb * BK, rb / 32, mat);
+    } else {
+      tma_load_3d(sb, bhi, bar, kb * BK, rb, mat);
+      tma_load_3d(sb + S::kBTile, blo, bar, kb * BK, rb, mat);
+    }
   } else if constexpr (kPair) {
     tma_load_2d_pair(st, ahi, bar, kb * BK, ra);
     tma_load_2d_pair(st + A_TILE, alo, bar, kb * BK, ra);
-    tma_load_2d_pair(st + 2 * A_TILE, bhi, bar, kb * BK, rb);
-    tma_load_2d_pair(st + 2 * A_TILE + S::kBTile, blo, bar, kb * BK, rb);
+    if (bmn) {
+      tma_load_3d_pair(sb, bhi, bar, 0, kb * BK, rb / 32);
+      tma_load_3d_pair(sb + S::kBTile, blo, bar, 0, kb * BK, rb / 32);
+    } else {
+      tma_load_2d_pair(sb, bhi, bar, kb * BK, rb);
+      tma_load_2d_pair(sb + S::kBTile, blo, bar, kb * BK, rb);
+    }
   } else {
     tma_load_2d(st, ahi, bar, kb * BK, ra);
     tma_load_2d(st + A_TILE, alo, bar, kb * BK, ra);
-    tma_load_2d(st + 2 * A_TILE, bhi, bar, kb * BK, rb);
-    tma_load_2d(st + 2 * A_TILE + S::kBTile, blo, bar, kb * BK, rb);
+    if (bmn) {
+      tma_load_3d(sb, bhi, bar, 0, kb * BK, rb / 32);
+      tma_load_3d(sb + S::kBTile, blo, bar, 0, kb * BK, rb / 32);
+    } else {
+      tma_load_2d(sb, bhi, bar, kb * BK, rb);
+      tma_load_2d(sb + S::kBTile, blo, bar, kb * BK, rb);
+    }
   }
 }
 
@@ -360,7 +411,8 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
     tc_split_gemm_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                          const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
                          int ktiles, int tiles_m, int tiles_n, int group, const int4* __restrict__ tiles,
-                         int ntiles_grouped, const int2* __restrict__ sym, const __grid_constant__ EpiParams P) {
+                         int ntiles_grouped, const int2* __restrict__ sym, int bmn,
+                         const __grid_constant__ EpiParams P) {
   static_assert(!(kGrouped && kPair), "grouped launches use single-CTA tiles");
   using S = EpiShape<kGrouped, kPair>;
   constexpr int STAGES = S::kStages;
@@ -497,7 +549,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
           const uint32_t st = smem_base + s * STAGE_BYTES;
           if (leader) mbar_expect_tx(full_bar(s), STAGE_BYTES * (kPair ? 2u : 1u));
           load_stage<kGrouped, kPair>(st, &tm_ahi, &tm_alo, &tm_bhi, &tm_blo, lead_bar_base + 8u * s, kb, ra, rb,
-                                      mat);
+                                      mat, bmn != 0);
           ++kg;
         }
       }
@@ -543,11 +595,14 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
           for (int j = 0; j < BK / 16; ++j) {
             const uint64_t a_hi = smem_desc(st + 32u * j);
             const uint64_t a_lo = smem_desc(st + A_TILE + 32u * j);
-            const uint64_t b_hi = smem_desc(st + 2 * A_TILE + 32u * j);
-            const uint64_t b_lo = smem_desc(st + 2 * A_TILE + S::kBTile + 32u * j);
-            umma_f16<kPair>(d, a_hi, b_hi, idesc, (kb | j) != 0);
-            umma_f16<kPair>(d, a_hi, b_lo, idesc, 1u);
-            umma_f16<kPair>(d, a_lo, b_hi, idesc, 1u);
+            const uint32_t sb = st + 2 * A_TILE;
+            // MN-major B: K slice j starts 16 rows (1 KiB) into every strip
+            const uint64_t b_hi = bmn ? smem_desc_mn(sb + 1024u * j) : smem_desc(sb + 32u * j);
+            const uint64_t b_lo = bmn ? smem_desc_mn(sb + S::kBTile + 1024u * j) : smem_desc(sb + S::kBTile + 32u * j);
+            const uint32_t id = idesc | (bmn ? (1u << 16) : 0u);  // bit 16: B is MN-major
+            umma_f16<kPair>(d, a_hi, b_hi, id, (kb | j) != 0);
+            umma_f16<kPair>(d, a_hi, b_lo, id, 1u);
+            umma_f16<kPair>(d, a_lo, b_hi, id, 1u);
           }
           umma_commit<kPair>(empty_bar(s));  // frees the stage in both CTAs of a pair
           ++kg;
@@ -628,8 +683,10 @@ template <bool kF16>
 __global__ void __launch_bounds__(PQ_THREADS, 1)
     tc_precise_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                       const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
-                      int ktiles, int tiles_m, int tiles_n, int group, const __grid_constant__ EpiParams P) {
-  constexpr uint32_t idesc = make_idesc_mn(kF16, 2 * BM, PQ_N);
+                      int ktiles, int tiles_m, int tiles_n, int group, int bmn,
+                      const __grid_constant__ EpiParams P) {
+  constexpr uint32_t idesc0 = make_idesc_mn(kF16, 2 * BM, PQ_N);
+  const uint32_t idesc = idesc0 | (bmn ? (1u << 16) : 0u);  // bit 16: B is MN-major
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // barriers: full[8], empty[8], xfull[2], xempty[2], sfull[2], sempty[2], drain
@@ -738,8 +795,13 @@ __global__ void __launch_bounds__(PQ_THREADS, 1)
           const uint32_t fb = lead_bar_base + 8u * st;
           tma_load_2d_pair(sa, &tm_ahi, fb, kb * BK, ra);
           tma_load_2d_pair(sa + A_TILE, &tm_alo, fb, kb * BK, ra);
-          tma_load_2d_pair(sa + 2 * A_TILE, &tm_bhi, fb, kb * BK, rb);
-          tma_load_2d_pair(sa + 2 * A_TILE + PQ_BTILE, &tm_blo, fb, kb * BK, rb);
+          if (bmn) {
+            tma_load_3d_pair(sa + 2 * A_TILE, &tm_bhi, fb, 0, kb * BK, rb / 32);
+            tma_load_3d_pair(sa + 2 * A_TILE + PQ_BTILE, &tm_blo, fb, 0, kb * BK, rb / 32);
+          } else {
+            tma_load_2d_pair(sa + 2 * A_TILE, &tm_bhi, fb, kb * BK, rb);
+            tma_load_2d_pair(sa + 2 * A_TILE + PQ_BTILE, &tm_blo, fb, kb * BK, rb);
+          }
           ++kg;
         }
       }
@@ -794,8 +856,9 @@ __global__ void __launch_bounds__(PQ_THREADS, 1)
             for (int q = 0; q < BK / 16; ++q) {
               const uint64_t a_hi = smem_desc(sa + 32u * q);
               const uint64_t a_lo = smem_desc(sa + A_TILE + 32u * q);
-              const uint64_t b_hi = smem_desc(sa + 2 * A_TILE + 32u * q);
-              const uint64_t b_lo = smem_desc(sa + 2 * A_TILE + PQ_BTILE + 32u * q);
+              const uint32_t sb = sa + 2 * A_TILE;
+              const uint64_t b_hi = bmn ? smem_desc_mn(sb + 1024u * q) : smem_desc(sb + 32u * q);
+              const uint64_t b_lo = bmn ? smem_desc_mn(sb + PQ_BTILE + 1024u * q) : smem_desc(sb + PQ_BTILE + 32u * q);
               umma_f16<true>(d, a_hi, b_hi, idesc, (kb != j * PQ_KC || q != 0) ? 1u : 0u);
               umma_f16<true>(d, a_hi, b_lo, idesc, 1u);
               umma_f16<true>(d, a_lo, b_hi, idesc, 1u);
@@ -913,12 +976,27 @@ bool make_map(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t box
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// MN-major B over a row-major array: dims (32 columns of a strip, K rows,
+// strips[, slabs]), so that one box {32, 32, strips} is the stage's strips of
+// 32 columns x 32 K rows, one after the other (64B swizzle in each).
+bool make_map_mn(CUtensorMap* m, void* base, int64_t npad, int64_t ld, uint32_t strips, int count, int fp16) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[4] = {32, (cuuint64_t)npad, (cuuint64_t)(npad / 32), (cuuint64_t)(count > 0 ? count : 1)};
+  cuuint64_t strides[3] = {(cuuint64_t)ld * 2, 64, (cuuint64_t)npad * (cuuint64_t)ld * 2};
+  cuuint32_t box[4] = {32, (cuuint32_t)BK, strips, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, count > 0 ? 4 : 3,
+             base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 bool tc_uses_pair(int64_t npad, int count) { return count == 0 && npad >= kPairMinN; }
 
 bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, int64_t npad, int64_t ld,
-                  int count, int fp16, int pair_mode, int group, int precise) {
+                  int count, int fp16, int pair_mode, int group, int precise, int b_mn) {
   if (npad % BN != 0 || ld < npad || (ld * 2) % 16 != 0 || group < 1) return false;
   m->fp16 = fp16;
   m->precise = precise && count == 0;
@@ -927,8 +1005,13 @@ bool tc_make_maps(TcMaps* m, void* a_hi, void* a_lo, void* bt_hi, void* bt_lo, i
   m->pair = count == 0 && (m->precise || (pair_mode < 0 ? tc_uses_pair(npad, count) : pair_mode > 0));
   m->group = group;
   const uint32_t brows = m->precise ? PQ_BROWS : m->pair ? BN / 2 : BN;
-  return make_map(&m->a_hi, a_hi, npad, ld, BM, count, fp16) && make_map(&m->a_lo, a_lo, npad, ld, BM, count, fp16) &&
-         make_map(&m->b_hi, bt_hi, npad, ld, brows, count, fp16) &&
+  m->b_mn = b_mn;
+  if (!make_map(&m->a_hi, a_hi, npad, ld, BM, count, fp16) || !make_map(&m->a_lo, a_lo, npad, ld, BM, count, fp16))
+    return false;
+  if (b_mn)
+    return make_map_mn(&m->b_hi, bt_hi, npad, ld, brows / 32, count, fp16) &&
+           make_map_mn(&m->b_lo, bt_lo, npad, ld, brows / 32, count, fp16);
+  return make_map(&m->b_hi, bt_hi, npad, ld, brows, count, fp16) &&
          make_map(&m->b_lo, bt_lo, npad, ld, brows, count, fp16);
 }
 
@@ -988,7 +1071,7 @@ cudaError_t launch_pair(const TcMaps& maps, int64_t npad, const EpiParams& P, cu
   const int pairs = work < max_pairs ? work : max_pairs;
   cfg.gridDim = dim3(2 * pairs);
   return cudaLaunchKernelEx(&cfg, k, maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n,
-                            maps.group, (const int4*)nullptr, maps.nsym, maps.sym, P);
+                            maps.group, (const int4*)nullptr, maps.nsym, maps.sym, maps.b_mn, P);
 }
 
 template <bool kF16>
@@ -1024,7 +1107,7 @@ cudaError_t launch_precise(const TcMaps& maps, int64_t npad, const EpiParams& P,
   const int pairs = tiles_m * tiles_n < max_pairs ? tiles_m * tiles_n : max_pairs;
   cfg.gridDim = dim3(2 * pairs);
   return cudaLaunchKernelEx(&cfg, k, maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n,
-                            maps.group, P);
+                            maps.group, maps.b_mn, P);
 }
 
 }  // namespace
@@ -1045,7 +1128,7 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
     const int grid = ntiles < sms ? ntiles : sms;
     auto k = maps.fp16 ? tc_split_gemm_kernel<true, true, false> : tc_split_gemm_kernel<true, false, false>;
     k<<<grid, EpiShape<true, false>::kThreads, EpiShape<true, false>::kSmem, s>>>(
-        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, 1, tiles, ntiles, (const int2*)nullptr, P);
+        maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, 0, 0, 0, 1, tiles, ntiles, (const int2*)nullptr, maps.b_mn, P);
     return cudaGetLastError();
   }
   if (maps.precise)
@@ -1056,7 +1139,7 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   auto k = maps.fp16 ? tc_split_gemm_kernel<false, true, false> : tc_split_gemm_kernel<false, false, false>;
   k<<<grid, EpiShape<false, false>::kThreads, EpiShape<false, false>::kSmem, s>>>(
       maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n, maps.group, nullptr, 0,
-      (const int2*)nullptr, P);
+      (const int2*)nullptr, maps.b_mn, P);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,9 @@ struct SlotBufs {
   size_t w, f64, a_hi, a_lo, b_hi, b_lo;
 };
 constexpr size_t NOBUF = (size_t)-1;
+// Tensor-core products read B MN-major from row-major hi/lo pairs (no
+// transposed pair is stored).
+constexpr bool kMnMajorB = true;
 
 Op mk_gemm(int a, int b) {
   Op op;
@@ -174,6 +177,9 @@ struct neumann_plan_s {
   bool sym = false;
   size_t off_sym = 0;
   int nsym = 0;
+  // tensor-core products read B MN-major from its row-major hi/lo pair, so no
+  // transposed pair is ever stored
+  bool bmn = false;
   int tune_pair = -1;                    // -1: CTA pairs from padded order 4096; 0 never; 1 always
   int tune_group = kDefaultRasterGroup;  // row tiles per raster group of a single product
   int chunk_run = 0;                     // grouped batches: matrices per pass (0: chunk)
@@ -602,14 +608,18 @@ int build(neumann_plan_s* p) {
     sc.levels();
   }
   sc.matmul();
-  if (p->sym) {  // symmetric matrices: the transposed pairs equal the row-major ones
-    for (Op& op : p->ops)
+  // Right operands come from row-major pairs: read MN-major (bmn), or, in a
+  // symmetric plan's scheme, read as their own transpose.
+  auto row_major_b = [](std::vector<Op>& ops) {
+    for (Op& op : ops)
       for (int j = 0; j < op.nout; ++j)
         if (op.out[j].reps & REP_OPB) op.out[j].reps = (op.out[j].reps & ~REP_OPB) | REP_OPA;
-  }
+  };
+  if (p->sym || p->bmn) row_major_b(p->ops);
+  if (p->bmn) row_major_b(p->mm_ops);
   memset(p->reps, 0, sizeof(p->reps));
-  note_reps(p, p->ops, p->sym);
-  note_reps(p, p->mm_ops);
+  note_reps(p, p->ops, p->sym || p->bmn);
+  note_reps(p, p->mm_ops, p->bmn);
   layout(p);
   return NEUMANN_OK;
 }
@@ -669,6 +679,7 @@ int init_plan(neumann_plan_s* p, int64_t n, int64_t k, int radix, int dtype, uin
   p->dt_io = (dtype == NEUMANN_FP32 || (p->path == PATH_TC && (flags & NEUMANN_FLAG_IO_FP32))) ? DT_F32 : DT_F64;
   if ((flags & NEUMANN_FLAG_SYMMETRIC) && (flags & NEUMANN_FLAG_PRECISE_ACC)) return NEUMANN_ENOTSUP;
   p->sym = (flags & NEUMANN_FLAG_SYMMETRIC) != 0;
+  p->bmn = p->path == PATH_TC && kMnMajorB;
   int rc = validate_and_levels(p);
   if (rc) return rc;
   if (radix == 15 || radix == 0) {
@@ -829,16 +840,17 @@ int64_t op_bytes(const neumann_plan_s* p, const Op& op) {
 // read from their row-major pairs, only the tiles on or above the diagonal).
 bool build_maps(neumann_plan_s* p, const std::vector<Op>& ops, std::vector<TcMaps>* maps, bool sym = false) {
   maps->assign(ops.size(), TcMaps());
+  const bool row_b = sym || p->bmn;  // B from its row-major pair
   for (size_t i = 0; i < ops.size(); ++i) {
     const Op& op = ops[i];
     if (op.kind != OP_GEMM) continue;
     const SlotBufs& a = p->bufs[op.a];
     const SlotBufs& b = p->bufs[op.b];
-    const size_t bhi = sym ? b.a_hi : b.b_hi, blo = sym ? b.a_lo : b.b_lo;
+    const size_t bhi = row_b ? b.a_hi : b.b_hi, blo = row_b ? b.a_lo : b.b_lo;
     if (!tc_make_maps(&(*maps)[i], p->ws + a.a_hi, p->ws + a.a_lo, p->ws + bhi, p->ws + blo, p->npad, p->npad,
                       p->grouped ? p->chunk : 0, p->dtype == NEUMANN_SPLIT_FP16,
                       sym ? 1 : (p->flags & NEUMANN_FLAG_SINGLE_CTA) ? 0 : p->tune_pair, p->tune_group,
-                      (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0))
+                      (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0, p->bmn && !sym))
       return false;
     if (sym) {
       (*maps)[i].sym = reinterpret_cast<const int2*>(p->ws + p->off_sym);
