@@ -140,6 +140,33 @@ def kernel_t15(coef: dict):
     return k
 
 
+def kernel_p5(coef: dict):
+    """Five-product approximate circuit of radix 24 or 25 (App. C, Table approx:
+    the 5-product budget; structure of Sec. 4.1 with one more product).
+
+    P_1 = B^2; basis B_1 = {I, B, P_1}; for i = 2, 3, 4, 5:
+    L_i = sum_{X in B_i} l_{i,X} X,  R_i = sum_{X in B_i} r_{i,X} X,
+    P_i = L_i R_i,  B_{i+1} = B_i + {P_i};
+    T~_m = I + g_1 B + g_2 P_1 + g_3 P_2 + g_4 P_3 + g_5 P_4 + P_5.  Five products.
+
+    `coef` holds l2..l5, r2..r5 over (I, B, P1, ..., P_{i-1}) and gamma (for
+    B, P1, P2, P3, P4), already in the algebra's number type (radix_p5.py).
+    """
+
+    def k(B, alg: Algebra):
+        P1 = alg.mul(B, B)
+        basis = [alg.one, B, P1]
+        for i in range(2, 6):
+            L = _lincomb(coef[f"l{i}"], basis)
+            R = _lincomb(coef[f"r{i}"], basis)
+            basis.append(alg.mul(L, R))
+        g = coef["gamma"]
+        _, _, P1, P2, P3, P4, P5 = basis
+        return alg.one + g[0] * B + g[1] * P1 + g[2] * P2 + g[3] * P3 + g[4] * P4 + P5
+
+    return k
+
+
 def _lincomb(cs, xs):
     acc = cs[0] * xs[0]
     for c, x in zip(cs[1:], xs[1:]):
@@ -148,4 +175,4 @@ def _lincomb(cs, xs):
 
 
 #: Products per kernel application, mu_m (Sec. 2.2 cost model).
-MU = {2: 0, 3: 1, 5: 2, 9: 3, 15: 4}
+MU = {2: 0, 3: 1, 5: 2, 9: 3, 15: 4, 24: 5, 25: 5}

@@ -1,9 +1,11 @@
-"""One-call oracle: S_k(A) (or the radix-15 framework result) in FP64 on the CPU.
+"""One-call oracle: S_k(A) (or the approximate kernels' framework result) in FP64 on the CPU.
 
 radix 1  naive (Sec. 2.1)
 radix 2  repeated squaring for k = 2^t, binary digits of k otherwise (Sec. 2.1)
 radix 3, 5, 9  exact radix-m splitting with kernels T_3, T_5, T_9 (Sec. 2.2, Thm 3.1)
 radix 15 residual framework with the approximate T~_15 (Sec. 5.3, App. B)
+radix 24, 25  residual framework with the five-product approximate kernels
+         (App. C, Table approx; circuits of radix_p5.py)
 radix 0  exact kernels over the factorisation of k into 9, 5, 3 and 2 (block
          concatenation holds for any factor order, Sec. 2.2)
 """
@@ -14,13 +16,19 @@ import numpy as np
 
 from . import circuits as C
 from . import radix15 as R15
+from . import radix_p5 as RP5
 from . import schemes as SC
 
 
 def kernels(coef15: str = "refined") -> dict:
     coef = R15.load_refined(float) if coef15 == "refined" else R15.printed(float)
     return {2: C.kernel_t2, 3: C.kernel_t3, 5: C.kernel_t5, 9: C.kernel_t9,
-            15: C.kernel_t15(coef)}
+            15: C.kernel_t15(coef),
+            24: C.kernel_p5(RP5.load_refined(24)), 25: C.kernel_p5(RP5.load_refined(25))}
+
+
+#: Radices whose kernels are approximate: they run in the residual framework (Sec. 5.3).
+APPROX = (15, 24, 25)
 
 
 def auto_levels(k: int) -> list:
@@ -47,8 +55,8 @@ def evaluate(A: np.ndarray, k: int, radix: int, coef15: str = "refined",
         S = SC.binary_pow2(A, k, alg) if k & (k - 1) == 0 else SC.binary_exact(A, k, alg)
     elif radix in (3, 5, 9):
         S = SC.radix_exact(A, SC.pure_levels(k, radix), ks, alg)
-    elif radix == 15:
-        S = SC.radix_residual(A, SC.pure_levels(k, 15), ks, alg, form)
+    elif radix in APPROX:
+        S = SC.radix_residual(A, SC.pure_levels(k, radix), ks, alg, form)
     elif radix == 0:
         S = SC.radix_exact(A, auto_levels(k), ks, alg)
     else:
@@ -58,11 +66,11 @@ def evaluate(A: np.ndarray, k: int, radix: int, coef15: str = "refined",
 
 def planted_reference(V, lam, k: int, radix: int, coef15: str = "refined", rows=None):
     """Closed form on a planted symmetric spectrum (closed_form.py): S_k for the
-    exact schemes, Y_t of Lemma 5.7 for radix 15. `rows` selects rows only."""
+    exact schemes, Y_t of Lemma 5.7 for the approximate radices. `rows` selects rows only."""
     from . import closed_form as CF
 
-    if radix == 15:
-        f = CF.radix_scalar(lam, SC.pure_levels(k, 15), kernels(coef15))
+    if radix in APPROX:
+        f = CF.radix_scalar(lam, SC.pure_levels(k, radix), kernels(coef15))
     else:
         f = CF.sk_scalar(lam, k)
     if rows is None:

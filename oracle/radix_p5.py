@@ -1,0 +1,373 @@
+"""Five-product approximate radix kernels, radix 24 and 25 (this project's circuits).
+
+Test infrastructure: only tests, the smoke check and the benchmark's CPU legs use it.
+
+App. C (Table approx) reports approximate kernels of radix 24 to 33 built from
+five products. Their kernel residuals (the prefix objective of Sec. 4.2) run
+from 7e-5 at radix 24 to 0.6 at radix 33. The paper prints only the radix-33
+polynomial, not a circuit. This module builds its own circuits.
+
+Structure. The circuit of Sec. 4.1 (eq. factors, radix15kernel), extended by
+one product:
+  P_1 = B^2;  B_1 = {I, B, P_1};
+  for i = 2..5:  L_i = sum_{X in B_i} l_{i,X} X,  R_i = sum_{X in B_i} r_{i,X} X,
+                 P_i = L_i R_i,  B_{i+1} = B_i + {P_i};
+  T~_m = I + g_1 B + g_2 P_1 + g_3 P_2 + g_4 P_3 + g_5 P_4 + P_5.
+That is 41 parameters and a polynomial of degree 32. The I and P_5 coefficients
+are fixed at 1, as in eq. radix15kernel.
+
+Search. The prefix equations are [T~_m]_j = 1 for j = 0..m-1 (the objective of
+Sec. 4.2). They are solved by damped minimum-norm Gauss-Newton:
+  x <- x - J^T (J J^T + mu I)^{-1} F(x),
+with mu adapted per step, from seeded N(0, 0.7^2) starts. That is a different
+solver from the paper's L-BFGS-B. It reaches exact-prefix solutions (sum of
+squares ~1e-30 in float64) for every m up to 25. At m = 26 it stops at 2.8e-5
+from every start tried.
+- Among the exact solutions, the circuit kept has the smallest growth: the
+  largest of |L_i(x)|, |R_i(x)|, |P_i(x)| over x in [-1, 1], which bounds the
+  size of the intermediate matrices for a spectrum inside the unit disc.
+- Its parameters, rounded to 6 decimals, are published below (STARTS). They
+  play the part App. B's printed values play for radix 15: the refined kernel
+  is the minimum-norm Gauss-Newton solution of the m prefix equations started
+  there, in float64 and then in multi-precision.
+
+Both kernels converge on the whole real interval (-1, 1): |E(x)| < |x| there,
+with E(x) = 1 - (1 - x) T~_m(x) (Sec. 5.3). Radix 15 converges only to about
+|x| = 0.972.
+
+`python -m oracle.radix_p5 --search 24` repeats the search and selection.
+`python -m oracle.radix_p5 --write` regenerates radix_p5_refined.json (it needs
+mpmath). The stored file is what the oracle loads at run time.
+"""
+
+from __future__ import annotations
+
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+
+NPROD = 5
+DEG = 2 ** NPROD  # 32
+#: (name, length): l_i, r_i over B_i = (I, B, P1, ..., P_{i-1}); gamma for (B, P1, P2, P3, P4).
+LAYOUT = (("l2", 3), ("r2", 3), ("l3", 4), ("r3", 4), ("l4", 5), ("r4", 5), ("l5", 6), ("r5", 6),
+          ("gamma", 5))
+NPARAM = sum(n for _, n in LAYOUT)  # 41
+RADICES = (24, 25)
+
+#: Search settings that produced STARTS: seed = m, N(0, 0.7^2) starts, and the
+#: start index of the kept (least-growth) exact solution among SEARCH_STARTS[m].
+SEARCH_SCALE = 0.7
+SEARCH_STARTS = {24: 150, 25: 300}
+SEARCH_PICK = {24: 87, 25: 30}
+
+#: Published circuits, 6 decimals (search output, see the module docstring).
+STARTS: dict = {
+    24: {
+        "l2": ("0.097029", "0.357385", "0.655120"),
+        "r2": ("-0.980059", "0.190439", "-1.630648"),
+        "l3": ("0.321439", "-0.444368", "1.248264", "0.978297"),
+        "r3": ("0.324679", "-0.400960", "-0.327395", "-0.899070"),
+        "l4": ("1.112881", "-0.883204", "-0.277521", "-0.795105", "-1.173397"),
+        "r4": ("0.121624", "-0.211376", "1.115383", "0.889195", "-0.642986"),
+        "l5": ("-0.308654", "0.200839", "-0.197451", "-1.878574", "-0.682236", "1.614520"),
+        "r5": ("-0.052497", "0.289638", "0.558741", "0.123691", "-0.369093", "-0.178170"),
+        "gamma": ("0.925347", "0.790947", "-0.388488", "-0.553264", "0.288945"),
+    },
+    25: {
+        "l2": ("-0.064441", "-0.538114", "-0.561827"),
+        "r2": ("0.774079", "-0.013360", "-0.743178"),
+        "l3": ("0.026325", "-0.738013", "-0.556114", "-1.118781"),
+        "r3": ("-0.464421", "-0.661819", "-0.457016", "-2.013714"),
+        "l4": ("0.496175", "-0.500205", "1.048993", "1.376437", "0.797155"),
+        "r4": ("1.195995", "1.361799", "0.087941", "0.625491", "0.986071"),
+        "l5": ("-0.668592", "0.604396", "0.237796", "-0.142351", "-1.506913", "0.319748"),
+        "r5": ("0.787637", "0.932110", "0.649669", "0.074046", "0.410067", "0.814745"),
+        "gamma": ("0.938507", "0.999565", "-1.343732", "0.221997", "1.042277"),
+    },
+}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+REFINED_PATH = os.path.join(_HERE, "radix_p5_refined.json")
+
+
+def flatten(coef: dict) -> list:
+    return [v for name, n in LAYOUT for v in coef[name]]
+
+
+def unflatten(x) -> dict:
+    out, i = {}, 0
+    for name, n in LAYOUT:
+        out[name] = list(x[i:i + n])
+        i += n
+    return out
+
+
+def start(m: int, num=float) -> dict:
+    """The published 6-decimal circuit for radix m, converted with `num`."""
+    return {k: [num(Fraction(s)) for s in v] for k, v in STARTS[m].items()}
+
+
+def load_refined(m: int, num=float) -> dict:
+    """Refined coefficients of radix m from the stored file (float or mpf via `num`)."""
+    with open(REFINED_PATH) as f:
+        data = json.load(f)
+    return {name: [num(s) for s in data[str(m)]["coefficients"][name]] for name, _ in LAYOUT}
+
+
+def refined_metadata(m: int) -> dict:
+    with open(REFINED_PATH) as f:
+        return json.load(f)[str(m)]
+
+
+# --------------------------------------------------------------------------
+# The circuit as a polynomial in z, float64 with numpy (the search)
+# --------------------------------------------------------------------------
+
+def circuit_np(x, jacobian: bool = True):
+    """Coefficients of T~(z), degrees 0..32, and d coeff / d x (NPARAM x 33)."""
+    D = DEG + 1
+    x = np.asarray(x, dtype=np.float64)
+
+    def mono(d):
+        v = np.zeros(D)
+        v[d] = 1.0
+        return v
+
+    vals = [mono(0), mono(1), mono(2)]            # I, B, P1
+    grads = [np.zeros((NPARAM, D)) for _ in range(3)]
+    off = 0
+    for _ in range(2, NPROD + 1):
+        nb = len(vals)
+        Lv = sum(x[off + j] * vals[j] for j in range(nb))
+        Rv = sum(x[off + nb + j] * vals[j] for j in range(nb))
+        if jacobian:
+            Lg = sum(x[off + j] * grads[j] for j in range(nb))
+            Rg = sum(x[off + nb + j] * grads[j] for j in range(nb))
+            for j in range(nb):
+                Lg[off + j] += vals[j]
+                Rg[off + nb + j] += vals[j]
+        off += 2 * nb
+        vals.append(np.convolve(Lv, Rv)[:D])
+        if jacobian:
+            grads.append(np.array([np.convolve(Lg[p], Rv)[:D] + np.convolve(Lv, Rg[p])[:D]
+                                   for p in range(NPARAM)]))
+    T = vals[0] + vals[-1] + sum(x[off + j] * vals[1 + j] for j in range(NPROD))
+    if not jacobian:
+        return T
+    G = grads[-1] + sum(x[off + j] * grads[1 + j] for j in range(NPROD))
+    for j in range(NPROD):
+        G[off + j] += vals[1 + j]
+    return T, G
+
+
+def gauss_newton(m: int, x0, iters: int = 300):
+    """Damped minimum-norm Gauss-Newton on [T~]_j = 1, j < m. Returns (x, sum of squares)."""
+    x = np.array(x0, dtype=np.float64)
+    mu = 1e-3
+    T, G = circuit_np(x)
+    F = T[:m] - 1.0
+    f = float(F @ F)
+    for _ in range(iters):
+        J = G[:, :m].T
+        try:
+            step = J.T @ np.linalg.solve(J @ J.T + mu * np.eye(m), F)
+        except np.linalg.LinAlgError:
+            break
+        xn = x - step
+        Tn, Gn = circuit_np(xn)
+        Fn = Tn[:m] - 1.0
+        fn = float(Fn @ Fn)
+        if fn < f:
+            x, G, F, f = xn, Gn, Fn, fn
+            mu = max(mu / 3.0, 1e-15)
+            if f < 1e-28:
+                break
+        else:
+            mu *= 4.0
+            if mu > 1e8:
+                break
+    return x, f
+
+
+def search(m: int, starts: int, seed: int | None = None, scale: float = SEARCH_SCALE):
+    """Gauss-Newton from `starts` seeded random points: [(start index, x, sum of squares)]."""
+    rng = np.random.default_rng(m if seed is None else seed)
+    out = []
+    for s in range(starts):
+        x, f = gauss_newton(m, rng.standard_normal(NPARAM) * scale)
+        out.append((s, x, f))
+    return out
+
+
+def growth(x, grid: int = 4001) -> float:
+    """max over z in [-1, 1] of |L_i(z)|, |R_i(z)|, |P_i(z)|, i = 2..5."""
+    z = np.linspace(-1.0, 1.0, grid)
+    vals = [np.ones_like(z), z, z * z]
+    off, g = 0, 0.0
+    for _ in range(2, NPROD + 1):
+        nb = len(vals)
+        L = sum(x[off + j] * vals[j] for j in range(nb))
+        R = sum(x[off + nb + j] * vals[j] for j in range(nb))
+        off += 2 * nb
+        P = L * R
+        g = max(g, float(np.abs(L).max()), float(np.abs(R).max()), float(np.abs(P).max()))
+        vals.append(P)
+    return g
+
+
+def select(m: int, starts: int | None = None, seed: int | None = None):
+    """The exact-prefix solution (sum of squares < 1e-26) of least growth: (start, x, growth)."""
+    best = None
+    for s, x, f in search(m, SEARCH_STARTS[m] if starts is None else starts, seed):
+        if f < 1e-26:
+            g = growth(x)
+            if best is None or g < best[2]:
+                best = (s, x, g)
+    return best
+
+
+def to_start_strings(x) -> dict:
+    return {name: [f"{v:.6f}" for v in vals] for name, vals in unflatten(list(x)).items()}
+
+
+# --------------------------------------------------------------------------
+# Generic-number circuit with forward derivatives (the refinement)
+# --------------------------------------------------------------------------
+
+def circuit_poly(x, zero=0.0, one=1.0, with_jacobian=False):
+    """Coefficients of T~(z) (degrees 0..32) for x in any number type, and
+    optionally d coeff / d x as NPARAM rows of DEG+1 entries."""
+    D = DEG + 1
+
+    def pmul(a, b):
+        out = [zero] * D
+        for i, ai in enumerate(a):
+            if ai == 0:
+                continue
+            for j in range(D - i):
+                if b[j] != 0:
+                    out[i + j] = out[i + j] + ai * b[j]
+        return out
+
+    def padd(a, b):
+        return [u + v for u, v in zip(a, b)]
+
+    def scale(c, a):
+        return [c * v for v in a]
+
+    def mono(d):
+        p = [zero] * D
+        p[d] = one
+        return p
+
+    def zgrad():
+        return [[zero] * D for _ in range(NPARAM)] if with_jacobian else None
+
+    vals = [mono(0), mono(1), mono(2)]
+    grads = [zgrad(), zgrad(), zgrad()]
+
+    def lin(idx, nb):
+        v = [zero] * D
+        for j in range(nb):
+            v = padd(v, scale(x[idx + j], vals[j]))
+        if not with_jacobian:
+            return v, None
+        g = []
+        for p in range(NPARAM):
+            gp = [zero] * D
+            for j in range(nb):
+                gp = padd(gp, scale(x[idx + j], grads[j][p]))
+                if p == idx + j:
+                    gp = padd(gp, vals[j])
+            g.append(gp)
+        return v, g
+
+    off = 0
+    for _ in range(2, NPROD + 1):
+        nb = len(vals)
+        Lv, Lg = lin(off, nb)
+        Rv, Rg = lin(off + nb, nb)
+        off += 2 * nb
+        vals.append(pmul(Lv, Rv))
+        grads.append([padd(pmul(Lg[p], Rv), pmul(Lv, Rg[p])) for p in range(NPARAM)]
+                     if with_jacobian else None)
+    T = padd(vals[0], vals[-1])
+    for j in range(NPROD):
+        T = padd(T, scale(x[off + j], vals[1 + j]))
+    if not with_jacobian:
+        return T
+    G = []
+    for p in range(NPARAM):
+        gp = list(grads[-1][p])
+        for j in range(NPROD):
+            gp = padd(gp, scale(x[off + j], grads[1 + j][p]))
+            if p == off + j:
+                gp = padd(gp, vals[1 + j])
+        G.append(gp)
+    return T, G
+
+
+def refine(m: int, x0=None, dps: int = 60, float_iters: int = 10, mp_iters: int = 10):
+    """Minimum-norm Gauss-Newton on the m prefix equations from the published start.
+
+    Step: x <- x - J^T (J J^T)^{-1} F(x), J = dF/dx (m x 41); float64, then mpmath.
+    Returns (x as mpf list, report dict). Needs mpmath.
+    """
+    import mpmath as mp
+
+    x = [float(v) for v in (flatten(start(m)) if x0 is None else x0)]
+    for _ in range(float_iters):
+        T, G = circuit_np(x)
+        F = T[:m] - 1.0
+        J = G[:, :m].T
+        x = list(np.array(x) - J.T @ np.linalg.solve(J @ J.T, F))
+    mp.mp.dps = dps
+    xm = [mp.mpf(v) for v in x]
+    zero, one = mp.mpf(0), mp.mpf(1)
+    for _ in range(mp_iters):
+        T, G = circuit_poly(xm, zero, one, True)
+        F = mp.matrix([T[j] - 1 for j in range(m)])
+        J = mp.matrix(m, NPARAM)
+        for j in range(m):
+            for p in range(NPARAM):
+                J[j, p] = G[p][j]
+        y = mp.lu_solve(J * J.T, F)
+        step = J.T * y
+        xm = [xm[p] - step[p] for p in range(NPARAM)]
+    T = circuit_poly(xm, zero, one)
+    err = max(abs(T[j] - 1) for j in range(m))
+    return xm, {"prefix_error": err, "spill": T[m], "top": T[DEG]}
+
+
+def _write():
+    import mpmath as mp
+
+    out = {}
+    for m in RADICES:
+        xm, rep = refine(m)
+        coef = unflatten([mp.nstr(v, 45) for v in xm])
+        out[str(m)] = {
+            "coefficients": coef,
+            "prefix_error": mp.nstr(rep["prefix_error"], 5),
+            "spill": mp.nstr(rep["spill"], 20),
+            "top": mp.nstr(rep["top"], 20),
+            "growth": round(growth([float(v) for v in xm]), 6),
+            "search": {"seed": m, "starts": SEARCH_STARTS[m], "pick": SEARCH_PICK[m], "scale": SEARCH_SCALE},
+        }
+    with open(REFINED_PATH, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+
+
+if __name__ == "__main__":
+    import sys
+
+    if "--write" in sys.argv:
+        _write()
+    elif "--search" in sys.argv:
+        m = int(sys.argv[sys.argv.index("--search") + 1])
+        s, x, g = select(m)
+        print(f"radix {m}: start {s}, growth {g:.4f}")
+        print(json.dumps(to_start_strings(x)))

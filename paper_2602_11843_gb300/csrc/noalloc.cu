@@ -10,8 +10,8 @@
 // one on first use.
 //
 // What it does: the same two steps as neumann_plan_matmul on a SPLIT_BF16
-// plan. An element-wise pass splits A (row-major) and B (transposed) into
-// hi/lo BF16 pairs, then the persistent tcgen05 kernel forms
+// plan. An element-wise pass splits A and B into row-major hi/lo BF16 pairs
+// (the kernel reads B's pair MN-major), then the persistent tcgen05 kernel forms
 // Ahi Bhi + Ahi Blo + Alo Bhi and writes C. The only difference is where the
 // hi/lo operand scratch lives: in g_noalloc_scratch below, a file-scope device
 // array that the CUDA runtime places in every device context that loads this
@@ -36,7 +36,7 @@ namespace {
 constexpr int64_t kNoAllocMaxN = 1024;
 constexpr size_t kNoAllocMatBytes = (size_t)kNoAllocMaxN * kNoAllocMaxN * 2;  // one BF16 matrix
 
-// Ahi | Alo | Bhi^T | Blo^T, each padded_n x padded_n with padded_n <= 1024.
+// Ahi | Alo | Bhi | Blo, each padded_n x padded_n with padded_n <= 1024.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[4 * kNoAllocMatBytes];
 
 constexpr int kMaxDevices = 64;
@@ -68,8 +68,8 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
   return x < y + bbytes && y < x + abytes;
 }
 
-// Element-wise split of one FP64 matrix into a hi/lo pair (row-major or transposed).
-EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char* hi, char* lo, int transposed) {
+// Element-wise split of one FP64 matrix into a row-major hi/lo pair.
+EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char* hi, char* lo) {
   EpiParams P;
   memset(&P, 0, sizeof(P));
   P.n = (int)n;
@@ -82,7 +82,7 @@ EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char
   o.in_f[0] = 1.0f;
   o.f64 = 1;
   o.nsplit = 1;
-  o.split[0] = EpiSplit{hi, lo, npad, transposed};
+  o.split[0] = EpiSplit{hi, lo, npad, 0};
   P.status = nullptr;
   P.f64_in = -1;
   return P;
@@ -111,13 +111,14 @@ extern "C" int neumann_matmul_noalloc(int64_t n, const void* A, int64_t lda, con
   char* b_lo = ws + 3 * mat;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-  EpiParams pa = split_params(n, npad, A, lda, a_hi, a_lo, 0);
+  EpiParams pa = split_params(n, npad, A, lda, a_hi, a_lo);
   if (launch_ewise(pa, s) != cudaSuccess) return NEUMANN_ECUDA;
-  EpiParams pb = split_params(n, npad, B, ldb, b_hi, b_lo, 1);
+  EpiParams pb = split_params(n, npad, B, ldb, b_hi, b_lo);
   if (launch_ewise(pb, s) != cudaSuccess) return NEUMANN_ECUDA;
 
   TcMaps maps;
-  if (!tc_make_maps(&maps, a_hi, a_lo, b_hi, b_lo, npad, npad)) return NEUMANN_ECUDA;
+  if (!tc_make_maps(&maps, a_hi, a_lo, b_hi, b_lo, npad, npad, 0, 0, -1, kDefaultRasterGroup, 0, /*b_mn=*/1))
+    return NEUMANN_ECUDA;
   EpiParams pc;
   memset(&pc, 0, sizeof(pc));
   pc.n = (int)n;
