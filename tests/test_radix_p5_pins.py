@@ -188,8 +188,10 @@ def test_table_approx_metric_and_exact_rows(golden):
 
 
 def test_counts_and_coefficient():
-    """C(m) = mu_m + 2 = 7 for both; 7 / log2 25 is below radix 15's 6 / log2 15."""
+    """C(m) = mu_m + 2 = 7 for both; mu_m = 5 meets the Sec. 2.2 bound
+    ceil(log2(m - 1)); 7 / log2 25 is below radix 15's 6 / log2 15."""
     for m in RADICES:
+        assert C.MU[m] == 5 == math.ceil(math.log2(m - 1))
         assert CT.update_cost(m) == 7
         assert CT.radix_formula(m ** 3, m) == 21
     assert CT.coefficient(25) < CT.coefficient(24) < CT.coefficient(15)
