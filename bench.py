@@ -47,6 +47,9 @@ WORKLOADS = {
     "symmetric-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
                                            symmetric=True),
     "precision-r9-fp16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_fp16", sq_k=8192),
+    # five-product kernels (radix 24, 25: 7 products per level) on the same input
+    "precision-r25-bf16-n8192-k15625": dict(cfg=3, n=8192, k=15625, radix=25, dtype="split_bf16", sq_k=16384),
+    "precision-r24-bf16-n8192-k13824": dict(cfg=3, n=8192, k=13824, radix=24, dtype="split_bf16", sq_k=16384),
     # cfg 5: n = 16384, planted spectrum U[-0.95, 0.95] + rank-32 nonsymmetric term of norm 0.01;
     # the FP64 comparison (about two minutes at this size) runs only with --fp64-large
     "large-r15-fp16-n16384-k3375": dict(cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
@@ -62,14 +65,15 @@ WORKLOADS = {
     "batched-r15-bf16-4096-k225": dict(cfg=4, count=4096, k=225, radix=15, dtype="split_bf16", batched=True),
     "batched-r9-fp32-4096-k81": dict(cfg=4, count=4096, k=81, radix=9, dtype="fp32", batched=True),
     "batched-r15-fp32-4096-k225": dict(cfg=4, count=4096, k=225, radix=15, dtype="fp32", batched=True),
+    "batched-r25-bf16-4096-k625": dict(cfg=4, count=4096, k=625, radix=25, dtype="split_bf16", batched=True),
 }
 DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 
 # DRAM bytes (read + write) per launch of the tensor-core product, the mean over
-# the 16 launches of one n = 8192 radix-15 evaluation, from one ncu capture
+# the 16 launches of one evaluation of the named workload, from one ncu capture
 # (profiles/tc_split_gemm_n8192_r15_bench.md). Valid for the kernel sources
 # whose SHA-1 prefix is recorded beside it; reported as null otherwise.
-TC_TRAFFIC = {"sha1": "8a2af775a17e", "bytes_per_launch": 4.6036e9}
+TC_TRAFFIC = {"sha1": "2b6768433643", "workload": "precision-r15-bf16-n8192-k3375", "bytes_per_launch": 3.9027e9}
 
 
 def _peaks():
@@ -195,7 +199,7 @@ def cpu_baseline(wl, A_np, budget_products=None):
     ks = EV.kernels()
     levels = SC.pure_levels(wl["k"], wl["radix"])
     count_alg = C.matrix_algebra(2)
-    (SC.radix_residual if wl["radix"] == 15 else SC.radix_exact)(np.eye(2), levels, ks, count_alg)
+    (SC.radix_residual if wl["radix"] in EV.APPROX else SC.radix_exact)(np.eye(2), levels, ks, count_alg)
     total = count_alg.products
     t0 = time.perf_counter()
     ks[wl["radix"]](A_np, alg)  # first level's kernel: mu_m products of the oracle
@@ -260,7 +264,7 @@ def run_reference(args, wl):
 
     calg = C.matrix_algebra(2)
     levels = SC.pure_levels(wl["k"], wl["radix"])
-    (SC.radix_residual if wl["radix"] == 15 else SC.radix_exact)(np.eye(2), levels, ks, calg)
+    (SC.radix_residual if wl["radix"] in EV.APPROX else SC.radix_exact)(np.eye(2), levels, ks, calg)
     per_eval = statistics.median(times) * calg.products
     value = 1.0 / per_eval
     line = {
@@ -584,8 +588,8 @@ def run_ours(args, wl):
             work = "3 x 2 x padded_n x 256^2 x (tiles on or above the diagonal) BF16 tensor flops"
         peak = peaks["bf16_tflops_sustained"]
         sha = _src_sha("kernels_tc.cu", "epilogue.cuh")
-        traffic = (TC_TRAFFIC["bytes_per_launch"] if TC_TRAFFIC["sha1"] == sha and n == 8192 and not pflags
-                   else None)
+        traffic = (TC_TRAFFIC["bytes_per_launch"]
+                   if TC_TRAFFIC["sha1"] == sha and args.workload == TC_TRAFFIC["workload"] else None)
         roof = {"bound": "tensor", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": None, "traffic": traffic,
                 "kernel": "tc_split_gemm_kernel", "peak_source": f"bf16_tflops_sustained ({peak_src})",

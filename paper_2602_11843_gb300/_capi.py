@@ -75,6 +75,7 @@ def _load():
         "neumann_plan_timing": (c_int, [P, POINTER(c_float), c_int, POINTER(c_int)]),
         "neumann_radix15_coefficients": (c_int, [c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double),
                                                  POINTER(c_double)]),
+        "neumann_radix_p5_coefficients": (c_int, [c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
         "neumann_plan_selftest_timeout": (c_int, [P, ctypes.c_uint64, c_void_p]),
         "neumann_matmul_noalloc": (c_int, [c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                            c_void_p]),
@@ -199,6 +200,13 @@ def neumann_radix15_coefficients(coef_set: int = 0):
     _check(_lib.neumann_radix15_coefficients(coef_set, c, byref(e), byref(a), byref(b)),
            "neumann_radix15_coefficients")
     return list(c), e.value, a.value, b.value
+
+
+def neumann_radix_p5_coefficients(m: int):
+    c = (c_double * 41)()
+    e, a = c_double(), c_double()
+    _check(_lib.neumann_radix_p5_coefficients(m, c, byref(e), byref(a)), "neumann_radix_p5_coefficients")
+    return list(c), e.value, a.value
 
 
 def neumann_matmul_noalloc(n: int, A: int, lda: int, B: int, ldb: int, C: int, ldc: int, stream: int = 0) -> None:

@@ -28,7 +28,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels_simt.cu", "kernels_tc.cu", "noalloc.cu"]
-CPP_SOURCES = ["plan.cpp", "radix15.cpp"]
+CPP_SOURCES = ["plan.cpp", "approx_kernels.cpp"]
 
 
 def _cmds():

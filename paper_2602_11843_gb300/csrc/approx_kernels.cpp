@@ -1,0 +1,299 @@
+// Parameters of the approximate radix kernels: radix 15 (four products) and
+// radix 24 and 25 (five products).
+//
+// Circuit (Sec. 4.1, eq. factors / radix15kernel; one more product for the
+// five-product kernels of App. C, Table approx):
+//   P1 = B^2;  B_1 = {I, B, P1};
+//   for i = 2..NPROD:  L_i, R_i = linear combinations over B_i,  P_i = L_i R_i,
+//                      B_{i+1} = B_i + {P_i};
+//   T~ = I + g_1 B + g_2 P1 + ... + g_NPROD P_{NPROD-1} + P_NPROD.
+// Parameter order: l2, r2 over (I, B, P1); l3, r3 over (I, B, P1, P2); ...;
+// then gamma for (B, P1, ..., P_{NPROD-1}). The I and last-product
+// coefficients of T~ are fixed at 1.
+//
+// Radix 15. App. B prints the 28 parameters to three decimals. Those values
+// satisfy the prefix conditions [T~15]_j = 1 (j = 0..14, Sec. 4.2) only to
+// about 3e-3, while the text states < 9e-7 for the optimised kernel; the
+// printed numbers are therefore a rounding. The refined kernel solves the 15
+// prefix equations by minimum-norm Gauss-Newton,
+//   x <- x - J^T (J J^T)^{-1} F(x),
+// started at the printed values, in double precision. It agrees with the
+// printed values to their three decimals and has spillover
+// [T~15]_15 ~ 0.1852, [T~15]_16 ~ 0.4584 (Sec. 4.2 prints 0.185 and 0.458).
+//
+// Radix 24 and 25. The paper prints no five-product circuit. These are this
+// project's own circuits, published to six decimals (kRadix24, kRadix25 below;
+// they came from a seeded search for exact-prefix solutions). The kernel used
+// is the same minimum-norm Gauss-Newton solution of the m prefix equations
+// [T~]_j = 1, j < m, started at those values. Its prefix error is at rounding
+// level; the spillover [T~]_m is about 0.3516 (radix 24) and 0.9064 (radix 25).
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace neumann {
+
+namespace {
+
+const double kPrinted15[28] = {
+    0.238, 0.241, 1.574,                  // l2
+    0.048, -0.047, 0.889,                 // r2
+    0.263, 0.919, 0.842, 0.819,           // l3
+    0.184, 0.068, 0.134, -1.405,          // r3
+    -0.005, -1.385, 0.022, 0.122, 0.275,  // l4
+    -0.701, 0.602, -0.624, -0.137, 0.328, // r4
+    0.078, 1.778, 0.664, -0.024,          // gamma
+};
+
+const double kRadix24[41] = {
+    0.097029, 0.357385, 0.655120,                                // l2
+    -0.980059, 0.190439, -1.630648,                              // r2
+    0.321439, -0.444368, 1.248264, 0.978297,                     // l3
+    0.324679, -0.400960, -0.327395, -0.899070,                   // r3
+    1.112881, -0.883204, -0.277521, -0.795105, -1.173397,        // l4
+    0.121624, -0.211376, 1.115383, 0.889195, -0.642986,          // r4
+    -0.308654, 0.200839, -0.197451, -1.878574, -0.682236, 1.614520,  // l5
+    -0.052497, 0.289638, 0.558741, 0.123691, -0.369093, -0.178170,   // r5
+    0.925347, 0.790947, -0.388488, -0.553264, 0.288945,          // gamma
+};
+
+const double kRadix25[41] = {
+    -0.064441, -0.538114, -0.561827,                             // l2
+    0.774079, -0.013360, -0.743178,                              // r2
+    0.026325, -0.738013, -0.556114, -1.118781,                   // l3
+    -0.464421, -0.661819, -0.457016, -2.013714,                  // r3
+    0.496175, -0.500205, 1.048993, 1.376437, 0.797155,           // l4
+    1.195995, 1.361799, 0.087941, 0.625491, 0.986071,            // r4
+    -0.668592, 0.604396, 0.237796, -0.142351, -1.506913, 0.319748,   // l5
+    0.787637, 0.932110, 0.649669, 0.074046, 0.410067, 0.814745,      // r5
+    0.938507, 0.999565, -1.343732, 0.221997, 1.042277,           // gamma
+};
+
+// The circuit with NPROD products as a polynomial in z, with the derivative of
+// every coefficient with respect to every parameter (forward mode).
+template <int NPROD>
+struct Circuit {
+  static constexpr int NP = [] {
+    int n = NPROD;  // gamma
+    for (int i = 2; i <= NPROD; ++i) n += 2 * (i + 1);
+    return n;
+  }();
+  static constexpr int DEG = 1 << NPROD;
+
+  struct DPoly {
+    double v[DEG + 1];
+    double d[NP][DEG + 1];
+  };
+
+  static void zero(DPoly* p) { memset(p, 0, sizeof(DPoly)); }
+
+  // out = sum_j x[idx0 + j] * basis[j], j < nb
+  static void lincomb(const double* x, int idx0, const DPoly* const* basis, int nb, DPoly* out) {
+    zero(out);
+    for (int j = 0; j < nb; ++j) {
+      const double c = x[idx0 + j];
+      const DPoly* b = basis[j];
+      for (int e = 0; e <= DEG; ++e) out->v[e] += c * b->v[e];
+      for (int p = 0; p < NP; ++p)
+        for (int e = 0; e <= DEG; ++e) out->d[p][e] += c * b->d[p][e];
+      for (int e = 0; e <= DEG; ++e) out->d[idx0 + j][e] += b->v[e];
+    }
+  }
+
+  static void mul_trunc(const double* a, const double* b, double* out) {
+    double t[DEG + 1] = {0};
+    for (int i = 0; i <= DEG; ++i) {
+      if (a[i] == 0.0) continue;
+      for (int j = 0; i + j <= DEG; ++j) t[i + j] += a[i] * b[j];
+    }
+    memcpy(out, t, sizeof(t));
+  }
+
+  static void mul(const DPoly* a, const DPoly* b, DPoly* out) {
+    mul_trunc(a->v, b->v, out->v);
+    double t1[DEG + 1], t2[DEG + 1];
+    for (int p = 0; p < NP; ++p) {
+      mul_trunc(a->d[p], b->v, t1);
+      mul_trunc(a->v, b->d[p], t2);
+      for (int e = 0; e <= DEG; ++e) out->d[p][e] = t1[e] + t2[e];
+    }
+  }
+
+  // T~(z) for parameters x. `work` holds NPROD + 6 polynomials.
+  static void eval(const double* x, DPoly* T, std::vector<DPoly>& work) {
+    work.resize(NPROD + 6);
+    DPoly* I = &work[0];
+    DPoly* Bz = &work[1];
+    DPoly* P = &work[2];  // P[0] = P1, ..., P[NPROD - 1]
+    DPoly* L = &work[NPROD + 2];
+    DPoly* R = &work[NPROD + 3];
+    DPoly* G = &work[NPROD + 4];
+    zero(I);
+    I->v[0] = 1.0;
+    zero(Bz);
+    Bz->v[1] = 1.0;
+    zero(&P[0]);
+    P[0].v[2] = 1.0;  // P1 = B^2
+    const DPoly* basis[NPROD + 2] = {I, Bz, &P[0]};
+    int off = 0;
+    for (int i = 2; i <= NPROD; ++i) {
+      const int nb = i + 1;
+      lincomb(x, off, basis, nb, L);
+      lincomb(x, off + nb, basis, nb, R);
+      off += 2 * nb;
+      mul(L, R, &P[i - 1]);
+      if (i < NPROD) basis[nb] = &P[i - 1];  // the last product closes the circuit
+    }
+    const DPoly* gb[NPROD];
+    gb[0] = Bz;
+    for (int j = 1; j < NPROD; ++j) gb[j] = &P[j - 1];
+    lincomb(x, off, gb, NPROD, G);
+    const DPoly& last = P[NPROD - 1];
+    for (int e = 0; e <= DEG; ++e) T->v[e] = G->v[e] + I->v[e] + last.v[e];
+    for (int p = 0; p < NP; ++p)
+      for (int e = 0; e <= DEG; ++e) T->d[p][e] = G->d[p][e] + last.d[p][e];
+  }
+
+  static double prefix_error(const DPoly& T, int neq) {
+    double e = 0.0;
+    for (int j = 0; j < neq; ++j) e = fmax(e, fabs(T.v[j] - 1.0));
+    return e;
+  }
+
+  // Minimum-norm Gauss-Newton on [T~]_j = 1, j < neq, from x (in place).
+  // Keeps the best iterate; returns its prefix error and [T~]_neq, [T~]_{neq+1}.
+  static double refine(double* x, int neq, double* s0, double* s1);
+};
+
+// Solve M y = f (n x n, partial pivoting). Returns false if singular.
+bool solve(double* M, double* f, int n) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(M[r * n + c]) > fabs(M[piv * n + c])) piv = r;
+    if (M[piv * n + c] == 0.0) return false;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) {
+        double t = M[c * n + j];
+        M[c * n + j] = M[piv * n + j];
+        M[piv * n + j] = t;
+      }
+      double t = f[c];
+      f[c] = f[piv];
+      f[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const double m = M[r * n + c] / M[c * n + c];
+      for (int j = c; j < n; ++j) M[r * n + j] -= m * M[c * n + j];
+      f[r] -= m * f[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = f[r];
+    for (int j = r + 1; j < n; ++j) s -= M[r * n + j] * f[j];
+    f[r] = s / M[r * n + r];
+  }
+  return true;
+}
+
+template <int NPROD>
+double Circuit<NPROD>::refine(double* x, int neq, double* s0, double* s1) {
+  std::vector<DPoly> work;
+  std::vector<DPoly> Tbuf(1);
+  DPoly& T = Tbuf[0];
+  double best = 1e300;
+  double best_x[NP];
+  memcpy(best_x, x, sizeof(best_x));
+  std::vector<double> F(neq), M((size_t)neq * neq);
+  for (int it = 0; it < 40; ++it) {
+    eval(x, &T, work);
+    const double e = prefix_error(T, neq);
+    if (e < best) {
+      best = e;
+      memcpy(best_x, x, sizeof(best_x));
+    } else if (it > 6) {
+      break;  // converged to rounding level
+    }
+    for (int j = 0; j < neq; ++j) F[j] = T.v[j] - 1.0;
+    for (int a = 0; a < neq; ++a)
+      for (int b = 0; b < neq; ++b) {
+        double s = 0.0;
+        for (int p = 0; p < NP; ++p) s += T.d[p][a] * T.d[p][b];
+        M[(size_t)a * neq + b] = s;
+      }
+    if (!solve(M.data(), F.data(), neq)) break;
+    for (int p = 0; p < NP; ++p) {
+      double s = 0.0;
+      for (int j = 0; j < neq; ++j) s += T.d[p][j] * F[j];
+      x[p] -= s;
+    }
+  }
+  memcpy(x, best_x, sizeof(best_x));
+  eval(x, &T, work);
+  if (s0) *s0 = T.v[neq];
+  if (s1) *s1 = T.v[neq + 1];
+  return prefix_error(T, neq);
+}
+
+static_assert(Circuit<4>::NP == 28 && Circuit<4>::DEG == 16, "radix-15 layout");
+static_assert(Circuit<5>::NP == kApproxP5Params && Circuit<5>::DEG == 32, "five-product layout");
+
+struct Refined {
+  double x[kApproxP5Params];
+  double err, s0, s1;
+  bool ok;
+};
+
+}  // namespace
+
+bool radix15_coefficients(int set, double coef[28], double* prefix_err, double* s15, double* s16) {
+  static Refined refined;
+  static std::once_flag once;
+  if (set == 1) {
+    double x[28], e, a, b;
+    memcpy(x, kPrinted15, sizeof(x));
+    // the printed values as they are: evaluate without refining
+    std::vector<Circuit<4>::DPoly> work, T(1);
+    Circuit<4>::eval(x, &T[0], work);
+    e = Circuit<4>::prefix_error(T[0], 15);
+    a = T[0].v[15];
+    b = T[0].v[16];
+    memcpy(coef, kPrinted15, sizeof(kPrinted15));
+    if (prefix_err) *prefix_err = e;
+    if (s15) *s15 = a;
+    if (s16) *s16 = b;
+    return true;
+  }
+  std::call_once(once, [] {
+    memcpy(refined.x, kPrinted15, sizeof(kPrinted15));
+    refined.err = Circuit<4>::refine(refined.x, 15, &refined.s0, &refined.s1);
+    refined.ok = refined.err < 1e-13;
+  });
+  memcpy(coef, refined.x, 28 * sizeof(double));
+  if (prefix_err) *prefix_err = refined.err;
+  if (s15) *s15 = refined.s0;
+  if (s16) *s16 = refined.s1;
+  return refined.ok;
+}
+
+bool radix_p5_coefficients(int m, double coef[kApproxP5Params], double* prefix_err, double* spill) {
+  if (m != 24 && m != 25) return false;
+  static Refined refined[2];
+  static std::once_flag once[2];
+  const int i = m - 24;
+  std::call_once(once[i], [i, m] {
+    memcpy(refined[i].x, i == 0 ? kRadix24 : kRadix25, sizeof(kRadix24));
+    refined[i].err = Circuit<5>::refine(refined[i].x, m, &refined[i].s0, &refined[i].s1);
+    refined[i].ok = refined[i].err < 1e-13;
+  });
+  memcpy(coef, refined[i].x, sizeof(refined[i].x));
+  if (prefix_err) *prefix_err = refined[i].err;
+  if (spill) *spill = refined[i].s0;
+  return refined[i].ok;
+}
+
+}  // namespace neumann

@@ -150,8 +150,11 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
 // sets NEUMANN_STATUS_TIMEOUT in *status when the limit passes.
 cudaError_t launch_wait_probe(unsigned* status, uint64_t limit_ns, cudaStream_t s);
 
-// ---- radix-15 coefficients (radix15.cpp) ----
-// set 0: refined, 1: printed. Returns false if the refinement did not converge.
+// ---- approximate kernel coefficients (approx_kernels.cpp) ----
+// Radix 15: set 0 refined, 1 printed. Returns false if the refinement did not converge.
 bool radix15_coefficients(int set, double coef[28], double* prefix_err, double* s15, double* s16);
+// Radix 24 or 25 (five products): l2, r2, l3, r3, l4, r4, l5, r5, gamma.
+constexpr int kApproxP5Params = 41;
+bool radix_p5_coefficients(int m, double coef[kApproxP5Params], double* prefix_err, double* spill);
 
 }  // namespace neumann

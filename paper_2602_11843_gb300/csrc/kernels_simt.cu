@@ -8,6 +8,7 @@
 // epilogue rewrites the padding with zeros, so the main loop has no bounds
 // checks.
 #include <mutex>
+#include <type_traits>
 
 #include "epilogue.cuh"
 
@@ -238,6 +239,194 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
   epi_flag(P, bad);
 }
 
+// Element-wise pass, vector form. A persistent grid walks the 32 x 32 tiles;
+// in a tile each of the 256 threads takes a run of 4 consecutive columns of
+// one row, and every step a thread loads the runs of two tiles before it forms
+// and stores either, so its loads stay in flight together. NI (the op's input
+// count) and kIn64 (some input is FP64) are compile-time, so a thread holds
+// only the inputs it reads. The arithmetic is epi_row's with a zero
+// accumulator: FP32 terms summed in FP32, then FP64 inputs added by FMA.
+// For ops whose inputs are 16-byte aligned with a row stride that is a
+// multiple of 16 bytes (workspace buffers always are) and that store no
+// transposed split.
+template <int NI, bool kIn64>
+using EwIn = typename std::conditional<kIn64, double, float>::type[NI][4];
+
+template <int NI, bool kIn64>
+__device__ __forceinline__ void ew_load(const EpiParams& P, const EpiCtx& x, int r, int c0, EwIn<NI, kIn64>& in) {
+  if (r >= x.n || c0 + 4 > x.n) return;  // padding and ragged runs: ew_emit's own paths
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const EpiIn& e = P.in[i];
+    const int64_t off = x.off + (int64_t)r * e.ld + c0;
+    if (kIn64 && e.dt == DT_F64) {
+      double t[4];
+      ld_vec<4>(reinterpret_cast<const double*>(e.p) + off, t);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) in[i][w] = t[w];
+    } else {
+      float t[4];
+      ld_vec<4>(reinterpret_cast<const float*>(e.p) + off, t);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) in[i][w] = t[w];
+    }
+  }
+}
+
+template <int NI, bool kIn64, bool kF16>
+__device__ __forceinline__ bool ew_emit(const EpiParams& P, const EpiCtx& x, int r, int c0,
+                                        const EwIn<NI, kIn64>& in) {
+  constexpr int W = 4;
+  if (r >= x.n) {
+    epi_row_zero<W, kF16>(P, x, r, c0);
+    return false;
+  }
+  if (c0 + W > x.n) {
+    bool bad = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) bad |= epi_element<float, kF16>(P, x, r, c0 + w, 0.f);
+    return bad;
+  }
+  bool bad = false;
+#pragma unroll 1
+  for (int j = 0; j < P.nout; ++j) {
+    const EpiOut& o = P.out[j];
+    if (o.f64) {
+      // FP64 runs at 1/64 of the FP32 rate: an output that is one FP64 input
+      // with coefficient 1 (plus the identity) is formed without FP64
+      // arithmetic off the diagonal, where fma(1, x, 0) is x itself.
+      int copy = -1, nterms = 0;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        if (kIn64 && P.in[i].dt == DT_F64 ? o.in_d[i] != 0.0 : o.in_f[i] != 0.f) {
+          ++nterms;
+          if (kIn64 && P.in[i].dt == DT_F64 && o.in_d[i] == 1.0) copy = i;
+        }
+      }
+      double v[W];
+      if (kIn64 && nterms == 1 && copy >= 0) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+          if (i == copy)
+#pragma unroll
+            for (int w = 0; w < W; ++w) v[w] = (double)in[i][w];
+        if (o.id_d != 0.0 && r >= c0 && r < c0 + W) {  // the one run that holds the diagonal element
+#pragma unroll
+          for (int w = 0; w < W; ++w)
+            if (r == c0 + w) v[w] += o.id_d;
+        }
+      } else {
+        float vf[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) vf[w] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+          if (o.in_f[i] != 0.f && (!kIn64 || P.in[i].dt != DT_F64))
+#pragma unroll
+            for (int w = 0; w < W; ++w) vf[w] = fmaf(o.in_f[i], (float)in[i][w], vf[w]);
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = (double)vf[w] + (r == c0 + w ? o.id_d : 0.0);
+        if (kIn64) {
+#pragma unroll
+          for (int i = 0; i < NI; ++i)
+            if (o.in_d[i] != 0.0 && P.in[i].dt == DT_F64)
+#pragma unroll
+              for (int w = 0; w < W; ++w) v[w] = fma(o.in_d[i], (double)in[i][w], v[w]);
+        }
+      }
+      // finite: exponent field not all ones (integer test, no FP64 instruction)
+#pragma unroll
+      for (int w = 0; w < W; ++w) bad |= (__double2hiint(v[w]) & 0x7ff00000) == 0x7ff00000;
+      bad |= fp16_overflow<W, double, kF16>(o, v);
+      st_row<W, double, kF16>(o, x, r, c0, v);
+    } else {
+      float v[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[w] = r == c0 + w ? o.id_f : 0.f;
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+        if (o.in_f[i] != 0.f)
+#pragma unroll
+          for (int w = 0; w < W; ++w) v[w] = fmaf(o.in_f[i], (float)in[i][w], v[w]);
+#pragma unroll
+      for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
+      bad |= fp16_overflow<W, float, kF16>(o, v);
+      st_row<W, float, kF16>(o, x, r, c0, v);
+    }
+  }
+  return bad;
+}
+
+// Tile t: the grouped table's entry, or row-major over tpr tiles per row.
+__device__ __forceinline__ void ew_tile(const int4* tiles, int tpr, int t, int* mat, int* tr, int* tc) {
+  if (tiles) {
+    const int4 e = tiles[t];
+    *mat = e.x;
+    *tr = e.y;
+    *tc = e.z;
+  } else {
+    *mat = 0;
+    *tr = t / tpr;
+    *tc = t - *tr * tpr;
+  }
+}
+
+// Two tiles' inputs per thread: three CTAs per SM fit for up to two inputs,
+// two CTAs (128 registers) for three or four.
+template <int NI, bool kIn64, bool kF16>
+__global__ void __launch_bounds__(256, NI <= 2 ? 3 : 2) ewise_vec_kernel(const int4* __restrict__ tiles, int ntiles, int tpr,
+                                                            const __grid_constant__ EpiParams P) {
+  const int dr = (int)(threadIdx.x >> 3), dc = 4 * (int)(threadIdx.x & 7);
+  bool bad = false;
+  for (int t = blockIdx.x; t < ntiles; t += 2 * gridDim.x) {
+    const int u = t + gridDim.x;
+    const bool two = u < ntiles;
+    int ma, ra, ca, mb = 0, rb = 0, cb = 0;
+    ew_tile(tiles, tpr, t, &ma, &ra, &ca);
+    if (two) ew_tile(tiles, tpr, u, &mb, &rb, &cb);
+    const EpiCtx xa = epi_ctx(P, ma);
+    const EpiCtx xb = epi_ctx(P, mb);
+    EwIn<NI, kIn64> a, b;
+    ew_load<NI, kIn64>(P, xa, ra * 32 + dr, ca * 32 + dc, a);
+    if (two) ew_load<NI, kIn64>(P, xb, rb * 32 + dr, cb * 32 + dc, b);
+    bad |= ew_emit<NI, kIn64, kF16>(P, xa, ra * 32 + dr, ca * 32 + dc, a);
+    if (two) bad |= ew_emit<NI, kIn64, kF16>(P, xb, rb * 32 + dr, cb * 32 + dc, b);
+  }
+  epi_flag(P, bad);
+}
+
+int sm_count() {
+  static int n = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+      n = 0;
+    cudaGetLastError();
+  });
+  return n > 0 ? n : 152;
+}
+
+template <int NI, bool kIn64>
+void launch_ewise_vec(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles, int tpr) {
+  const int want = (ntiles + 1) / 2;  // two tiles per CTA and step
+  const int cap = (NI <= 2 ? 3 : 2) * sm_count();
+  const int grid = want < cap ? want : cap;
+  if (P.fp16)
+    ewise_vec_kernel<NI, kIn64, true><<<grid, 256, 0, s>>>(tiles, ntiles, tpr, P);
+  else
+    ewise_vec_kernel<NI, kIn64, false><<<grid, 256, 0, s>>>(tiles, ntiles, tpr, P);
+}
+
+template <int NI>
+void launch_ewise_vec(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles, int tpr, bool in64) {
+  if (in64)
+    launch_ewise_vec<NI, true>(P, s, tiles, ntiles, tpr);
+  else
+    launch_ewise_vec<NI, false>(P, s, tiles, ntiles, tpr);
+}
+
 template <typename T>
 cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const int4* tiles, int ntiles,
                         const EpiParams& P, cudaStream_t s, bool sym) {
@@ -286,10 +475,33 @@ cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles, 
     if (P.npad <= 0 || P.npad % 32 != 0) return P.npad <= 0 ? cudaSuccess : cudaErrorInvalidValue;
     grid = dim3((unsigned)(P.npad / 32), (unsigned)(P.npad / 32));
   }
-  if (P.fp16)
+  // the vector form: inputs in the workspace, or a caller's single matrix whose
+  // base and row stride are multiples of 16 bytes; no transposed split
+  bool vec = true;
+  for (int i = 0; i < P.nin; ++i) {
+    const EpiIn& in = P.in[i];
+    const size_t es = in.dt == DT_F64 ? 8 : 4;
+    const bool aligned = ((uintptr_t)in.p % 16 == 0) && ((size_t)in.ld * es) % 16 == 0;
+    vec &= in.mode == EPI_WS || (in.mode == EPI_PTR && !tiles && aligned);
+  }
+  for (int j = 0; j < P.nout; ++j)
+    for (int k = 0; k < P.out[j].nsplit; ++k) vec &= !P.out[j].split[k].transposed;
+  bool in64 = false;
+  for (int i = 0; i < P.nin; ++i) in64 |= P.in[i].dt == DT_F64;
+  if (vec && P.nin >= 1) {
+    const int tpr = tiles ? 0 : (int)(P.npad / 32);
+    const int nt = tiles ? ntiles : tpr * tpr;
+    switch (P.nin) {
+      case 1: launch_ewise_vec<1>(P, s, tiles, nt, tpr, in64); break;
+      case 2: launch_ewise_vec<2>(P, s, tiles, nt, tpr, in64); break;
+      case 3: launch_ewise_vec<3>(P, s, tiles, nt, tpr, in64); break;
+      default: launch_ewise_vec<4>(P, s, tiles, nt, tpr, in64); break;
+    }
+  } else if (P.fp16) {
     ewise_kernel<true><<<grid, dim3(32, 8), 0, s>>>(tiles, P);
-  else
+  } else {
     ewise_kernel<false><<<grid, dim3(32, 8), 0, s>>>(tiles, P);
+  }
   return cudaGetLastError();
 }
 

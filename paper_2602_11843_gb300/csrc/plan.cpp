@@ -36,7 +36,11 @@ constexpr uint32_t REP_ALL = REP_W | REP_F64 | REP_OPA | REP_OPB;
 
 // Workspace matrices ("slots"). R and Y ping-pong: a product that reads one
 // of them as an operand writes the other.
-enum : int { SL_R0, SL_R1, SL_Y0, SL_Y1, SL_LF0, SL_LF1, SL_RF0, SL_RF1, SL_P1, SL_P2, SL_C, SL_G, SL_A0, SL_N };
+// SL_P3, SL_Q5L, SL_Q5R: the five-product kernels' third product and partial fifth factors.
+enum : int {
+  SL_R0, SL_R1, SL_Y0, SL_Y1, SL_LF0, SL_LF1, SL_RF0, SL_RF1, SL_P1, SL_P2, SL_C, SL_G, SL_A0,
+  SL_P3, SL_Q5L, SL_Q5R, SL_N
+};
 constexpr int SL_NONE = -1, SL_USER_A = -2, SL_USER_B = -3, SL_USER_S = -4;
 
 struct InRef {
@@ -112,6 +116,8 @@ int mu_of(int m) {
     case 5: return 2;
     case 9: return 3;
     case 15: return 4;
+    case 24:
+    case 25: return 5;
   }
   return -1;
 }
@@ -145,6 +151,7 @@ struct neumann_plan_s {
   std::vector<TcMaps> maps, mm_maps;
   bool maps_ready = false;
   double c15[28];
+  double cp5[kApproxP5Params];  // radix 24 / 25 circuit
   cudaStream_t last_stream = nullptr;
   std::vector<cudaEvent_t> events;
   // neumann_eval_host: two sets of device staging buffers, an input and an
@@ -340,6 +347,82 @@ struct Sched {
       add_in(op4, SL_C, REP_W);
       tail(op4, 1.0, {1.0});
       ops().push_back(op4);
+    } else if (m == 24 || m == 25) {  // five-product circuit (App. C, Table approx; Sec. 4.1 structure)
+      const double* x = p->cp5;
+      const double *l2 = x, *r2 = x + 3, *l3 = x + 6, *r3 = x + 10, *l4 = x + 14, *r4 = x + 19;
+      const double *l5 = x + 24, *r5 = x + 30, *g = x + 36;
+      // P1 = B B; L2, R2 over (I, B, P1)
+      Op op1 = mk_gemm(R, R);
+      add_in(op1, R, REP_W);
+      add_out(op1, SL_P1, REP_W, 1.0, 0.0);
+      add_out(op1, SL_LF0, REP_OPA, l2[2], l2[0]).in[0] = l2[1];
+      add_out(op1, SL_RF0, REP_OPB, r2[2], r2[0]).in[0] = r2[1];
+      ops().push_back(op1);
+      // P2 = L2 R2; L3, R3 over (I, B, P1, P2); C = g1 B + g2 P1 + g3 P2
+      Op op2 = mk_gemm(SL_LF0, SL_RF0);
+      add_in(op2, R, REP_W);
+      add_in(op2, SL_P1, REP_W);
+      add_out(op2, SL_P2, REP_W, 1.0, 0.0);
+      {
+        OutSpec& L = add_out(op2, SL_LF1, REP_OPA, l3[3], l3[0]);
+        L.in[0] = l3[1];
+        L.in[1] = l3[2];
+        OutSpec& Rr = add_out(op2, SL_RF1, REP_OPB, r3[3], r3[0]);
+        Rr.in[0] = r3[1];
+        Rr.in[1] = r3[2];
+        OutSpec& C = add_out(op2, SL_C, REP_W, g[2], 0.0);
+        C.in[0] = g[0];
+        C.in[1] = g[1];
+      }
+      ops().push_back(op2);
+      // P3 = L3 R3; L4, R4 over (I, B, P1, P2, P3); C += g4 P3; P3 kept for the fifth factors
+      Op op3 = mk_gemm(SL_LF1, SL_RF1);
+      add_in(op3, R, REP_W);
+      add_in(op3, SL_P1, REP_W);
+      add_in(op3, SL_P2, REP_W);
+      add_in(op3, SL_C, REP_W);
+      {
+        OutSpec& L = add_out(op3, SL_LF0, REP_OPA, l4[4], l4[0]);
+        L.in[0] = l4[1];
+        L.in[1] = l4[2];
+        L.in[2] = l4[3];
+        OutSpec& Rr = add_out(op3, SL_RF0, REP_OPB, r4[4], r4[0]);
+        Rr.in[0] = r4[1];
+        Rr.in[1] = r4[2];
+        Rr.in[2] = r4[3];
+        add_out(op3, SL_C, REP_W, g[3], 0.0).in[3] = 1.0;
+        add_out(op3, SL_P3, REP_W, 1.0, 0.0);
+      }
+      ops().push_back(op3);
+      // element-wise: the parts of L5, R5 over (I, B, P1, P2, P3)
+      Op ew = mk_ewise();
+      add_in(ew, R, REP_W);
+      add_in(ew, SL_P1, REP_W);
+      add_in(ew, SL_P2, REP_W);
+      add_in(ew, SL_P3, REP_W);
+      {
+        OutSpec& L = add_out(ew, SL_Q5L, REP_W, 0.0, l5[0]);
+        OutSpec& Rr = add_out(ew, SL_Q5R, REP_W, 0.0, r5[0]);
+        for (int j = 0; j < 4; ++j) {
+          L.in[j] = l5[1 + j];
+          Rr.in[j] = r5[1 + j];
+        }
+      }
+      ops().push_back(ew);
+      // P4 = L4 R4; L5 = Q5L + l5_P4 P4, R5 = Q5R + r5_P4 P4; C += g5 P4
+      Op op4 = mk_gemm(SL_LF0, SL_RF0);
+      add_in(op4, SL_Q5L, REP_W);
+      add_in(op4, SL_Q5R, REP_W);
+      add_in(op4, SL_C, REP_W);
+      add_out(op4, SL_LF1, REP_OPA, l5[5], 0.0).in[0] = 1.0;
+      add_out(op4, SL_RF1, REP_OPB, r5[5], 0.0).in[1] = 1.0;
+      add_out(op4, SL_C, REP_W, g[4], 0.0).in[2] = 1.0;
+      ops().push_back(op4);
+      // P5 = L5 R5; G = C + P5 (T~ = I + G)
+      Op op5 = mk_gemm(SL_LF1, SL_RF1);
+      add_in(op5, SL_C, REP_W);
+      tail(op5, 1.0, {1.0});
+      ops().push_back(op5);
     }
   }
 
@@ -644,6 +727,8 @@ int validate_and_levels(neumann_plan_s* p) {
     case 5:
     case 9:
     case 15:
+    case 24:
+    case 25:
       if (!pure_power(k, p->radix, &p->levels)) return NEUMANN_EINVAL;
       break;
     case 0: {
@@ -686,6 +771,10 @@ int init_plan(neumann_plan_s* p, int64_t n, int64_t k, int radix, int dtype, uin
     double e, s15, s16;
     if (!radix15_coefficients((flags & NEUMANN_FLAG_PRINTED_COEFFS) ? 1 : 0, p->c15, &e, &s15, &s16))
       return NEUMANN_ENOTSUP;
+  }
+  if (radix == 24 || radix == 25) {
+    double e, sp;
+    if (!radix_p5_coefficients(radix, p->cp5, &e, &sp)) return NEUMANN_ENOTSUP;
   }
   return build(p);
 }
@@ -1637,6 +1726,15 @@ int neumann_radix15_coefficients(int set, double* coef28, double* prefix_error, 
   if (prefix_error) *prefix_error = e;
   if (spill15) *spill15 = a;
   if (spill16) *spill16 = b;
+  return ok ? NEUMANN_OK : NEUMANN_ENOTSUP;
+}
+
+int neumann_radix_p5_coefficients(int m, double* coef41, double* prefix_error, double* spill) {
+  if ((m != 24 && m != 25) || !coef41) return NEUMANN_EINVAL;
+  double e = 0, a = 0;
+  const bool ok = radix_p5_coefficients(m, coef41, &e, &a);
+  if (prefix_error) *prefix_error = e;
+  if (spill) *spill = a;
   return ok ? NEUMANN_OK : NEUMANN_ENOTSUP;
 }
 

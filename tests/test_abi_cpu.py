@@ -13,7 +13,8 @@ nm = pytest.importorskip("paper_2602_11843_gb300", reason="library not built")
 from paper_2602_11843_gb300 import _capi as C  # noqa: E402
 
 from oracle import counts as CT  # noqa: E402
-from oracle import radix15 as R15  # noqa: E402
+from oracle import radix15 as R15
+from oracle import radix_p5 as RP5  # noqa: E402
 
 
 def test_exports_every_declared_symbol():
@@ -30,6 +31,7 @@ def test_exports_every_declared_symbol():
 @pytest.mark.parametrize("n,k,radix,dtype,flags", [
     (0, 81, 9, C.FP64, 0), (10, 0, 9, C.FP64, 0), (10, 80, 9, C.FP64, 0), (10, 100, 15, C.FP64, 0),
     (10, 12, 2, C.FP64, 0), (10, 7 * 9, 0, C.FP64, 0), (10, 81, 7, C.FP64, 0), (10, 81, 9, 9, 0),
+    (10, 625, 24, C.FP64, 0), (10, 576, 25, C.FP64, 0), (10, 576, 23, C.FP64, 0),
 ])
 def test_invalid_arguments(n, k, radix, dtype, flags):
     with pytest.raises(C.NeumannError) as e:
@@ -58,7 +60,8 @@ def _info(n, k, radix, dtype=C.FP64, flags=0):
 
 
 @pytest.mark.parametrize("k,radix", [(81, 9), (729, 9), (6561, 9), (225, 15), (3375, 15), (125, 5), (625, 5),
-                                     (27, 3), (128, 2), (1024, 2), (4096, 2)])
+                                     (27, 3), (128, 2), (1024, 2), (4096, 2), (24, 24), (576, 24),
+                                     (13824, 24), (625, 25), (15625, 25)])
 def test_product_counts_match_paper(k, radix):
     """products_formula = the paper's count (Table tab:results, Sec. 2.2 cost model,
     Sec. 6 binary); products_executed = formula - 2 (no product with S_1 = I, no unused power)."""
@@ -108,6 +111,21 @@ def test_library_radix15_coefficients_match_oracle():
     pcoef, perr, _, _ = C.neumann_radix15_coefficients(1)
     assert pcoef == R15.flatten(R15.printed(float))
     assert 2e-3 < perr < 4e-3
+
+
+@pytest.mark.parametrize("m", RP5.RADICES)
+def test_library_radix_p5_coefficients_match_oracle(m):
+    """The library refines the published six-decimal circuit in double precision;
+    the oracle refines it in multi-precision. Same start, same solution."""
+    coef, err, spill = C.neumann_radix_p5_coefficients(m)
+    ref = RP5.flatten(RP5.load_refined(m))
+    assert max(abs(a - b) for a, b in zip(coef, ref)) < 1e-12
+    assert err < 1e-13
+    assert abs(spill - float(RP5.refined_metadata(m)["spill"])) < 1e-12
+    for bad in (15, 23, 26):
+        with pytest.raises(C.NeumannError) as e:
+            C.neumann_radix_p5_coefficients(bad)
+        assert e.value.code == C.EINVAL
 
 
 def test_batched_plan_and_empty_batch():
