@@ -719,7 +719,7 @@ __device__ __forceinline__ void st8_split_diag(const EpiSplit& sp, const EpiCtx&
 
 template <bool kF16, int RB, int NF, bool kD>
 __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                               int lane, int sym) {
+                                               int lane, int sym, bool edge) {
   static_assert(RB % 8 == 0 && 32 % RB == 0, "row batch");
   const int fi = P.f64_in;  // the FP64 input, or -1
   const int nf = P.nf32;    // FP32 inputs (<= NF)
@@ -748,6 +748,12 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
     for (int h = 0; h < RB; h += 8) {
       const int r0 = rbase + g0 + h;
       const bool diag = (unsigned)(c - r0) < 8u;  // this lane's column holds the diagonal in these rows
+      // boundary chunk (edge, warp-uniform): bit w set where (r0 + w, c) lies in the n x n block
+      unsigned live = 0xffu;
+      if (edge) {
+        const int nr = x.n - r0;
+        live = c >= x.n || nr <= 0 ? 0u : nr >= 8 ? 0xffu : (1u << nr) - 1u;
+      }
       float a8[8];
 #pragma unroll
       for (int w = 0; w < 8; ++w) a8[w] = stg[(g0 + h + w) * 33 + lane];
@@ -781,6 +787,11 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
 #pragma unroll
             for (int w = 0; w < 8; ++w) v[w] = fma(o.in_d[fi], din[h + w], v[w]);
           }
+          if (edge) {  // padding holds zeros
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+              if (!((live >> w) & 1u)) v[w] = 0.0;
+          }
 #pragma unroll
           for (int w = 0; w < 8; ++w) vf[w] = (float)v[w];
           if (sym == 2) {
@@ -789,14 +800,27 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
             for (int d = 0; d < o.ndst; ++d) {
               const EpiDst& ds = o.dst[d];
               int64_t ld;
+              const unsigned keep = (edge && ds.mode != EPI_WS) ? live : 0xffu;  // caller's matrix: n x n only
               if (ds.dt == DT_F64) {
                 double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
+                if (keep == 0xffu) {
 #pragma unroll
-                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = v[w];
+                  for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = v[w];
+                } else {
+#pragma unroll
+                  for (int w = 0; w < 8; ++w)
+                    if ((keep >> w) & 1u) q[(int64_t)w * ld] = v[w];
+                }
               } else {
                 float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+                if (keep == 0xffu) {
 #pragma unroll
-                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+                  for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+                } else {
+#pragma unroll
+                  for (int w = 0; w < 8; ++w)
+                    if ((keep >> w) & 1u) q[(int64_t)w * ld] = vf[w];
+                }
               }
             }
             if (sym == 1) st8_mirror_dst(o, x, r0, c, vf, v);
@@ -821,20 +845,38 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
 #pragma unroll
             for (int w = 0; w < 8; ++w) vf[w] = fmaf(o.in_f[fi], (float)din[h + w], vf[w]);
           }
+          if (edge) {  // padding holds zeros
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+              if (!((live >> w) & 1u)) vf[w] = 0.f;
+          }
           if (sym == 2) {
             st8_dst_diag(o, x, r0, c, vf, nullptr);
           } else {
             for (int d = 0; d < o.ndst; ++d) {
               const EpiDst& ds = o.dst[d];
               int64_t ld;
+              const unsigned keep = (edge && ds.mode != EPI_WS) ? live : 0xffu;  // caller's matrix: n x n only
               if (ds.dt == DT_F64) {
                 double* q = dst_base<double>(ds, x, &ld) + (int64_t)r0 * ld + c;
+                if (keep == 0xffu) {
 #pragma unroll
-                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = (double)vf[w];
+                  for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = (double)vf[w];
+                } else {
+#pragma unroll
+                  for (int w = 0; w < 8; ++w)
+                    if ((keep >> w) & 1u) q[(int64_t)w * ld] = (double)vf[w];
+                }
               } else {
                 float* q = dst_base<float>(ds, x, &ld) + (int64_t)r0 * ld + c;
+                if (keep == 0xffu) {
 #pragma unroll
-                for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+                  for (int w = 0; w < 8; ++w) q[(int64_t)w * ld] = vf[w];
+                } else {
+#pragma unroll
+                  for (int w = 0; w < 8; ++w)
+                    if ((keep >> w) & 1u) q[(int64_t)w * ld] = vf[w];
+                }
               }
             }
             if (sym == 1) st8_mirror_dst(o, x, r0, c, vf, nullptr);
@@ -864,10 +906,10 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
 
 template <bool kF16>
 __device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                               int lane, int sym = 0) {
-  if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane, sym);
-  if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane, sym);
-  return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane, sym);
+                                               int lane, int sym, bool edge) {
+  if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane, sym, edge);
+  if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane, sym, edge);
+  return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane, sym, edge);
 }
 
 // Boundary chunks (padding, ragged edges, grouped row limits) and ops with
@@ -917,8 +959,11 @@ __device__ __noinline__ bool epi_chunk_diag(const EpiParams& P, EpiCtx x, int rb
 template <bool kF16>
 __device__ __forceinline__ bool epi_chunk(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
                                           int lane, int lim, int sym = 0) {
-  if (P.fast && c < x.n && rbase + 32 <= x.n && rbase + 32 <= lim)
-    return epi_chunk_fast<kF16>(P, x, rbase, c, stg, lane, sym);
+  if (P.fast && rbase + 32 <= lim) {
+    // boundary chunk: part of it lies outside the n x n block (warp-uniform)
+    const bool edge = !__all_sync(0xffffffffu, c < x.n && rbase + 32 <= x.n);
+    if (!edge || (sym == 0 && P.edge_ok)) return epi_chunk_fast<kF16>(P, x, rbase, c, stg, lane, sym, edge);
+  }
   if (sym == 2) return epi_chunk_diag<kF16>(P, x, rbase, c, stg, lane);
   return epi_chunk_generic<kF16>(P, x, rbase, c, stg, lane, lim, sym == 1);
 }

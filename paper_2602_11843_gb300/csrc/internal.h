@@ -90,6 +90,10 @@ struct EpiParams {
   int f64_in;
   int nf32;
   int f32_idx[kMaxIn];
+  // Every input is a workspace buffer: reads anywhere in the padded block are
+  // in bounds, so the lean path may also take boundary chunks (zeros stored
+  // outside the n x n block, the caller's matrices written inside it only).
+  int edge_ok;
 };
 
 // Split-operand tensor maps of one tensor-core product C = A B:

@@ -894,6 +894,8 @@ void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiPa
     }
   }
   P->fast = nf64 <= 1;
+  P->edge_ok = 1;
+  for (int i = 0; i < op.nin; ++i) P->edge_ok &= P->in[i].mode == EPI_WS;
 }
 
 // Algorithmic device-memory bytes of one op per matrix element: each input

@@ -4,6 +4,9 @@
   python -m paper_2602_11843_gb300.profile_case r15 N REPS      radix-15, k = 3375, split-BF16
   python -m paper_2602_11843_gb300.profile_case batched N REPS  512 matrices of order N, radix 9,
                                                                 k = 81, split-BF16, one grouped pass
+  python -m paper_2602_11843_gb300.profile_case mixed C REPS    C matrices of orders 16, 32, ..., 256
+                                                                in turn (the batched workload's mix),
+                                                                radix 9, k = 81, split-BF16
 
 Inputs are drawn on the device (no host copies): A, B ~ N(0, 1) for the
 product; for r15 and batched symmetric matrices with spectral radius about 0.45. Prints the
@@ -42,6 +45,17 @@ def main(argv):
         As = list((X + X.transpose(1, 2)) * (0.45 / (2.0 * n ** 0.5)))
         outs = [torch.empty_like(a) for a in As]
         p = nm.BatchedPlan(count, n, 81, 9, "split_bf16")
+        for _ in range(reps):
+            p(As, outs)
+    elif mode == "mixed":
+        count = n
+        orders = [16 * (1 + i % 16) for i in range(count)]
+        As = []
+        for m in orders:
+            X = torch.randn((m, m), dtype=torch.float64, device="cuda", generator=g)
+            As.append((X + X.T) * (0.45 / (2.0 * m ** 0.5)))
+        outs = [torch.empty_like(a) for a in As]
+        p = nm.BatchedPlan(count, 256, 81, 9, "split_bf16")
         for _ in range(reps):
             p(As, outs)
     else:

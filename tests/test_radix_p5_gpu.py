@@ -92,6 +92,19 @@ def test_p5_symmetric_flag(dtype, radix, n):
     assert CF.rel_fro(S, ref) < _tol(dtype, 0.9)
 
 
+@pytest.mark.parametrize("dtype", ["split_bf16", "split_fp16"])
+def test_p5_precise_and_io_fp32(dtype):
+    """NEUMANN_FLAG_PRECISE_ACC (chunked accumulation) and FLAG_IO_FP32 (float A and S)."""
+    nm = _nm()
+    pl = G.planted_symmetric(1000, 0.9, 21)
+    ref = EV.planted_reference(pl["V"], pl["lam"], 625, 25)
+    S, st, _ = _run(pl["A"], 625, 25, dtype, nm.FLAG_PRECISE_ACC)
+    assert st == 0 and CF.rel_fro(S, ref) < _tol(dtype, 0.9)
+    S, st, p = _run(pl["A"], 625, 25, dtype, nm.FLAG_IO_FP32)
+    assert p.io_dtype == torch.float32
+    assert st == 0 and CF.rel_fro(S, ref) < max(_tol(dtype, 0.9), 1e-5)
+
+
 @pytest.mark.parametrize("n,k,radix", [(1, 24, 24), (17, 25, 25), (33, 625, 25), (129, 576, 24)])
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_p5_edge_sizes(n, k, radix, dtype):
