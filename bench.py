@@ -73,7 +73,7 @@ DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 # the 16 launches of one evaluation of the named workload, from one ncu capture
 # (profiles/tc_split_gemm_n8192_r15_bench.md). Valid for the kernel sources
 # whose SHA-1 prefix is recorded beside it; reported as null otherwise.
-TC_TRAFFIC = {"sha1": "2b6768433643", "workload": "precision-r15-bf16-n8192-k3375", "bytes_per_launch": 3.9027e9}
+TC_TRAFFIC = {"sha1": "0330704bb74c", "workload": "precision-r15-bf16-n8192-k3375", "bytes_per_launch": 3.9327e9}
 
 
 def _peaks():
