@@ -142,6 +142,26 @@ def test_leading_dimensions_and_io_fp32():
     assert st == 0 and CF.rel_fro(S, ref) < 2e-4
 
 
+@pytest.mark.parametrize("dtype", ["fp64", "split_bf16", "split_fp16"])
+@pytest.mark.parametrize("n,lda,offset", [(100, 161, 0), (100, 160, 1), (101, 104, 0), (101, 101, 0)])
+def test_split_of_a_alignment(dtype, n, lda, offset):
+    """The first element-wise pass reads the caller's A as 4-wide vectors when its base
+    and row stride are multiples of 16 bytes, and element by element otherwise (odd
+    stride, base one element in). Odd n leaves a ragged run at the end of each row."""
+    nm = _nm()
+    g = G.gaussian_scaled(n, 0.5, 30 + n)
+    ref, _ = EV.evaluate(g["A"], 81, 9)
+    p = nm.Plan(n, 81, 9, dtype)
+    flat = torch.zeros(offset + n * lda + 8, dtype=torch.float64, device="cuda")
+    view = flat[offset:offset + n * lda].view(n, lda)
+    view[:, :n] = torch.tensor(g["A"], device="cuda")
+    out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    nm.neumann_eval(p.handle, view.data_ptr(), lda, out.data_ptr(), n, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    assert CF.rel_fro(out.cpu().numpy(), ref) < _tol(dtype, 0.5)
+
+
 def test_nonfinite_status_for_divergent_input():
     """Undamped Jacobi splitting has rho(A) > 1; S_k overflows and the epilogue
     reports NEUMANN_STATUS_NONFINITE instead of trapping."""
