@@ -32,40 +32,42 @@ sys.path.insert(0, ROOT)
 METRIC = "S_k(A) evals/s & % tensor peak: radix-15/9 vs squaring, split-BF16 vs FP64"
 UNIT = "S_k/s"
 
+# steps: the default number of timed steps, sized so that the timed region lasts about 2 s on
+# one GB300 (the products' power-capped regime, where the sustained peak is measured).
 WORKLOADS = {
-    "precision-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096),
-    "precision-r9-bf16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_bf16", sq_k=8192),
-    "precision-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096),
-    "precise-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
+    "precision-r15-bf16-n8192-k3375": dict(steps=64, cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096),
+    "precision-r9-bf16-n8192-k6561": dict(steps=56, cfg=3, n=8192, k=6561, radix=9, dtype="split_bf16", sq_k=8192),
+    "precision-r15-fp16-n8192-k3375": dict(steps=64, cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096),
+    "precise-r15-fp16-n8192-k3375": dict(steps=44, cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
                                          precise=True),
-    "precise-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096,
+    "precise-r15-bf16-n8192-k3375": dict(steps=44, cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096,
                                          precise=True),
     # the same symmetric input through NEUMANN_FLAG_SYMMETRIC: products compute the tiles on or
     # above the diagonal only, so the roofline counts that work, not 2 n^3
-    "symmetric-r15-bf16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096,
+    "symmetric-r15-bf16-n8192-k3375": dict(steps=108, cfg=3, n=8192, k=3375, radix=15, dtype="split_bf16", sq_k=4096,
                                            symmetric=True),
-    "symmetric-r15-fp16-n8192-k3375": dict(cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
+    "symmetric-r15-fp16-n8192-k3375": dict(steps=108, cfg=3, n=8192, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
                                            symmetric=True),
-    "precision-r9-fp16-n8192-k6561": dict(cfg=3, n=8192, k=6561, radix=9, dtype="split_fp16", sq_k=8192),
+    "precision-r9-fp16-n8192-k6561": dict(steps=56, cfg=3, n=8192, k=6561, radix=9, dtype="split_fp16", sq_k=8192),
     # five-product kernels (radix 24, 25: 7 products per level) on the same input
-    "precision-r25-bf16-n8192-k15625": dict(cfg=3, n=8192, k=15625, radix=25, dtype="split_bf16", sq_k=16384),
-    "precision-r24-bf16-n8192-k13824": dict(cfg=3, n=8192, k=13824, radix=24, dtype="split_bf16", sq_k=16384),
+    "precision-r25-bf16-n8192-k15625": dict(steps=48, cfg=3, n=8192, k=15625, radix=25, dtype="split_bf16", sq_k=16384),
+    "precision-r24-bf16-n8192-k13824": dict(steps=48, cfg=3, n=8192, k=13824, radix=24, dtype="split_bf16", sq_k=16384),
     # cfg 5: n = 16384, planted spectrum U[-0.95, 0.95] + rank-32 nonsymmetric term of norm 0.01;
     # the FP64 comparison (about two minutes at this size) runs only with --fp64-large
-    "large-r15-fp16-n16384-k3375": dict(cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
+    "large-r15-fp16-n16384-k3375": dict(steps=8, cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16", sq_k=4096,
                                         fp64=False),
-    "large-precise-r15-fp16-n16384-k3375": dict(cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16",
+    "large-precise-r15-fp16-n16384-k3375": dict(steps=6, cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16",
                                                 sq_k=4096, fp64=False, precise=True),
-    "plain-r9-fp32-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
-    "plain-r15-fp32-n4096-k225": dict(cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
-    "plain-r9-fp64-n4096-k729": dict(cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
+    "plain-r9-fp32-n4096-k729": dict(steps=50, cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
+    "plain-r15-fp32-n4096-k225": dict(steps=64, cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
+    "plain-r9-fp64-n4096-k729": dict(steps=3, cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
     # cfg 4: 4096 damped-Jacobi matrices, n uniform in {16, 32, ..., 256}; a step is one
     # grouped evaluation of the whole batch
-    "batched-r9-bf16-4096-k81": dict(cfg=4, count=4096, k=81, radix=9, dtype="split_bf16", batched=True),
-    "batched-r15-bf16-4096-k225": dict(cfg=4, count=4096, k=225, radix=15, dtype="split_bf16", batched=True),
-    "batched-r9-fp32-4096-k81": dict(cfg=4, count=4096, k=81, radix=9, dtype="fp32", batched=True),
-    "batched-r15-fp32-4096-k225": dict(cfg=4, count=4096, k=225, radix=15, dtype="fp32", batched=True),
-    "batched-r25-bf16-4096-k625": dict(cfg=4, count=4096, k=625, radix=25, dtype="split_bf16", batched=True),
+    "batched-r9-bf16-4096-k81": dict(steps=160, cfg=4, count=4096, k=81, radix=9, dtype="split_bf16", batched=True),
+    "batched-r15-bf16-4096-k225": dict(steps=130, cfg=4, count=4096, k=225, radix=15, dtype="split_bf16", batched=True),
+    "batched-r9-fp32-4096-k81": dict(steps=90, cfg=4, count=4096, k=81, radix=9, dtype="fp32", batched=True),
+    "batched-r15-fp32-4096-k225": dict(steps=64, cfg=4, count=4096, k=225, radix=15, dtype="fp32", batched=True),
+    "batched-r25-bf16-4096-k625": dict(steps=76, cfg=4, count=4096, k=625, radix=25, dtype="split_bf16", batched=True),
 }
 DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 
@@ -118,15 +120,20 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) of this GPU's clocks and throttle reasons."""
+    """nvidia-smi samples (200 ms) of this GPU's clocks and throttle reasons.
 
-    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    The sampler starts before the timed region and stops after it; summary() keeps
+    the samples whose nvidia-smi timestamp falls inside the region (from entering
+    the `with` block to leaving it)."""
+
+    FIELDS = ("timestamp,index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, uuid):
         self.uuid = uuid
         self.proc = None
+        self.t0 = self.t1 = None
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
 
     def __enter__(self):
@@ -137,9 +144,11 @@ class ClockSampler:
             time.sleep(0.3)
         except Exception:
             self.proc = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *exc):
+        self.t1 = time.time()
         if self.proc is not None:
             time.sleep(0.25)
             self.proc.terminate()
@@ -148,6 +157,15 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self):
         self.tmp.flush()
         rows = []
@@ -155,15 +173,19 @@ class ClockSampler:
             with open(self.tmp.name) as f:
                 for line in f:
                     parts = [p.strip() for p in line.split(",")]
-                    if len(parts) < 10:
+                    if len(parts) < 11:
                         continue
-                    if self.uuid and self.uuid not in parts[1]:
+                    if self.uuid and self.uuid not in parts[2]:
                         continue
                     rows.append(parts)
         finally:
             os.unlink(self.tmp.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        inside = [r for r in rows if (t := self._stamp(r[0])) is not None and self.t0 <= t <= self.t1]
+        note = None
+        if not inside:  # a region shorter than the sampling interval
+            inside, note = rows, "no sample inside the timed region: all samples of the run"
 
         def num(x):
             try:
@@ -171,11 +193,15 @@ class ClockSampler:
             except ValueError:
                 return None
 
-        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        sm = [num(r[3]) for r in inside if num(r[3]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][3]),
-                "power_w_max": max((num(r[4]) or 0.0) for r in rows), "samples": len(rows), "reasons": reasons}
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[7 + i].lower().startswith("active")})
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(inside[0][4]),
+               "power_w_max": max((num(r[5]) or 0.0) for r in inside), "samples": len(inside),
+               "region_s": round(self.t1 - self.t0, 3), "reasons": reasons}
+        if note:
+            out["note"] = note
+        return out
 
 
 def make_input(wl, seed_rep):
@@ -655,7 +681,8 @@ def run_ours(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's, a timed region of about 2 s; 10 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
@@ -665,6 +692,8 @@ def main():
     ap.add_argument("--fp64-large", action="store_true", help="run the FP64 comparison on the n = 16384 workload")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.steps is None:
+        args.steps = 10 if args.impl == "reference" else wl.get("steps", 10)
     if args.impl == "reference":
         run_reference(args, wl)
     else:
