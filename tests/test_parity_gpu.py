@@ -160,6 +160,10 @@ def test_split_of_a_alignment(dtype, n, lda, offset):
     torch.cuda.synchronize()
     assert p.status() == 0
     assert CF.rel_fro(out.cpu().numpy(), ref) < _tol(dtype, 0.5)
+    # the same arithmetic on either read path: bit-identical to a contiguous, aligned A
+    S = p(torch.tensor(g["A"], device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.equal(S, out)
 
 
 def test_nonfinite_status_for_divergent_input():
