@@ -246,11 +246,24 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
 // count) and kIn64 (some input is FP64) are compile-time, so a thread holds
 // only the inputs it reads. The arithmetic is epi_row's with a zero
 // accumulator: FP32 terms summed in FP32, then FP64 inputs added by FMA.
-// For ops whose inputs are 16-byte aligned with a row stride that is a
-// multiple of 16 bytes (workspace buffers always are) and that store no
-// transposed split.
+// For every op that stores no transposed split. Runs of the workspace are
+// always 16-byte aligned; a caller's matrix (single, or a grouped batch's
+// per-matrix table) is read as vectors where its runs are aligned.
 template <int NI, bool kIn64>
 using EwIn = typename std::conditional<kIn64, double, float>::type[NI][4];
+
+// A run of 4 elements at q: one vector load when q is 16-byte aligned (always so
+// in the workspace), else 4 element loads (a caller's matrix with an odd base or
+// row stride).
+template <typename T>
+__device__ __forceinline__ void ld_run4(const T* q, T (&t)[4]) {
+  if (((uintptr_t)q & 15u) == 0) {
+    ld_vec<4>(q, t);
+  } else {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) t[w] = q[w];
+  }
+}
 
 template <int NI, bool kIn64>
 __device__ __forceinline__ void ew_load(const EpiParams& P, const EpiCtx& x, int r, int c0, EwIn<NI, kIn64>& in) {
@@ -258,15 +271,15 @@ __device__ __forceinline__ void ew_load(const EpiParams& P, const EpiCtx& x, int
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const EpiIn& e = P.in[i];
-    const int64_t off = x.off + (int64_t)r * e.ld + c0;
+    int64_t ld;
     if (kIn64 && e.dt == DT_F64) {
       double t[4];
-      ld_vec<4>(reinterpret_cast<const double*>(e.p) + off, t);
+      ld_run4(in_base<double>(e, x, &ld) + (int64_t)r * ld + c0, t);
 #pragma unroll
       for (int w = 0; w < 4; ++w) in[i][w] = t[w];
     } else {
       float t[4];
-      ld_vec<4>(reinterpret_cast<const float*>(e.p) + off, t);
+      ld_run4(in_base<float>(e, x, &ld) + (int64_t)r * ld + c0, t);
 #pragma unroll
       for (int w = 0; w < 4; ++w) in[i][w] = t[w];
     }
@@ -475,15 +488,9 @@ cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles, 
     if (P.npad <= 0 || P.npad % 32 != 0) return P.npad <= 0 ? cudaSuccess : cudaErrorInvalidValue;
     grid = dim3((unsigned)(P.npad / 32), (unsigned)(P.npad / 32));
   }
-  // the vector form: inputs in the workspace, or a caller's single matrix whose
-  // base and row stride are multiples of 16 bytes; no transposed split
+  // the vector form serves every op without a transposed split (its loads fall
+  // back to single elements where a caller's run is not 16-byte aligned)
   bool vec = true;
-  for (int i = 0; i < P.nin; ++i) {
-    const EpiIn& in = P.in[i];
-    const size_t es = in.dt == DT_F64 ? 8 : 4;
-    const bool aligned = ((uintptr_t)in.p % 16 == 0) && ((size_t)in.ld * es) % 16 == 0;
-    vec &= in.mode == EPI_WS || (in.mode == EPI_PTR && !tiles && aligned);
-  }
   for (int j = 0; j < P.nout; ++j)
     for (int k = 0; k < P.out[j].nsplit; ++k) vec &= !P.out[j].split[k].transposed;
   bool in64 = false;
