@@ -1,0 +1,53 @@
+"""Host logic of bench.py that needs no GPU: the clock record keeps only the
+nvidia-smi samples taken inside the timed region, and every workload names its
+default step count."""
+
+import datetime
+import importlib.util
+import os
+import time
+
+from tests.conftest import ROOT
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _line(t, mhz, cap):
+    ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return (f"{ts}, 0, GPU-test, {mhz}, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, "
+            f"{'Active' if cap else 'Not Active'}\n")
+
+
+def test_clock_record_keeps_samples_inside_the_timed_region():
+    b = _bench()
+    c = b.ClockSampler("GPU-test")
+    now = time.time()
+    c.t0, c.t1 = now - 1.0, now
+    for t, mhz, cap in ((now - 1.4, 2070, False), (now - 0.7, 1600, True), (now - 0.3, 1500, True),
+                        (now + 0.2, 2070, False)):
+        c.tmp.write(_line(t, mhz, cap))
+    out = c.summary()
+    assert out["samples"] == 2 and out["sm_mhz"] == 1550 and out["reasons"] == ["sw_power_cap"]
+    assert out["sm_max_mhz"] == 2070 and "note" not in out
+
+
+def test_clock_record_of_a_region_shorter_than_the_interval():
+    b = _bench()
+    c = b.ClockSampler("GPU-test")
+    now = time.time()
+    c.t0, c.t1 = now - 0.05, now
+    c.tmp.write(_line(now - 0.5, 2070, False))
+    c.tmp.write(_line(now + 0.2, 1900, False))
+    out = c.summary()
+    assert out["samples"] == 2 and "note" in out and out["reasons"] == []
+
+
+def test_every_workload_has_default_steps():
+    b = _bench()
+    for name, wl in b.WORKLOADS.items():
+        assert isinstance(wl.get("steps"), int) and wl["steps"] >= 3, name
