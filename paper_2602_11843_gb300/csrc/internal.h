@@ -11,7 +11,7 @@ namespace neumann {
 enum : int { DT_F32 = 0, DT_F64 = 1 };
 
 constexpr int kMaxIn = 4;
-constexpr int kMaxOut = 4;
+constexpr int kMaxOut = 5;
 constexpr int kMaxDst = 2;
 constexpr int kMaxSplit = 2;
 

@@ -375,7 +375,12 @@ struct Sched {
         C.in[1] = g[1];
       }
       ops().push_back(op2);
-      // P3 = L3 R3; L4, R4 over (I, B, P1, P2, P3); C += g4 P3; P3 kept for the fifth factors
+      // P3 = L3 R3; L4, R4 over (I, B, P1, P2, P3); C += g4 P3. The parts of L5,
+      // R5 over (I, B, P1, P2, P3) come from this epilogue in a grouped batch,
+      // whose products are bound by their epilogues anyway. A single product's
+      // epilogue with five outputs would no longer hide behind its main loop,
+      // so there P3 is stored and an element-wise pass forms them.
+      const bool fold = p->grouped;
       Op op3 = mk_gemm(SL_LF1, SL_RF1);
       add_in(op3, R, REP_W);
       add_in(op3, SL_P1, REP_W);
@@ -391,24 +396,32 @@ struct Sched {
         Rr.in[1] = r4[2];
         Rr.in[2] = r4[3];
         add_out(op3, SL_C, REP_W, g[3], 0.0).in[3] = 1.0;
-        add_out(op3, SL_P3, REP_W, 1.0, 0.0);
+        if (fold) {
+          OutSpec& L5 = add_out(op3, SL_Q5L, REP_W, l5[4], l5[0]);
+          OutSpec& R5 = add_out(op3, SL_Q5R, REP_W, r5[4], r5[0]);
+          for (int j = 0; j < 3; ++j) {
+            L5.in[j] = l5[1 + j];
+            R5.in[j] = r5[1 + j];
+          }
+        } else {
+          add_out(op3, SL_P3, REP_W, 1.0, 0.0);
+        }
       }
       ops().push_back(op3);
-      // element-wise: the parts of L5, R5 over (I, B, P1, P2, P3)
-      Op ew = mk_ewise();
-      add_in(ew, R, REP_W);
-      add_in(ew, SL_P1, REP_W);
-      add_in(ew, SL_P2, REP_W);
-      add_in(ew, SL_P3, REP_W);
-      {
+      if (!fold) {  // element-wise: the parts of L5, R5 over (I, B, P1, P2, P3)
+        Op ew = mk_ewise();
+        add_in(ew, R, REP_W);
+        add_in(ew, SL_P1, REP_W);
+        add_in(ew, SL_P2, REP_W);
+        add_in(ew, SL_P3, REP_W);
         OutSpec& L = add_out(ew, SL_Q5L, REP_W, 0.0, l5[0]);
         OutSpec& Rr = add_out(ew, SL_Q5R, REP_W, 0.0, r5[0]);
         for (int j = 0; j < 4; ++j) {
           L.in[j] = l5[1 + j];
           Rr.in[j] = r5[1 + j];
         }
+        ops().push_back(ew);
       }
-      ops().push_back(ew);
       // P4 = L4 R4; L5 = Q5L + l5_P4 P4, R5 = Q5R + r5_P4 P4; C += g5 P4
       Op op4 = mk_gemm(SL_LF0, SL_RF0);
       add_in(op4, SL_Q5L, REP_W);
@@ -1640,11 +1653,15 @@ int neumann_plan_create_batched(neumann_plan_t* out, int count, int64_t max_n, i
     p->grouped = true;
     p->chunk = count < kGroupedChunk ? count : kGroupedChunk;
     p->npad = kGroupedMaxN;
+    int brc = NEUMANN_OK;
     try {
-      layout(p);
+      brc = build(p);  // the ops again, now for grouped launches, then the layout
     } catch (...) {
+      brc = NEUMANN_ENOMEM;
+    }
+    if (brc != NEUMANN_OK) {
       neumann_plan_destroy(p);
-      return NEUMANN_ENOMEM;
+      return brc;
     }
   }
   apply_tuned(p);

@@ -1,8 +1,8 @@
 """GPU parity of the five-product approximate kernels (radix 24 and 25).
 
-Each level runs five products plus one element-wise pass that forms the parts
-of the fifth factors over (I, B, P1, P2, P3), then the concatenation and
-residual products of the framework (Sec. 5.3). The reference is the oracle's
+Each level runs five products (the third product's epilogue writes five
+outputs, among them the parts of the fifth factors over I, B, P1, P2, P3),
+then the concatenation and residual products of the framework (Sec. 5.3). The reference is the oracle's
 result for the same scheme: Lemma 5.7's closed form on planted symmetric
 spectra, and the matrix iteration for other inputs. Tolerances are those of
 the other schemes at the same spectral radius (test_parity_gpu.py).
