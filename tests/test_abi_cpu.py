@@ -128,6 +128,28 @@ def test_library_radix_p5_coefficients_match_oracle(m):
         assert e.value.code == C.EINVAL
 
 
+@pytest.mark.parametrize("radix,k", [(24, 576), (25, 15625)])
+def test_five_product_levels_pass_count(radix, k):
+    """A single radix-24/25 plan forms the fifth factors' parts in one element-wise
+    pass per level (after the split of A); a grouped batch folds them into the
+    third product's epilogue, so it launches only the split and the products."""
+    levels = {576: 2, 15625: 3}[k]
+    h = C.neumann_plan_create(1024, k, radix, C.SPLIT_BF16, 0)
+    try:
+        i = C.neumann_plan_info(h)
+    finally:
+        C.neumann_plan_destroy(h)
+    assert i["products_executed"] == 7 * levels - 2
+    assert i["launches"] == i["products_executed"] + 1 + levels
+    hb = C.neumann_plan_create_batched(64, 256, k, radix, C.SPLIT_BF16, 0)
+    try:
+        ib = C.neumann_plan_info(hb)
+    finally:
+        C.neumann_plan_destroy(hb)
+    assert ib["products_executed"] == 7 * levels - 2
+    assert ib["launches"] == ib["products_executed"] + 1
+
+
 def test_batched_plan_and_empty_batch():
     h = C.neumann_plan_create_batched(4, 256, 81, 9, C.FP32, 0)
     try:
