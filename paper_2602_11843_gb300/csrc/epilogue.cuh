@@ -561,13 +561,13 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
 // ---------------------------------------------------------------------------
 // Chunk form for the tensor-core products: rows rbase .. rbase+31 of column c,
 // the accumulator of row rbase + i at stg[i * 33 + lane] (the warp's staged
-// 32 x 32 chunk). Interior chunks of ops the host marked `fast` (at most one
-// FP64 input, index f64_in) take a lean path: input addresses are formed once
-// per 8 rows, the identity term is applied only to the diagonal element,
-// non-finite results (and FP16 split overflow) are detected once per chunk,
-// and hi/lo pairs come from paired RN conversions (cvt.rn.bf16x2 / f16x2,
-// the same bits as two scalar conversions). Everything else (padding, ragged
-// edges, grouped row limits) goes through epi_col row group by row group.
+// 32 x 32 chunk). Chunks of ops the host marked `fast` (at most one FP64 input,
+// index f64_in) take a lean path: input addresses formed once per 8 rows, the
+// identity only on the diagonal element, non-finite results (and FP16 split
+// overflow) detected once per chunk, hi/lo pairs from paired RN conversions
+// (cvt.rn.bf16x2 / f16x2). Boundary chunks take it too when `edge_ok` (zeros
+// outside the n x n block); symmetric mirrors there, caller-owned inputs and
+// rows past a grouped tile's limit go through epi_col row group by row group.
 
 // hi/lo of (a, b) as packed pairs: low half from a, high half from b.
 template <bool kF16>

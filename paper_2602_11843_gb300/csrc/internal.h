@@ -84,7 +84,7 @@ struct EpiParams {
   const int* mat_n;
   int64_t mat_stride;
   // Set by the host for ops with at most one FP64 input (f64_in, else -1):
-  // the tensor-core epilogue may take its lean path on interior chunks.
+  // the tensor-core epilogue may take its lean path (boundary chunks: edge_ok).
   // f32_idx[0 .. nf32-1]: the FP32 inputs in index order.
   int fast;
   int f64_in;
