@@ -51,3 +51,12 @@ def test_every_workload_has_default_steps():
     b = _bench()
     for name, wl in b.WORKLOADS.items():
         assert isinstance(wl.get("steps"), int) and wl["steps"] >= 3, name
+
+
+def test_traffic_key_ignores_comments_only():
+    b = _bench()
+    code = "int f(int x) {  // doubles\n  /* block\n     comment */\n  return 2 * x;\n}\n"
+    same = "// header\nint f(int x) {\n\n  return 2 * x;  // changed comment\n}\n"
+    other = "int f(int x) {\n  return 3 * x;\n}\n"
+    assert b._code_only(code) == b._code_only(same)
+    assert b._code_only(code) != b._code_only(other)
