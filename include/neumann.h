@@ -17,7 +17,9 @@
  *             library's own, with exact prefix [T~]_j = 1 for j < m
  *             (neumann_radix_p5_coefficients)
  *   radix 0   exact kernels over the factorisation of k into 9, 5, 3, 2
- *             (block concatenation, Sec. 2.2, eq. decomposition)
+ *             (block concatenation, Sec. 2.2, eq. decomposition); with
+ *             NEUMANN_FLAG_ALLOW_APPROX also radix-15 levels (Lemma 5.7 holds
+ *             level by level, Sec. 5.3)
  * Every level applies a kernel f to the current residual R (R_0 = A), updates
  * the partial sum Y <- Y f(R) (Y_0 = I) and the residual R <- I - (I - R) f(R)
  * (Sec. 5.3, eq. generalradix and the proof of Lemma 5.7). For an exact
@@ -106,6 +108,13 @@ typedef enum {
                                              to 96 updates. 2-CTA 256 x 128 tiles; slower. Single plans only
                                              (a grouped batch's K is at most 256) */
 
+#define NEUMANN_FLAG_ALLOW_APPROX 0x100u /* radix 0: k = 2^a 3^b 5^c is split into the levels of least product
+                                             count over the exact kernels 2, 3, 5, 9 AND the approximate radix-15
+                                             kernel (ties: fewer radix-15 levels, then fewer levels); exact levels
+                                             run first, radix-15 levels last. The result is then the residual-
+                                             framework value of Lemma 5.7 for that level sequence, which agrees
+                                             with S_k through degree k-1 */
+
 #define NEUMANN_MAX_LEVELS 64
 
 typedef struct {
@@ -142,7 +151,7 @@ typedef struct {
  *   n      matrix order, >= 1
  *   k      number of series terms, >= 1; for radix 3, 5, 9, 15, 24, 25 a power of the radix;
  *          for radix 2 a power of two unless NEUMANN_FLAG_EXACT_K; for radix 0 of the
- *          form 2^a 3^b 5^c
+ *          form 2^a 3^b 5^c (levels as NEUMANN_FLAG_ALLOW_APPROX says)
  *   radix  0, 1, 2, 3, 5, 9, 15, 24 or 25 (see above)
  *   dtype  neumann_dtype_t
  *   flags  NEUMANN_FLAG_*
@@ -304,20 +313,44 @@ int neumann_radix_p5_coefficients(int m, double* coef41, double* prefix_error, d
  * a workspace, nor let neumann_plan_matmul allocate one.
  * Arithmetic and kernels are those of neumann_plan_matmul on a
  * NEUMANN_SPLIT_BF16 plan (hi/lo BF16 operands, three tensor-core products,
- * FP32 accumulation); the hi/lo operand scratch is a fixed 8 MiB device array
- * inside the library, present on every GPU that loads it until the process exits.
+ * FP32 accumulation); the scratch (a status word and the hi/lo operands) is a
+ * fixed device array of 8 MiB + 256 bytes inside the library, present on every
+ * GPU that loads the library's code until the process exits.
  *   n      order, 1 <= n <= 1024; larger n returns NEUMANN_EINVAL
  *   A, B   device, double, n x n row-major, leading dimensions lda, ldb >= n; read only
  *   C      device, double, n x n row-major, leading dimension ldc >= n; must not
  *          overlap A or B
- * Stream-ordered. The first call on a device looks up the scratch array's
- * device address (a runtime query, no allocation); make that first call before
- * any stream capture. Every call on a device shares the array: calls whose work
- * overlaps on the GPU (different streams, different host threads) race and must
- * be serialised by the caller. Device status bits are not reported.
- * Errors: NEUMANN_EINVAL, NEUMANN_ENOTSUP (device index >= 64), NEUMANN_ECUDA. */
+ *   stream a stream of the current device
+ * Stream-ordered. Set-up: under CUDA's default lazy module loading, the first
+ * call on a device loads the library's device code into that device's context,
+ * which is when the driver reserves the 8 MiB array (and the kernels' own
+ * memory); that load may synchronise the device. Make the first call in set-up
+ * code, before any stream capture and outside any allocator hook; later calls
+ * only look up the array's address (a runtime table query, no allocation).
+ * Every call on a device shares the array: calls whose work overlaps on the
+ * GPU (different streams, different host threads) race and must be serialised
+ * by the caller. Device status bits (a non-finite result, an expired bounded
+ * wait) are OR-ed into the array's status word; read them with
+ * neumann_matmul_noalloc_status.
+ * Errors: NEUMANN_EINVAL, NEUMANN_ECUDA. */
 int neumann_matmul_noalloc(int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
                            int64_t ldc, void* stream);
+
+/* Synchronise `stream` (of the current device), return in *status the OR of
+ * the NEUMANN_STATUS_* bits that neumann_matmul_noalloc calls on this device
+ * set since the previous read, and clear them. Allocates nothing. The paper
+ * has no counterpart to this call.
+ * Errors: NEUMANN_EINVAL (status NULL), NEUMANN_ECUDA. */
+int neumann_matmul_noalloc_status(void* stream, unsigned* status);
+
+/* Measurement aid (no counterpart in the paper): the CUDA cores' FMA rate of
+ * the current device in TFLOP/s, for dtype NEUMANN_FP32 or NEUMANN_FP64, from
+ * timed launches (CUDA events on `stream`, best of three after a warm-up) of a
+ * kernel whose threads run 8 independent FMA chains, 2048 threads per SM. It is
+ * the roofline denominator of the FP32 and FP64 product kernels. *sms (may be
+ * NULL) receives the device's SM count. Synchronises `stream`; allocates nothing.
+ * Errors: NEUMANN_EINVAL, NEUMANN_ECUDA. */
+int neumann_measure_fma_peak(int dtype, double* tflops, int* sms, void* stream);
 
 /* Release a plan and the workspace it allocated (not a caller-set one). NULL is ignored. */
 void neumann_plan_destroy(neumann_plan_t plan);

@@ -34,6 +34,7 @@ FLAG_IO_FP32 = 0x10
 FLAG_SINGLE_CTA = 0x20
 FLAG_PRECISE_ACC = 0x40
 FLAG_SYMMETRIC = 0x80
+FLAG_ALLOW_APPROX = 0x100
 
 MAX_LEVELS = 64
 
@@ -79,9 +80,11 @@ def _load():
         "neumann_plan_selftest_timeout": (c_int, [P, ctypes.c_uint64, c_void_p]),
         "neumann_matmul_noalloc": (c_int, [c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
                                            c_void_p]),
+        "neumann_matmul_noalloc_status": (c_int, [c_void_p, POINTER(c_uint32)]),
         "neumann_plan_autotune": (c_int, [P, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p]),
         "neumann_plan_autotune_batched": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_void_p), POINTER(c_void_p),
                                                   c_int, c_void_p]),
+        "neumann_measure_fma_peak": (c_int, [c_int, POINTER(c_double), POINTER(c_int), c_void_p]),
         "neumann_plan_destroy": (None, [P]),
         "neumann_error_string": (ctypes.c_char_p, [c_int]),
     }
@@ -213,6 +216,21 @@ def neumann_matmul_noalloc(n: int, A: int, lda: int, B: int, ldb: int, C: int, l
     """C = A B (FP64 in/out, split-BF16 tensor-core arithmetic) with no device
     allocation; the operand scratch is a fixed array inside the library, n <= 1024."""
     _check(_lib.neumann_matmul_noalloc(n, A, lda, B, ldb, C, ldc, stream), "neumann_matmul_noalloc")
+
+
+def neumann_matmul_noalloc_status(stream: int = 0) -> int:
+    """Synchronise `stream`; the NEUMANN_STATUS_* bits the allocation-free
+    product set on the current device since the last read (then cleared)."""
+    v = c_uint32()
+    _check(_lib.neumann_matmul_noalloc_status(stream, byref(v)), "neumann_matmul_noalloc_status")
+    return v.value
+
+
+def neumann_measure_fma_peak(dtype: int, stream: int = 0):
+    """(TFLOP/s of the CUDA cores' FMA pipe for FP32 or FP64, SM count) of the current device."""
+    t, n = c_double(), c_int()
+    _check(_lib.neumann_measure_fma_peak(dtype, byref(t), byref(n), stream), "neumann_measure_fma_peak")
+    return t.value, n.value
 
 
 def neumann_plan_destroy(plan: int) -> None:

@@ -13,19 +13,27 @@
 // plan. An element-wise pass splits A and B into row-major hi/lo BF16 pairs
 // (the kernel reads B's pair MN-major), then the persistent tcgen05 kernel forms
 // Ahi Bhi + Ahi Blo + Alo Bhi and writes C. The only difference is where the
-// hi/lo operand scratch lives: in g_noalloc_scratch below, a file-scope device
-// array that the CUDA runtime places in every device context that loads this
-// library and keeps until the process exits. Its size fixes the largest order
-// this call accepts, kNoAllocMaxN = 1024 (4 matrices x 1024^2 x 2 bytes = 8 MiB).
+// scratch lives: in g_noalloc_scratch below, a file-scope device array that the
+// CUDA runtime places in every device context that loads this library's code
+// and keeps until the process exits. It holds a 256-byte status block (the
+// device status word, NEUMANN_STATUS_* bits, read and cleared by
+// neumann_matmul_noalloc_status) followed by the four operand matrices. Its
+// size fixes the largest order this call accepts, kNoAllocMaxN = 1024
+// (4 matrices x 1024^2 x 2 bytes = 8 MiB).
 //
 // Sharing: every call on a device uses the same array. The split pass rewrites
-// all of it (padding included) before the product reads it, so no contents
-// need to survive between calls and nothing has to start at zero. Calls whose
+// all of the operand area (padding included) before the product reads it, so
+// no operand contents need to survive between calls; the status word starts at
+// zero when the module is loaded and is cleared only by its reader. Calls whose
 // work overlaps on the GPU (concurrent streams, or host threads on different
 // streams) race on the array; serialise them.
+//
+// The device address of the array is looked up on every call, with the
+// caller's device current (the stream must belong to that device). Once the
+// module is loaded the lookup is a runtime table query that allocates nothing;
+// looking it up per call, rather than caching it, keeps a call correct after
+// the primary context was reset and the module reloaded at another address.
 #include <string.h>
-
-#include <mutex>
 
 #include "internal.h"
 #include "neumann.h"
@@ -36,29 +44,20 @@ namespace {
 constexpr int64_t kNoAllocMaxN = 1024;
 constexpr size_t kNoAllocMatBytes = (size_t)kNoAllocMaxN * kNoAllocMaxN * 2;  // one BF16 matrix
 
-// Ahi | Alo | Bhi | Blo, each padded_n x padded_n with padded_n <= 1024.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[4 * kNoAllocMatBytes];
+constexpr size_t kStatusBytes = 256;  // status word, padded to keep the operands 256-byte aligned
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+// status block | Ahi | Alo | Bhi | Blo, each matrix padded_n x padded_n with padded_n <= 1024.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kStatusBytes + 4 * kNoAllocMatBytes];
 
-// The host symbol g_noalloc_scratch is only a handle; its device address is
-// looked up once per device, with that device current.
+// The host symbol g_noalloc_scratch is only a handle; its device address in
+// the current device's context is looked up with that device current.
 int scratch_address(char** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return NEUMANN_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return NEUMANN_ENOTSUP;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return NEUMANN_ECUDA;
-    }
-    g_noalloc_ptr[dev] = p;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return NEUMANN_ECUDA;
   }
-  *out = reinterpret_cast<char*>(g_noalloc_ptr[dev]);
+  *out = reinterpret_cast<char*>(p);
   return NEUMANN_OK;
 }
 
@@ -69,7 +68,7 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
 }
 
 // Element-wise split of one FP64 matrix into a row-major hi/lo pair.
-EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char* hi, char* lo) {
+EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char* hi, char* lo, unsigned* status) {
   EpiParams P;
   memset(&P, 0, sizeof(P));
   P.n = (int)n;
@@ -83,7 +82,7 @@ EpiParams split_params(int64_t n, int64_t npad, const void* X, int64_t ldx, char
   o.f64 = 1;
   o.nsplit = 1;
   o.split[0] = EpiSplit{hi, lo, npad, 0};
-  P.status = nullptr;
+  P.status = status;
   P.f64_in = -1;
   return P;
 }
@@ -105,15 +104,17 @@ extern "C" int neumann_matmul_noalloc(int64_t n, const void* A, int64_t lda, con
   if (rc) return rc;
   const int64_t npad = (n + 255) / 256 * 256;
   const size_t mat = (size_t)npad * (size_t)npad * 2;
+  unsigned* status = reinterpret_cast<unsigned*>(ws);
+  ws += kStatusBytes;
   char* a_hi = ws;
   char* a_lo = ws + mat;
   char* b_hi = ws + 2 * mat;
   char* b_lo = ws + 3 * mat;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-  EpiParams pa = split_params(n, npad, A, lda, a_hi, a_lo);
+  EpiParams pa = split_params(n, npad, A, lda, a_hi, a_lo, status);
   if (launch_ewise(pa, s) != cudaSuccess) return NEUMANN_ECUDA;
-  EpiParams pb = split_params(n, npad, B, ldb, b_hi, b_lo);
+  EpiParams pb = split_params(n, npad, B, ldb, b_hi, b_lo, status);
   if (launch_ewise(pb, s) != cudaSuccess) return NEUMANN_ECUDA;
 
   TcMaps maps;
@@ -129,9 +130,27 @@ extern "C" int neumann_matmul_noalloc(int64_t n, const void* A, int64_t lda, con
   pc.out[0].f64 = 1;
   pc.out[0].ndst = 1;
   pc.out[0].dst[0] = EpiDst{C, ldc, DT_F64, EPI_PTR};
-  pc.status = nullptr;
+  pc.status = status;
   pc.fast = 1;
   pc.f64_in = -1;
   if (launch_tc_gemm(maps, npad, pc, s) != cudaSuccess) return NEUMANN_ECUDA;
+  return NEUMANN_OK;
+}
+
+extern "C" int neumann_matmul_noalloc_status(void* stream, unsigned* status) {
+  if (!status) return NEUMANN_EINVAL;
+  *status = 0;
+  char* ws = nullptr;
+  int rc = scratch_address(&ws);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned v = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess ||
+      cudaMemcpyAsync(&v, ws, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return NEUMANN_ECUDA;
+  if (v && (cudaMemsetAsync(ws, 0, sizeof(v), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
+    return NEUMANN_ECUDA;
+  *status = v;
   return NEUMANN_OK;
 }
