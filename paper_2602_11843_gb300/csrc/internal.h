@@ -6,7 +6,53 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace neumann {
+
+// Values a launcher looks up once (SM count, resident clusters, a kernel's
+// shared-memory attribute) belong to one device: a process may drive several
+// GPUs from several host threads. They are cached per device index, 0 meaning
+// "not looked up yet"; two threads that race on an entry compute the same value.
+constexpr int kMaxDevices = 64;
+
+inline int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return d >= 0 && d < kMaxDevices ? d : -1;
+}
+
+// The cached value for the current device, computing it with `get` (which
+// returns a value > 0, or <= 0 on failure: not cached) on first use.
+template <typename F>
+inline int per_device_value(std::atomic<int> (&cache)[kMaxDevices], F get) {
+  const int d = current_device();
+  if (d < 0) return get();
+  int v = cache[d].load(std::memory_order_acquire);
+  if (v <= 0) {
+    v = get();
+    if (v > 0) cache[d].store(v, std::memory_order_release);
+  }
+  return v;
+}
+
+// Runs `init` (returning cudaError_t) once per device; later calls on that
+// device return its first result.
+template <typename F>
+inline cudaError_t once_per_device(std::atomic<int> (&state)[kMaxDevices], F init) {
+  const int d = current_device();
+  if (d < 0) return cudaErrorInvalidDevice;
+  int s = state[d].load(std::memory_order_acquire);
+  if (s == 0) {
+    const cudaError_t e = init();
+    s = e == cudaSuccess ? 1 : 2 + (int)e;
+    state[d].store(s, std::memory_order_release);
+  }
+  return s == 1 ? cudaSuccess : (cudaError_t)(s - 2);
+}
 
 enum : int { DT_F32 = 0, DT_F64 = 1 };
 
@@ -43,9 +89,8 @@ struct EpiDst {
 
 // A split store, row-major or transposed:
 //   BF16: hi = RN_bf16(v), lo = RN_bf16(v - hi)
-//   FP16: w = v * 2^8, hi = RN_fp16(w), lo = RN_fp16(w - hi)  (the fixed power of
-//         two keeps lo out of the FP16 subnormals for |v| >= 2^-11 and limits |v| to
-//         < 2^7; a product of two such operands carries 2^16, removed in the epilogue)
+//   FP16: w = v * 2^e, hi = RN_fp16(w), lo = RN_fp16(w - hi), with the matrix's
+//         own e (SxParams below)
 struct EpiSplit {
   void* hi;
   void* lo;
@@ -53,7 +98,47 @@ struct EpiSplit {
   int transposed;
 };
 
-constexpr float kFp16SplitScale = 256.0f;  // 2^8
+// Per-matrix power-of-two scaling of the FP16 split operands. Every matrix a
+// split-FP16 plan stores as a hi/lo pair is stored as x * 2^e with its own e,
+// chosen before the producing launch from a bound on max |x| so that the bound
+// maps to at most 2^14: hi never overflows FP16 (65504) and lo stays a normal
+// FP16 number down to |x| ~ 2^-17 of the bound. A product of operands stored
+// with e_A and e_B carries 2^(e_A + e_B), removed exactly in its epilogue.
+// The bound of an output comes from "records" of what earlier launches wrote:
+//   amax    max |x| (IEEE bits; a product's epilogue measures it with atomicMax,
+//           an element-wise pass stores its bound)
+//   colmax  max_j sum_i |x_ij|, the largest column sum (from `col`, the column
+//           sums a product's epilogue accumulates, or an element-wise bound)
+//   exp     the e its split was stored with
+// For out = a (L R) + sum_i c_i in_i + d I:
+//   |out_ij| <= |a| amax(L) colmax(R) + sum_i |c_i| amax(in_i) + |d|
+// (|(L R)_ij| <= max|L| sum_k |R_kj|). fp16_scale_kernel evaluates this before
+// each launch; the input stats kernel measures the caller's matrices.
+constexpr float kFp16SplitScale = 256.0f;  // 2^8 (fixed scale, being replaced)
+constexpr int kSxTarget = 14;  // the bound is mapped to at most 2^14
+constexpr int kSxMaxExp = 60;  // |e| <= 60 keeps every scale a normal FP32 power of two
+
+struct SxParams {
+  int active;        // split-FP16 plan: the fields below are valid
+  int nmat;          // matrices per record (1, or the matrices of a grouped pass)
+  int npad;          // padded order (column-sum arrays hold npad entries per matrix)
+  unsigned* amax;    // [rec * nmat + m], float bits
+  float* colmax;     // [rec * nmat + m]
+  int* exp;          // [rec * nmat + m]
+  float* col;        // column sums: record r at col + col_off[r] (+ m * npad)
+  const int64_t* col_off;  // device [rec]: offset of the record's column sums, -1 if it has none
+  int rec_a, rec_b;  // records of a product's operands (-1: element-wise pass)
+  int rec_out[kMaxOut];     // record of each output (-1: the caller's S, no record)
+  int64_t col_out[kMaxOut]; // offset of the output's column sums (-1: none accumulated)
+};
+
+// One launch's FP16 scales for one matrix, read at tile start.
+struct SxTile {
+  float acc;            // 2^-(e_A + e_B): the accumulator in true units
+  float sc[kMaxOut];    // 2^e of each output's split
+  unsigned* amax[kMaxOut];  // where each output's max |x| is recorded (nullptr: not)
+  float* col[kMaxOut];      // its column sums for this matrix (nullptr: not)
+};
 
 // out = acc_coef * acc + sum_i in_coef[i] * in[i] + id_coef * [r == c]
 struct EpiOut {
@@ -94,6 +179,7 @@ struct EpiParams {
   // in bounds, so the lean path may also take boundary chunks (zeros stored
   // outside the n x n block, the caller's matrices written inside it only).
   int edge_ok;
+  SxParams sx;  // split-FP16 scaling (sx.active = 0 otherwise)
 };
 
 // Split-operand tensor maps of one tensor-core product C = A B:
@@ -121,6 +207,11 @@ struct TcMaps {
 constexpr int kDefaultRasterGroup = 8;
 
 // ---- launchers (kernels_simt.cu) ----
+// Streaming multiprocessors of the current device (cached per device; 1 if unknown).
+int sm_count();
+// The CUDA cores' FMA rate (FP32, or FP64 when f64), TFLOP/s: the best of three
+// timed launches of independent FMA chains on every SM (synchronises `s`).
+cudaError_t measure_fma_peak(int f64, double* tflops, cudaStream_t s);
 // tiles == nullptr: one padded npad x npad product. Otherwise a grouped launch
 // over a batch: ntiles entries {matrix, tile row, tile column, K steps of 8}.
 // sym (single products only): the product is symmetric; only the 128 x 128

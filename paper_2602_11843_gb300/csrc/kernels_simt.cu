@@ -408,19 +408,6 @@ __global__ void __launch_bounds__(256, NI <= 2 ? 3 : 2) ewise_vec_kernel(const i
   epi_flag(P, bad);
 }
 
-int sm_count() {
-  static int n = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess)
-      n = 0;
-    cudaGetLastError();
-  });
-  return n > 0 ? n : 152;
-}
-
 template <int NI, bool kIn64>
 void launch_ewise_vec(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles, int tpr) {
   const int want = (ntiles + 1) / 2;  // two tiles per CTA and step
@@ -446,11 +433,10 @@ cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const 
   if (npad % BM != 0 || npad % BN != 0 || ld < npad) return cudaErrorInvalidValue;
   // FP32: 64 running sums per thread in dynamic shared memory (64 KB)
   constexpr size_t dyn = sizeof(T) == 4 ? 64 * TPB * sizeof(float) : 0;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
+  static std::atomic<int> attr_state[kMaxDevices];
   if (dyn) {
-    std::call_once(once, [] {
-      attr = cudaFuncSetAttribute(simt_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    const cudaError_t attr = once_per_device(attr_state, [] {
+      return cudaFuncSetAttribute(simt_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     });
     if (attr != cudaSuccess) return attr;
   }
@@ -477,6 +463,84 @@ cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, i
 cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int64_t npad, const int4* tiles,
                                  int ntiles, const EpiParams& P, cudaStream_t s, bool sym) {
   return launch_simt<float>(A, B, ld, npad, tiles, ntiles, P, s, sym);
+}
+
+// ---- CUDA-core peak probe ----
+// Every thread runs kChains independent FMA chains a = a * b + c for `iters`
+// rounds (2 flops per FMA), so the FMA pipes see kChains independent
+// instructions per warp per round; the grid holds 2048 threads per SM. The
+// sum of the chains is written only if it equals a value it cannot reach,
+// which keeps the compiler from removing the loop without a store per thread.
+constexpr int kPeakChains = 8;
+constexpr int kPeakThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kPeakThreads) fma_peak_kernel(T* sink, int iters, T b, T c) {
+  T a[kPeakChains];
+#pragma unroll
+  for (int j = 0; j < kPeakChains; ++j) a[j] = (T)(threadIdx.x + j) * (T)1e-3;
+#pragma unroll 1
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int j = 0; j < kPeakChains; ++j) a[j] = fma(a[j], b, c);
+    }
+  }
+  T t = 0;
+#pragma unroll
+  for (int j = 0; j < kPeakChains; ++j) t += a[j];
+  if (t == (T)-12345.678) *sink = t;
+}
+
+__device__ double g_peak_sink;
+
+cudaError_t measure_fma_peak(int f64, double* tflops, cudaStream_t s) {
+  *tflops = 0.0;
+  double* sink = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&sink), g_peak_sink);
+  if (e != cudaSuccess) return e;
+  const int grid = sm_count() * (2048 / kPeakThreads);
+  // a few ms of FMA work per launch on either pipe at GB300's rates
+  const int iters = f64 ? 64 : 4096;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return e;
+  }
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first run is a warm-up
+    cudaEventRecord(e0, s);
+    if (f64)
+      fma_peak_kernel<double><<<grid, kPeakThreads, 0, s>>>(sink, iters, 0.999999, 1e-7);
+    else
+      fma_peak_kernel<float><<<grid, kPeakThreads, 0, s>>>(reinterpret_cast<float*>(sink), iters, 0.999999f, 1e-7f);
+    cudaEventRecord(e1, s);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  const double flops = 2.0 * kPeakChains * 16.0 * iters * (double)grid * kPeakThreads;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  return cudaSuccess;
+}
+
+int sm_count() {
+  static std::atomic<int> cache[kMaxDevices];
+  const int n = per_device_value(cache, [] {
+    const int d = current_device();
+    int v = 0;
+    if (d < 0 || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return v;
+  });
+  return n > 0 ? n : 1;
 }
 
 cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles) {

@@ -77,8 +77,8 @@ struct EpiShape {
 };
 constexpr uint32_t ACC_COLS = BN;              // one FP32 accumulator: 128 lanes x 256 columns
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // double-buffered
-constexpr uint64_t kTimeoutNs = 2000000000ull;
-constexpr int64_t kPairMinN = 4096;  // padded orders from which a product runs on CTA pairs  // 2 s; a whole launch normally takes < 20 ms
+constexpr uint64_t kTimeoutNs = 2000000000ull;  // 2 s; a whole launch normally takes < 20 ms
+constexpr int64_t kPairMinN = 4096;  // padded orders from which a product runs on CTA pairs
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A and B both
 // BF16 (format 1 at bits 7-9 and 10-12) or both FP16 (format 0), both K-major
@@ -1023,9 +1023,8 @@ cudaError_t launch_wait_probe(unsigned* status, uint64_t limit_ns, cudaStream_t 
 namespace {
 
 cudaError_t set_smem_attributes() {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
+  static std::atomic<int> state[kMaxDevices];
+  return once_per_device(state, [] {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e[6] = {
         cudaFuncSetAttribute(tc_split_gemm_kernel<false, false, false>, a, (int)EpiShape<false, false>::kSmem),
@@ -1035,9 +1034,22 @@ cudaError_t set_smem_attributes() {
         cudaFuncSetAttribute(tc_split_gemm_kernel<false, false, true>, a, (int)EpiShape<false, true>::kSmem),
         cudaFuncSetAttribute(tc_split_gemm_kernel<false, true, true>, a, (int)EpiShape<false, true>::kSmem)};
     for (cudaError_t x : e)
-      if (x != cudaSuccess) attr_err = x;
+      if (x != cudaSuccess) return x;
+    return cudaSuccess;
   });
-  return attr_err;
+}
+
+// Clusters of the kernel that can be resident at once on the current device.
+template <typename K>
+int resident_clusters(K k, cudaLaunchConfig_t cfg, std::atomic<int> (&cache)[kMaxDevices]) {
+  return per_device_value(cache, [&] {
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return nc;
+  });
 }
 
 // One product on CTA pairs: as many 2-CTA clusters as can be resident at once
@@ -1058,15 +1070,10 @@ cudaError_t launch_pair(const TcMaps& maps, int64_t npad, const EpiParams& P, cu
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  static int max_pairs = 0;
-  if (max_pairs == 0) {
-    cfg.gridDim = dim3(2 * tiles_m * tiles_n);
-    int nc = 0;
-    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, k, &cfg);
-    if (e != cudaSuccess) return e;
-    if (nc <= 0) return cudaErrorInvalidConfiguration;
-    max_pairs = nc;
-  }
+  static std::atomic<int> cache[kMaxDevices];
+  cfg.gridDim = dim3(2 * tiles_m * tiles_n);
+  const int max_pairs = resident_clusters(k, cfg, cache);
+  if (max_pairs <= 0) return cudaErrorInvalidConfiguration;
   const int work = maps.sym ? maps.nsym : tiles_m * tiles_n;
   const int pairs = work < max_pairs ? work : max_pairs;
   cfg.gridDim = dim3(2 * pairs);
@@ -1077,11 +1084,9 @@ cudaError_t launch_pair(const TcMaps& maps, int64_t npad, const EpiParams& P, cu
 template <bool kF16>
 cudaError_t launch_precise(const TcMaps& maps, int64_t npad, const EpiParams& P, cudaStream_t s) {
   auto k = tc_precise_kernel<kF16>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PQ_SMEM);
-  });
+  static std::atomic<int> attr_state[kMaxDevices];
+  const cudaError_t attr_err = once_per_device(
+      attr_state, [&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PQ_SMEM); });
   if (attr_err != cudaSuccess) return attr_err;
   const int tiles_m = (int)(npad / (2 * BM)), tiles_n = (int)(npad / PQ_N);
   cudaLaunchAttribute attr[1];
@@ -1095,15 +1100,10 @@ cudaError_t launch_precise(const TcMaps& maps, int64_t npad, const EpiParams& P,
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  static int max_pairs = 0;
-  if (max_pairs == 0) {
-    cfg.gridDim = dim3(2 * tiles_m * tiles_n);
-    int nc = 0;
-    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, k, &cfg);
-    if (e != cudaSuccess) return e;
-    if (nc <= 0) return cudaErrorInvalidConfiguration;
-    max_pairs = nc;
-  }
+  static std::atomic<int> cache[kMaxDevices];
+  cfg.gridDim = dim3(2 * tiles_m * tiles_n);
+  const int max_pairs = resident_clusters(k, cfg, cache);
+  if (max_pairs <= 0) return cudaErrorInvalidConfiguration;
   const int pairs = tiles_m * tiles_n < max_pairs ? tiles_m * tiles_n : max_pairs;
   cfg.gridDim = dim3(2 * pairs);
   return cudaLaunchKernelEx(&cfg, k, maps.a_hi, maps.a_lo, maps.b_hi, maps.b_lo, (int)(npad / BK), tiles_m, tiles_n,
@@ -1117,12 +1117,7 @@ cudaError_t launch_tc_gemm(const TcMaps& maps, int64_t npad, const EpiParams& P,
   if (npad % BN != 0) return cudaErrorInvalidValue;
   cudaError_t attr_err = set_smem_attributes();
   if (attr_err != cudaSuccess) return attr_err;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-  }
+  const int sms = sm_count();
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
     const int grid = ntiles < sms ? ntiles : sms;

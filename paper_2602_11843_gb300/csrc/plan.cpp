@@ -720,6 +720,66 @@ int build(neumann_plan_s* p) {
   return NEUMANN_OK;
 }
 
+// Radix 0 with NEUMANN_FLAG_ALLOW_APPROX: the levels of least product count
+// sum_i (mu_{m_i} + 2) (Sec. 2.2 cost model) with prod_i m_i = k, over the
+// exact kernels 2, 3, 5, 9 and the approximate radix-15 kernel; among equal
+// counts, fewer approximate levels, then fewer levels. Block concatenation
+// (Sec. 2.2) and Lemma 5.7 (Sec. 5.3) hold level by level, so any order is
+// valid; the exact levels run first (9, 5, 3, 2) and the radix-15 levels last,
+// where the residual they act on is a power of A of small norm, far inside
+// the kernel's convergence region. k = 2^a 3^b 5^c only (else false).
+bool mixed_levels(int64_t k, std::vector<int>* levels) {
+  int e[3] = {0, 0, 0};
+  int64_t q = k;
+  const int prime[3] = {2, 3, 5};
+  for (int i = 0; i < 3; ++i)
+    while (q % prime[i] == 0) {
+      q /= prime[i];
+      ++e[i];
+    }
+  if (q != 1 || k < 1) return false;
+  struct Factor {
+    int m, d2, d3, d5, approx;
+  };
+  const Factor fac[5] = {{2, 1, 0, 0, 0}, {3, 0, 1, 0, 0}, {5, 0, 0, 1, 0}, {9, 0, 2, 0, 0}, {15, 0, 1, 1, 1}};
+  // cost (products, approximate levels, levels) of the best split of 2^a 3^b 5^c
+  typedef std::tuple<int, int, int> Cost;
+  const int A = e[0] + 1, B = e[1] + 1, Cc = e[2] + 1;
+  std::vector<Cost> best((size_t)A * B * Cc, Cost(1 << 30, 0, 0));
+  std::vector<int> pick((size_t)A * B * Cc, -1);
+  auto at = [&](int a, int b, int c) { return ((size_t)a * B + b) * Cc + c; };
+  best[at(0, 0, 0)] = Cost(0, 0, 0);
+  for (int a = 0; a < A; ++a)
+    for (int b = 0; b < B; ++b)
+      for (int c = 0; c < Cc; ++c) {
+        if (a + b + c == 0) continue;
+        for (int f = 0; f < 5; ++f) {
+          const Factor& x = fac[f];
+          if (a < x.d2 || b < x.d3 || c < x.d5) continue;
+          const Cost& prev = best[at(a - x.d2, b - x.d3, c - x.d5)];
+          if (std::get<0>(prev) >= (1 << 30)) continue;
+          const Cost cand(std::get<0>(prev) + mu_of(x.m) + 2, std::get<1>(prev) + x.approx, std::get<2>(prev) + 1);
+          if (cand < best[at(a, b, c)]) {
+            best[at(a, b, c)] = cand;
+            pick[at(a, b, c)] = f;
+          }
+        }
+      }
+  std::vector<int> ms;
+  for (int a = e[0], b = e[1], c = e[2]; a + b + c > 0;) {
+    const Factor& x = fac[pick[at(a, b, c)]];
+    ms.push_back(x.m);
+    a -= x.d2;
+    b -= x.d3;
+    c -= x.d5;
+  }
+  levels->clear();
+  for (int m : {9, 5, 3, 2, 15})
+    for (int x : ms)
+      if (x == m) levels->push_back(m);
+  return true;
+}
+
 int validate_and_levels(neumann_plan_s* p) {
   const int64_t k = p->k;
   p->levels.clear();
@@ -745,6 +805,10 @@ int validate_and_levels(neumann_plan_s* p) {
       if (!pure_power(k, p->radix, &p->levels)) return NEUMANN_EINVAL;
       break;
     case 0: {
+      if (p->flags & NEUMANN_FLAG_ALLOW_APPROX) {
+        if (!mixed_levels(k, &p->levels)) return NEUMANN_EINVAL;
+        break;
+      }
       int64_t q = k;
       for (int m : {9, 5, 3, 2}) {
         while (q % m == 0) {
@@ -1782,6 +1846,14 @@ void neumann_plan_destroy(neumann_plan_t p) {
   if (p->h_tab) cudaFreeHost(p->h_tab);
   if (p->ws_owned) cudaFree(p->ws);
   delete p;
+}
+
+int neumann_measure_fma_peak(int dtype, double* tflops, int* sms, void* stream) {
+  if (!tflops || (dtype != NEUMANN_FP32 && dtype != NEUMANN_FP64)) return NEUMANN_EINVAL;
+  if (sms) *sms = sm_count();
+  return measure_fma_peak(dtype == NEUMANN_FP64, tflops, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? NEUMANN_OK
+             : NEUMANN_ECUDA;
 }
 
 const char* neumann_error_string(int code) {
