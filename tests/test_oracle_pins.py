@@ -338,6 +338,21 @@ def test_probe_horner():
     assert CF.rel_fro(CF.horner_probes(A, X, 40), S @ X) < 1e-14
 
 
+@pytest.mark.parametrize("n", [5, 300])
+def test_probe_horner_from_factors_matches_dense(n):
+    """Horner with A applied from its generator's factors (compact WY form of
+    the reflectors plus the rank-32 term) against Horner on the dense A the
+    generator returns: the same matrix, so the same S_k X to rounding."""
+    inp = G.config_inputs(5, n=n)
+    X = inp["probes"][:, :8]
+    dense = CF.horner_probes(inp["A"], X, 3375)
+    fact = CF.horner_probes_factored(inp["V"], inp["lam"], inp["X"], inp["Y"], X, 3375)
+    assert CF.rel_fro(fact, dense) < 1e-13
+    # and the factored product alone, on the identity: rebuilds A column by column
+    one = CF.horner_probes_factored(inp["V"], inp["lam"], inp["X"], inp["Y"], np.eye(n), 2) - np.eye(n)
+    assert np.abs(one - inp["A"]).max() < 1e-13
+
+
 # ---------------------------------------------------------------- generators
 
 def test_generators_shapes_and_spectra():
