@@ -88,6 +88,52 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+_PEAKS_LIVE = {}
+
+
+def live_peaks(dev):
+    """Denominators that MEASURED_PEAKS.json does not hold, measured on this
+    device in this run (no clock or setting is changed):
+      sms               the device's SM count
+      fp32_tflops       CUDA-core FP32 FMA rate (neumann_measure_fma_peak: timed
+      fp64_tflops       launches of independent FMA chains on every SM), FP64 likewise
+      fp16_over_bf16    cuBLAS FP16 / BF16 dense GEMM rate at 8192^3 (torch.matmul,
+                        best of 5 each, CUDA events), the factor that turns the
+                        measured BF16 tensor peak into the FP16 one
+    """
+    if dev in _PEAKS_LIVE:
+        return _PEAKS_LIVE[dev]
+    import torch
+
+    import paper_2602_11843_gb300 as nm
+
+    stream = torch.cuda.current_stream(dev)
+    f32, sms = nm.neumann_measure_fma_peak(nm.FP32, stream.cuda_stream)
+    f64, _ = nm.neumann_measure_fma_peak(nm.FP64, stream.cuda_stream)
+    rates = {}
+    n = 8192
+    for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16)):
+        a = torch.randn((n, n), device=dev, dtype=dt)
+        b = torch.randn((n, n), device=dev, dtype=dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for rep in range(6):
+            e0.record(stream)
+            torch.matmul(a, b)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+        rates[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b
+    out = {"sms": sms, "fp32_tflops": f32, "fp64_tflops": f64,
+           "bf16_tflops_torch_burst": rates["bf16"], "fp16_tflops_torch_burst": rates["fp16"],
+           "fp16_over_bf16": rates["fp16"] / rates["bf16"]}
+    _PEAKS_LIVE[dev] = out
+    return out
+
+
 def _code_only(text):
     """C++/CUDA source without its comments and blank lines: edits to comments
     leave the key of a captured kernel unchanged."""
@@ -215,10 +261,17 @@ class ClockSampler:
         return out
 
 
+_INPUTS = {}
+
+
 def make_input(wl, seed_rep):
     from workloads import generators as G
 
-    return G.config_inputs(wl["cfg"], r=seed_rep, n=wl["n"])
+    key = (wl["cfg"], seed_rep, wl["n"])
+    if key not in _INPUTS:
+        _INPUTS.clear()  # one workload's input at a time (n = 16384 holds 2 GB)
+        _INPUTS[key] = G.config_inputs(wl["cfg"], r=seed_rep, n=wl["n"])
+    return _INPUTS[key]
 
 
 def cpu_baseline(wl, A_np, budget_products=None):
@@ -243,8 +296,43 @@ def cpu_baseline(wl, A_np, budget_products=None):
     dt = time.perf_counter() - t0
     per_product = dt / alg.products
     return {"value": 1.0 / (per_product * total), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "extrapolated": f"{alg.products} of {total} products timed, scaled to {total}",
             "sample": f"first-level radix-{wl['radix']} kernel ({alg.products} of {total} products) at n={n}, "
                       f"FP64 NumPy/BLAS, scaled by product count; {dt:.1f} s"}
+
+
+def oracle_error(wl, inp, S_np):
+    """CPU-baseline leg, second part: the oracle's FP64 result for the same input
+    (closed form on the planted spectrum: S_k for exact radices, Lemma 5.7's value
+    for radix 15, 24, 25) and the GPU result's relative Frobenius error against it."""
+    from oracle import closed_form as CF
+    from oracle import evaluate as EV
+
+    if "V" not in inp or "X" in inp:  # no closed form (the perturbed n = 16384 input)
+        return None
+    t0 = time.perf_counter()
+    ref = EV.planted_reference(inp["V"], inp["lam"], wl["k"], wl["radix"])
+    err = CF.rel_fro(S_np, ref)
+    out = {"rel_fro": err, "reference": "oracle closed form, FP64 (" +
+           ("Lemma 5.7 framework value" if wl["radix"] in EV.APPROX else "S_k") + ")",
+           "host_s": round(time.perf_counter() - t0, 1)}
+    if wl["radix"] in EV.APPROX:
+        out["framework_vs_sk"] = CF.rel_fro(ref, EV.planted_reference(inp["V"], inp["lam"], wl["k"], 1))
+    return out
+
+
+def oracle_error_batched(wl, mats, outs, every=64):
+    """CPU-baseline leg for a batch: every `every`-th matrix against the oracle's
+    matrix scheme (FP64); the largest and median relative Frobenius error."""
+    import numpy as np
+
+    from oracle import closed_form as CF
+    from oracle import evaluate as EV
+
+    errs = [CF.rel_fro(outs[i].double().cpu().numpy(), EV.evaluate(mats[i]["A"], wl["k"], wl["radix"])[0])
+            for i in range(0, len(mats), every)]
+    return {"max_rel_fro": float(np.max(errs)), "median_rel_fro": float(np.median(errs)),
+            "matrices_checked": len(errs), "reference": "oracle matrix scheme, FP64"}
 
 
 def run_reference(args, wl):
@@ -317,9 +405,10 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, wl):
+def run_batched(args, wl, sub=False):
     """cfg 4: one grouped evaluation of the whole batch per step; compared with the
-    same batch evaluated one matrix (one plan, its own launches) at a time."""
+    same batch evaluated one matrix (one plan, its own launches) at a time.
+    sub: a secondary workload of the default run (one process): returns its line."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -330,7 +419,9 @@ def run_batched(args, wl):
     rank, world, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
+    if sub:
+        world = 1
+    elif world > 1:
         dist.init_process_group("nccl", device_id=dev)
     mats = G.jacobi_batch(wl["count"], 1000 * wl["cfg"] + rank)
     ns = [m["n"] for m in mats]
@@ -418,8 +509,8 @@ def run_batched(args, wl):
     prod_s = sum(prod_ms) / args.steps / 1e3  # product time per step
     bytes_step = sum(n * n for n in ns) * info["product_bytes_per_element"]
     flops_step = per * flops_one * (3 if tc else 1)
-    sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fpeak = peaks["bf16_tflops_sustained"] if tc else 152 * 128 * 2 * sm_hz / 1e12
+    live = live_peaks(dev)
+    fpeak = peaks["bf16_tflops_sustained"] if tc else live["fp32_tflops"]
     hbm = {"bound": "hbm", "achieved": bytes_step / prod_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "peak_source": f"hbm_gbs ({peak_src})",
            "work_per_launch": "algorithmic bytes: sum n_i^2 x the product's input, output and operand bytes per "
@@ -427,7 +518,7 @@ def run_batched(args, wl):
     alu = {"bound": "tensor" if tc else "alu", "achieved": flops_step / prod_s / 1e12, "peak": fpeak,
            "unit": "TFLOP/s",
            "peak_source": f"bf16_tflops_sustained ({peak_src})" if tc else
-                          "derived: 152 SM x 128 lanes x 2 flop x max SM clock",
+                          "FP32 FMA rate measured in this run (neumann_measure_fma_peak)",
            "work_per_launch": "3 x sum 2 n_i^3 BF16 tensor flops" if tc else "sum 2 n_i^3 FP32 flops"}
     t_hbm = bytes_step / (hbm["peak"] * 1e9)
     t_alu = flops_step / (alu["peak"] * 1e12)
@@ -463,7 +554,14 @@ def run_batched(args, wl):
         "roofline": roof,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_batched(wl, mats)
+        if not sub:
+            line["cpu_baseline"] = cpu_baseline_batched(wl, mats)
+        bp.launch()  # the outputs last held the per-matrix comparison's results
+        torch.cuda.synchronize()
+        line["vs_oracle"] = oracle_error_batched(wl, mats, outs)
+    if sub:
+        return line
+    line["peaks_measured_here"] = live_peaks(dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -488,9 +586,11 @@ def cpu_baseline_batched(wl, mats, budget_s=10.0):
             "sample": f"first {done} of {len(mats)} matrices (same order of draw), FP64 NumPy; {dt:.1f} s"}
 
 
-def run_ours(args, wl):
+def run_ours(args, wl, sub=False):
+    """One single-matrix workload. sub: a secondary workload of the default run
+    (one process, no FP64 comparison, no CPU timing): returns its line."""
     if wl.get("batched"):
-        return run_batched(args, wl)
+        return run_batched(args, wl, sub)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -500,7 +600,9 @@ def run_ours(args, wl):
     rank, world, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
+    if sub:
+        world = 1
+    elif world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
     def barrier():
@@ -562,7 +664,7 @@ def run_ours(args, wl):
     # 1/64 of the FP32 rate, so this takes seconds), and the split result's
     # relative Frobenius distance from it
     fp64 = None
-    if wl["dtype"] != "fp64" and not args.no_fp64 and (wl.get("fp64", True) or args.fp64_large):
+    if not sub and wl["dtype"] != "fp64" and not args.no_fp64 and (wl.get("fp64", True) or args.fp64_large):
         p64 = nm.Plan(n, k, wl["radix"], "fp64")
         A64 = A.double() if A.dtype != torch.float64 else A
         S64 = torch.empty_like(A64)
@@ -624,23 +726,27 @@ def run_ours(args, wl):
             flops = 3 * 2.0 * info["padded_n"] * 256 * 256 * (t * (t + 1) // 2)
             work = "3 x 2 x padded_n x 256^2 x (tiles on or above the diagonal) BF16 tensor flops"
         peak = peaks["bf16_tflops_sustained"]
+        peak_source = f"bf16_tflops_sustained ({peak_src})"
+        if wl["dtype"] == "split_fp16":  # FP16 operands: the BF16 figure x the measured cuBLAS FP16/BF16 ratio
+            r = live_peaks(dev)["fp16_over_bf16"]
+            peak *= r
+            peak_source += f" x {r:.3f} (cuBLAS FP16 / BF16 GEMM rate measured in this run)"
         sha = _src_sha("kernels_tc.cu", "epilogue.cuh")
         traffic = (TC_TRAFFIC["bytes_per_launch"]
                    if TC_TRAFFIC["sha1"] == sha and args.workload == TC_TRAFFIC["workload"] else None)
         roof = {"bound": "tensor", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": None, "traffic": traffic,
-                "kernel": "tc_split_gemm_kernel", "peak_source": f"bf16_tflops_sustained ({peak_src})",
+                "kernel": "tc_split_gemm_kernel", "peak_source": peak_source,
                 "work_per_launch": work, "launches_timed": len(prod_ms)}
     else:
         flops = 2.0 * n ** 3
-        # CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes (x 2 flop) at the
-        # maximum SM clock; FP64 at 1/64 of the FP32 rate
-        sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        fp32_peak = 152 * 128 * 2 * sm_hz / 1e12
-        peak = fp32_peak if wl["dtype"] == "fp32" else fp32_peak / 64
+        # CUDA-core FMA rate measured in this run (FP32 or FP64 chains on every SM)
+        live = live_peaks(dev)
+        peak = live["fp32_tflops"] if wl["dtype"] == "fp32" else live["fp64_tflops"]
         roof = {"bound": "alu", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "kernel": "simt_gemm_kernel",
-                "peak_source": "derived: 152 SM x 128 lanes x 2 flop x max SM clock (FP64: /64)",
+                "peak_source": f"{wl['dtype'].upper()} FMA rate measured in this run (neumann_measure_fma_peak, "
+                               f"{live['sms']} SMs)",
                 "work_per_launch": "2n^3 flops", "launches_timed": len(prod_ms)}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # mean device time of each product of an evaluation, in launch order
@@ -682,11 +788,58 @@ def run_ours(args, wl):
         "roofline": roof,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, A_np)
+        if not sub:
+            line["cpu_baseline"] = cpu_baseline(wl, A_np)
+        plan(A, out=S)  # S last held the squaring comparator's result
+        torch.cuda.synchronize()
+        line["vs_oracle"] = oracle_error(wl, inp, S.double().cpu().numpy())
+    if sub:
+        return line
+    line["peaks_measured_here"] = live_peaks(dev)
+    if world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_extras:
+        del plan, sq, A, S, A_host, S_host
+        torch.cuda.empty_cache()
+        line.update(run_extras(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# Secondary workloads of the default run, each timed like its own --workload run
+# over a shorter region (steps), reported as keys of the default line.
+EXTRAS = (("radix9", "precision-r9-bf16-n8192-k6561", 20), ("precise", "precise-r15-bf16-n8192-k3375", 16),
+          ("batched", "batched-r9-bf16-4096-k81", 48))
+
+
+def run_extras(args):
+    import copy
+
+    import torch
+
+    out = {}
+    for key, name, steps in EXTRAS:
+        sub_args = copy.copy(args)
+        sub_args.workload, sub_args.steps = name, steps
+        wl = WORKLOADS[name]
+        ln = run_ours(sub_args, wl, sub=True)
+        roof = ln["roofline"]
+        d = {"workload": name, "value": ln["value"], "unit": ln["unit"], "steps": steps,
+             "ms_per_step": ln["ms_per_step"], "e2e": ln["e2e"], "status": ln["status"],
+             "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")
+                          if k in roof},
+             "vs_oracle": ln.get("vs_oracle"), "clocks": ln["clocks"]}
+        if "other" in roof:
+            d["roofline"]["other"] = roof["other"]
+        if "vs_squaring" in ln:
+            vq = dict(ln["vs_squaring"])
+            vq["bar"] = 0.95 * vq["formula_ratio"]  # wall-time target: 0.95 x the product-count ratio
+            d["vs_squaring"] = vq
+        if "vs_per_matrix" in ln:
+            d["vs_per_matrix"] = ln["vs_per_matrix"]
+        out[key] = d
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -701,6 +854,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch configuration")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison evaluation")
     ap.add_argument("--fp64-large", action="store_true", help="run the FP64 comparison on the n = 16384 workload")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the secondary workloads (radix 9, precise, batched)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.steps is None:
