@@ -64,12 +64,13 @@ __device__ __forceinline__ T* dst_base(const EpiDst& ds, const EpiCtx& x, int64_
   return reinterpret_cast<T*>(ds.p);
 }
 
-// The 16-bit hi/lo pair of v as raw bits (BF16, or scaled FP16; see EpiSplit).
-// kF16 is a compile-time choice: a kernel instance serves one split type.
+// The 16-bit hi/lo pair of v as raw bits (BF16, or FP16 of v * sc with the
+// matrix's power of two sc; see EpiSplit). kF16 is a compile-time choice: a
+// kernel instance serves one split type.
 template <bool kF16>
-__device__ __forceinline__ void split_bits(float v, unsigned short* hi, unsigned short* lo) {
+__device__ __forceinline__ void split_bits(float v, float sc, unsigned short* hi, unsigned short* lo) {
   if (kF16) {
-    const float w = v * kFp16SplitScale;
+    const float w = v * sc;
     const __half h = __float2half_rn(w);
     *hi = __half_as_ushort(h);
     *lo = __half_as_ushort(__float2half_rn(w - __half2float(h)));
@@ -80,19 +81,35 @@ __device__ __forceinline__ void split_bits(float v, unsigned short* hi, unsigned
   }
 }
 
-// An FP16 hi that overflowed (|v| * 2^8 beyond the FP16 range) is non-finite.
+// An FP16 hi that overflowed (|v| * sc beyond the FP16 range) is non-finite.
 template <bool kF16>
-__device__ __forceinline__ bool split_bad(float v) {
-  return kF16 && !(fabsf(v) * kFp16SplitScale < 65504.f);
+__device__ __forceinline__ bool split_bad(float v, float sc) {
+  return kF16 && !(fabsf(v) * sc < 65504.f);
 }
 
 template <bool kF16>
-__device__ __forceinline__ void split_store(const EpiSplit& s, const EpiCtx& x, int r, int c, float v) {
+__device__ __forceinline__ void split_store(const EpiSplit& s, const EpiCtx& x, int r, int c, float v, float sc) {
   unsigned short hi, lo;
-  split_bits<kF16>(v, &hi, &lo);
+  split_bits<kF16>(v, sc, &hi, &lo);
   int64_t off = x.off + (s.transposed ? (int64_t)c * s.ld + r : (int64_t)r * s.ld + c);
   reinterpret_cast<unsigned short*>(s.hi)[off] = hi;
   reinterpret_cast<unsigned short*>(s.lo)[off] = lo;
+}
+
+// ---------------------------------------------------------------------------
+// Split-FP16 scaling (SxParams): the scales of one launch for matrix `mat`,
+// read once per tile.
+__device__ __forceinline__ void sx_tile(const EpiParams& P, int mat, SxTile* t) {
+  const SxParams& q = P.sx;
+  const int64_t m = mat;
+  t->acc = 1.f;
+  if (q.active && q.rec_a >= 0)
+    t->acc = ldexpf(1.f, -(q.exp[q.rec_a * (int64_t)q.nmat + m] + q.exp[q.rec_b * (int64_t)q.nmat + m]));
+#pragma unroll
+  for (int j = 0; j < kMaxOut; ++j) {
+    const int rec = (q.active && j < P.nout) ? q.rec_out[j] : -1;
+    t->sc[j] = rec >= 0 ? ldexpf(1.f, q.exp[rec * (int64_t)q.nmat + m]) : 1.f;
+  }
 }
 
 // Write 0 to every workspace destination of element (r, c) outside the n x n
@@ -128,9 +145,10 @@ __device__ __forceinline__ void epi_padding(const EpiParams& P, const EpiCtx& x,
 // kDeferT: outputs' transposed split stores are not written; the value they
 // would split (RN_fp32 of the output) is left in tv[j] for the caller to write
 // through a shared-memory transpose (0 in the padding).
+// t: split-FP16 scales and records of this tile (nullptr for other dtypes).
 template <typename AccT, bool kDeferT, bool kF16>
 __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCtx& x, int r, int c, AccT acc,
-                                                 float* tv) {
+                                                 float* tv, const SxTile* t) {
   bool bad = false;
   if (r >= x.n || c >= x.n) {
     if (kDeferT)
@@ -170,11 +188,11 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
       } else {
         // FP32 terms summed in FP32 (they carry FP32 rounding already); the FP64
         // inputs (a partial sum Y or residual R) are added in FP64, one DFMA each.
-        float t = o.acc_f * (float)acc;
+        float tt = (kF16 && t ? o.acc_f * t->acc : o.acc_f) * (float)acc;
 #pragma unroll
         for (int i = 0; i < kMaxIn; ++i)
-          if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) t = fmaf(o.in_f[i], fin[i], t);
-        v = (double)t + (diag ? o.id_d : 0.0);
+          if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) tt = fmaf(o.in_f[i], fin[i], tt);
+        v = (double)tt + (diag ? o.id_d : 0.0);
 #pragma unroll
         for (int i = 0; i < kMaxIn; ++i)
           if (i < P.nin && o.in_d[i] != 0.0 && P.in[i].dt == DT_F64) v = fma(o.in_d[i], din[i], v);
@@ -182,7 +200,7 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
       vf = (float)v;
       if (!isfinite(v)) bad = true;
     } else {
-      vf = o.acc_f * (float)acc + (diag ? o.id_f : 0.f);
+      vf = (kF16 && t ? o.acc_f * t->acc : o.acc_f) * (float)acc + (diag ? o.id_f : 0.f);
 #pragma unroll
       for (int i = 0; i < kMaxIn; ++i) {
         if (i < P.nin && o.in_f[i] != 0.f)
@@ -191,6 +209,7 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
       v = 0.0;  // unused: no FP64 destination is written from an FP32 output
       if (!isfinite(vf)) bad = true;
     }
+    const float sc = kF16 && t ? t->sc[j] : 1.f;
     for (int d = 0; d < o.ndst; ++d) {
       const EpiDst& ds = o.dst[d];
       int64_t ld;
@@ -201,11 +220,11 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
     }
     // hi/lo pairs are formed from RN_fp32 of the output: FP32 keeps 24 bits, the pair 16
     for (int s = 0; s < o.nsplit; ++s) {
-      bad |= split_bad<kF16>(vf);
+      bad |= split_bad<kF16>(vf, sc);
       if (kDeferT && o.split[s].transposed)
         tv[j] = vf;
       else
-        split_store<kF16>(o.split[s], x, r, c, vf);
+        split_store<kF16>(o.split[s], x, r, c, vf, sc);
     }
   }
   return bad;
@@ -214,8 +233,9 @@ __device__ __forceinline__ bool epi_element_impl(const EpiParams& P, const EpiCt
 // One copy serves every call site of the GEMM kernels; P is a __grid_constant__
 // kernel parameter, so passing it by reference copies nothing.
 template <typename AccT, bool kF16>
-__device__ __noinline__ bool epi_element(const EpiParams& P, EpiCtx x, int r, int c, AccT acc) {
-  return epi_element_impl<AccT, false, kF16>(P, x, r, c, acc, nullptr);
+__device__ __noinline__ bool epi_element(const EpiParams& P, EpiCtx x, int r, int c, AccT acc,
+                                         const SxTile* t = nullptr) {
+  return epi_element_impl<AccT, false, kF16>(P, x, r, c, acc, nullptr, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,8 +265,10 @@ __device__ __forceinline__ void ld_vec(const double* p, double (&v)[W]) {
 }
 
 // kWsOnly: write workspace destinations only (padding zeros never go to the caller).
+// sc: the output's split-FP16 scale.
 template <int W, typename V, bool kF16, bool kWsOnly = false>
-__device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, int c0, const V (&v)[W]) {
+__device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, int c0, const V (&v)[W],
+                                       float sc = 1.f) {
   for (int d = 0; d < o.ndst; ++d) {
     const EpiDst& ds = o.dst[d];
     int64_t ld;
@@ -276,7 +298,7 @@ __device__ __forceinline__ void st_row(const EpiOut& o, const EpiCtx& x, int r, 
     const EpiSplit& sp = o.split[s];
     unsigned short hi[W], lo[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) split_bits<kF16>((float)v[w], &hi[w], &lo[w]);  // from RN_fp32(v)
+    for (int w = 0; w < W; ++w) split_bits<kF16>((float)v[w], sc, &hi[w], &lo[w]);  // from RN_fp32(v)
     if (sp.transposed) {
 #pragma unroll
       for (int w = 0; w < W; ++w) {
@@ -319,11 +341,11 @@ __device__ __forceinline__ void epi_row_zero(const EpiParams& P, const EpiCtx& x
 
 // A scaled FP16 split of any of these values overflows.
 template <int W, typename V, bool kF16>
-__device__ __forceinline__ bool fp16_overflow(const EpiOut& o, const V (&v)[W]) {
+__device__ __forceinline__ bool fp16_overflow(const EpiOut& o, const V (&v)[W], float sc) {
   if (!kF16 || o.nsplit == 0) return false;
   bool bad = false;
 #pragma unroll
-  for (int w = 0; w < W; ++w) bad |= !(fabsf((float)v[w]) * kFp16SplitScale < 65504.f);
+  for (int w = 0; w < W; ++w) bad |= !(fabsf((float)v[w]) * sc < 65504.f);
   return bad;
 }
 
@@ -394,7 +416,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, double, kF16>(o, v);
+      bad |= fp16_overflow<W, double, kF16>(o, v, 1.f);
       st_row<W, double, kF16>(o, x, r, c0, v);
     } else {
       float v[W];
@@ -410,7 +432,7 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, float, kF16>(o, v);
+      bad |= fp16_overflow<W, float, kF16>(o, v, 1.f);
       st_row<W, float, kF16>(o, x, r, c0, v);
     }
   }
@@ -424,10 +446,11 @@ __device__ __forceinline__ bool epi_row(const EpiParams& P, const EpiCtx& x, int
 // W x 2-byte run per lane. Requires W == 8 (16-byte transposed runs).
 
 template <int W, bool kF16>
-__device__ __forceinline__ void st_col_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[W]) {
+__device__ __forceinline__ void st_col_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[W],
+                                             float sc) {
   unsigned short hi[W], lo[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) split_bits<kF16>(v[w], &hi[w], &lo[w]);
+  for (int w = 0; w < W; ++w) split_bits<kF16>(v[w], sc, &hi[w], &lo[w]);
   if (sp.transposed) {
     uint32_t ph[W / 2], pl[W / 2];
 #pragma unroll
@@ -450,7 +473,8 @@ __device__ __forceinline__ void st_col_split(const EpiSplit& sp, const EpiCtx& x
 
 // kWsOnly: padding, workspace destinations only
 template <int W, typename V, bool kF16, bool kWsOnly = false>
-__device__ __forceinline__ void st_col(const EpiOut& o, const EpiCtx& x, int r0, int c, const V (&v)[W]) {
+__device__ __forceinline__ void st_col(const EpiOut& o, const EpiCtx& x, int r0, int c, const V (&v)[W],
+                                       float sc = 1.f) {
   for (int d = 0; d < o.ndst; ++d) {
     const EpiDst& ds = o.dst[d];
     if (kWsOnly && ds.mode != EPI_WS) continue;
@@ -469,12 +493,13 @@ __device__ __forceinline__ void st_col(const EpiOut& o, const EpiCtx& x, int r0,
     float vf[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) vf[w] = (float)v[w];  // pairs from RN_fp32 of the output
-    for (int s = 0; s < o.nsplit; ++s) st_col_split<W, kF16>(o.split[s], x, r0, c, vf);
+    for (int s = 0; s < o.nsplit; ++s) st_col_split<W, kF16>(o.split[s], x, r0, c, vf, sc);
   }
 }
 
 template <int W, typename AccT, bool kF16>
-__device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int r0, int c, const AccT (&acc)[W]) {
+__device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int r0, int c, const AccT (&acc)[W],
+                                        const SxTile* t = nullptr) {
   static_assert(W == 8, "transposed runs are 16 bytes");
   static_assert(sizeof(AccT) == 4, "FP32 accumulators (tensor-core products)");
   if (c >= x.n || r0 >= x.n) {  // the whole run is padding
@@ -488,7 +513,7 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
   if (r0 + W > x.n) {  // ragged edge
     bool bad = false;
 #pragma unroll
-    for (int w = 0; w < W; ++w) bad |= epi_element<AccT, kF16>(P, x, r0 + w, c, acc[w]);
+    for (int w = 0; w < W; ++w) bad |= epi_element<AccT, kF16>(P, x, r0 + w, c, acc[w], t);
     return bad;
   }
   float fin[kMaxIn][W];
@@ -515,8 +540,9 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
     if (o.f64) {
       double v[W];
       float vf[W];
+      const float af = kF16 && t ? o.acc_f * t->acc : o.acc_f;
 #pragma unroll
-      for (int w = 0; w < W; ++w) vf[w] = o.acc_f * (float)acc[w];
+      for (int w = 0; w < W; ++w) vf[w] = af * (float)acc[w];
 #pragma unroll
       for (int i = 0; i < kMaxIn; ++i) {
         if (i < P.nin && o.in_f[i] != 0.f && P.in[i].dt != DT_F64) {
@@ -535,12 +561,14 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, double, kF16>(o, v);
-      st_col<W, double, kF16>(o, x, r0, c, v);
+      const float sc = kF16 && t ? t->sc[j] : 1.f;
+      bad |= fp16_overflow<W, double, kF16>(o, v, sc);
+      st_col<W, double, kF16>(o, x, r0, c, v, sc);
     } else {
       float v[W];
+      const float af = kF16 && t ? o.acc_f * t->acc : o.acc_f;
 #pragma unroll
-      for (int w = 0; w < W; ++w) v[w] = o.acc_f * (float)acc[w] + (r0 + w == c ? o.id_f : 0.f);
+      for (int w = 0; w < W; ++w) v[w] = af * (float)acc[w] + (r0 + w == c ? o.id_f : 0.f);
 #pragma unroll
       for (int i = 0; i < kMaxIn; ++i) {
         if (i < P.nin && o.in_f[i] != 0.f) {
@@ -551,8 +579,9 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
       }
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, float, kF16>(o, v);
-      st_col<W, float, kF16>(o, x, r0, c, v);
+      const float sc = kF16 && t ? t->sc[j] : 1.f;
+      bad |= fp16_overflow<W, float, kF16>(o, v, sc);
+      st_col<W, float, kF16>(o, x, r0, c, v, sc);
     }
   }
   return bad;
@@ -571,9 +600,9 @@ __device__ __forceinline__ bool epi_col(const EpiParams& P, const EpiCtx& x, int
 
 // hi/lo of (a, b) as packed pairs: low half from a, high half from b.
 template <bool kF16>
-__device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t* lo) {
+__device__ __forceinline__ void split2(float a, float b, float sc, uint32_t* hi, uint32_t* lo) {
   if (kF16) {
-    const float wa = a * kFp16SplitScale, wb = b * kFp16SplitScale;
+    const float wa = a * sc, wb = b * sc;
     const __half2 h = __floats2half2_rn(wa, wb);
     const float2 hf = __half22float2(h);
     const __half2 l = __floats2half2_rn(wa - hf.x, wb - hf.y);
@@ -590,10 +619,11 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t* hi, uint32_t*
 
 // Split stores of 8 consecutive rows r0 .. r0+7 of column c.
 template <bool kF16>
-__device__ __forceinline__ void st8_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[8]) {
+__device__ __forceinline__ void st8_split(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[8],
+                                          float sc) {
   uint32_t ph[4], pl[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], &ph[q], &pl[q]);
+  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], sc, &ph[q], &pl[q]);
   unsigned short* hi = reinterpret_cast<unsigned short*>(sp.hi) + x.off;
   unsigned short* lo = reinterpret_cast<unsigned short*>(sp.lo) + x.off;
   if (sp.transposed) {  // row c of the stored transpose, 8 consecutive entries: one 16-byte store each
@@ -658,10 +688,10 @@ __device__ __forceinline__ void st8_mirror_dst(const EpiOut& o, const EpiCtx& x,
 // splits): hi/lo of (c, r0 .. r0+7), one 16-byte store each.
 template <bool kF16>
 __device__ __forceinline__ void st8_split_mirror(const EpiSplit& sp, const EpiCtx& x, int r0, int c,
-                                                 const float (&v)[8]) {
+                                                 const float (&v)[8], float sc) {
   uint32_t ph[4], pl[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], &ph[q], &pl[q]);
+  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], sc, &ph[q], &pl[q]);
   const int64_t off = x.off + (int64_t)c * sp.ld + r0;
   *reinterpret_cast<uint4*>(reinterpret_cast<unsigned short*>(sp.hi) + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
   *reinterpret_cast<uint4*>(reinterpret_cast<unsigned short*>(sp.lo) + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
@@ -695,10 +725,11 @@ __device__ __forceinline__ void st8_dst_diag(const EpiOut& o, const EpiCtx& x, i
 }
 
 template <bool kF16>
-__device__ __forceinline__ void st8_split_diag(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[8]) {
+__device__ __forceinline__ void st8_split_diag(const EpiSplit& sp, const EpiCtx& x, int r0, int c, const float (&v)[8],
+                                               float sc) {
   uint32_t ph[4], pl[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], &ph[q], &pl[q]);
+  for (int q = 0; q < 4; ++q) split2<kF16>(v[2 * q], v[2 * q + 1], sc, &ph[q], &pl[q]);
   unsigned short* hi = reinterpret_cast<unsigned short*>(sp.hi) + x.off;
   unsigned short* lo = reinterpret_cast<unsigned short*>(sp.lo) + x.off;
   const int64_t ld = sp.ld;
@@ -717,14 +748,15 @@ __device__ __forceinline__ void st8_split_diag(const EpiSplit& sp, const EpiCtx&
   }
 }
 
+// Split-FP16 (kF16): t holds the tile's scales.
 template <bool kF16, int RB, int NF, bool kD>
 __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                               int lane, int sym, bool edge) {
+                                               int lane, int sym, bool edge, const SxTile* t) {
   static_assert(RB % 8 == 0 && 32 % RB == 0, "row batch");
   const int fi = P.f64_in;  // the FP64 input, or -1
   const int nf = P.nf32;    // FP32 inputs (<= NF)
   float chk = 0.f;          // becomes NaN once any output is non-finite
-  float amax = 0.f;         // largest |value| split to FP16
+  float ovf = 0.f;          // largest |value| * scale split to FP16
 #pragma unroll 1
   for (int g0 = 0; g0 < 32; g0 += RB) {
     float fin[NF > 0 ? NF : 1][RB];
@@ -761,9 +793,11 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
       for (int j = 0; j < P.nout; ++j) {
         const EpiOut& o = P.out[j];
         // the same terms in the same order as epi_col
+        const float af = kF16 ? o.acc_f * t->acc : o.acc_f;
+        const float sc = kF16 ? t->sc[j] : 1.f;
         float vf[8];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) vf[w] = o.acc_f * a8[w];
+        for (int w = 0; w < 8; ++w) vf[w] = af * a8[w];
         if (o.f64) {
           // FP32 terms summed in FP32; the identity and the FP64 input (a partial
           // sum Y or residual R) are added in FP64
@@ -884,32 +918,32 @@ __device__ __forceinline__ bool epi_chunk_lean(const EpiParams& P, const EpiCtx&
         }
 #pragma unroll
         for (int w = 0; w < 8; ++w) chk = fmaf(vf[w], 0.f, chk);
-        if (o.nsplit) {
-          if (kF16) {
+        if (kF16 && o.nsplit) {
+          float mx = 0.f;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) amax = fmaxf(amax, fabsf(vf[w]));
-          }
-          for (int s2 = 0; s2 < o.nsplit; ++s2) {
-            if (sym == 2) {
-              st8_split_diag<kF16>(o.split[s2], x, r0, c, vf);
-            } else {
-              st8_split<kF16>(o.split[s2], x, r0, c, vf);
-              if (sym == 1) st8_split_mirror<kF16>(o.split[s2], x, r0, c, vf);
-            }
+          for (int w = 0; w < 8; ++w) mx = fmaxf(mx, fabsf(vf[w]));
+          ovf = fmaxf(ovf, mx * sc);
+        }
+        for (int s2 = 0; s2 < o.nsplit; ++s2) {
+          if (sym == 2) {
+            st8_split_diag<kF16>(o.split[s2], x, r0, c, vf, sc);
+          } else {
+            st8_split<kF16>(o.split[s2], x, r0, c, vf, sc);
+            if (sym == 1) st8_split_mirror<kF16>(o.split[s2], x, r0, c, vf, sc);
           }
         }
       }
     }
   }
-  return chk != chk || (kF16 && !(amax * kFp16SplitScale < 65504.f));
+  return chk != chk || !(ovf < 65504.f);
 }
 
 template <bool kF16>
 __device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                               int lane, int sym, bool edge) {
-  if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane, sym, edge);
-  if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane, sym, edge);
-  return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane, sym, edge);
+                                               int lane, int sym, bool edge, const SxTile* t) {
+  if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane, sym, edge, t);
+  if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane, sym, edge, t);
+  return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane, sym, edge, t);
 }
 
 // Boundary chunks (padding, ragged edges, grouped row limits) and ops with
@@ -917,7 +951,7 @@ __device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx&
 // its registers then do not count against the lean path's.
 template <bool kF16>
 __device__ __noinline__ bool epi_chunk_generic(const EpiParams& P, EpiCtx x, int rbase, int c, const float* stg,
-                                               int lane, int lim, bool mirror) {
+                                               int lane, int lim, bool mirror, const SxTile* t) {
   bool bad = false;
 #pragma unroll 1
   for (int g = 0; g < 4; ++g) {
@@ -926,10 +960,10 @@ __device__ __noinline__ bool epi_chunk_generic(const EpiParams& P, EpiCtx x, int
     float a8[8];
 #pragma unroll
     for (int w = 0; w < 8; ++w) a8[w] = stg[(8 * g + w) * 33 + lane];
-    bad |= epi_col<8, float, kF16>(P, x, r0, c, a8);
+    bad |= epi_col<8, float, kF16>(P, x, r0, c, a8, t);
     if (mirror) {  // the transposed element of a symmetric result, one at a time
 #pragma unroll 1
-      for (int w = 0; w < 8; ++w) bad |= epi_element<float, kF16>(P, x, c, r0 + w, a8[w]);
+      for (int w = 0; w < 8; ++w) bad |= epi_element<float, kF16>(P, x, c, r0 + w, a8[w], t);
     }
   }
   return bad;
@@ -942,30 +976,73 @@ __device__ __noinline__ bool epi_chunk_generic(const EpiParams& P, EpiCtx x, int
 // too, so that the result is exactly symmetric.
 template <bool kF16>
 __device__ __noinline__ bool epi_chunk_diag(const EpiParams& P, EpiCtx x, int rbase, int c, const float* stg,
-                                            int lane) {
+                                            int lane, const SxTile* t) {
   bool bad = false;
 #pragma unroll 1
   for (int i = 0; i < 32; ++i) {
     const int r = rbase + i;
     const float a = stg[i * 33 + lane];
-    if (r <= c) bad |= epi_element<float, kF16>(P, x, r, c, a);
-    if (r < c) bad |= epi_element<float, kF16>(P, x, c, r, a);
+    if (r <= c) bad |= epi_element<float, kF16>(P, x, r, c, a, t);
+    if (r < c) bad |= epi_element<float, kF16>(P, x, c, r, a, t);
   }
   return bad;
 }
 
 // Symmetric products: sym = 0 for a chunk of a general product, 1 for a chunk
 // above the diagonal (also writes its transpose), 2 for a chunk on it.
+// Split-FP16 (kF16): t as in epi_chunk_lean (nullptr otherwise).
 template <bool kF16>
 __device__ __forceinline__ bool epi_chunk(const EpiParams& P, const EpiCtx& x, int rbase, int c, const float* stg,
-                                          int lane, int lim, int sym = 0) {
+                                          int lane, int lim, int sym, const SxTile* t) {
   if (P.fast && rbase + 32 <= lim) {
     // boundary chunk: part of it lies outside the n x n block (warp-uniform)
     const bool edge = !__all_sync(0xffffffffu, c < x.n && rbase + 32 <= x.n);
-    if (!edge || (sym == 0 && P.edge_ok)) return epi_chunk_fast<kF16>(P, x, rbase, c, stg, lane, sym, edge);
+    if (!edge || (sym == 0 && P.edge_ok)) return epi_chunk_fast<kF16>(P, x, rbase, c, stg, lane, sym, edge, t);
   }
-  if (sym == 2) return epi_chunk_diag<kF16>(P, x, rbase, c, stg, lane);
-  return epi_chunk_generic<kF16>(P, x, rbase, c, stg, lane, lim, sym == 1);
+  if (sym == 2) return epi_chunk_diag<kF16>(P, x, rbase, c, stg, lane, t);
+  return epi_chunk_generic<kF16>(P, x, rbase, c, stg, lane, lim, sym == 1, t);
+}
+
+// Split-FP16 statistics of a product's accumulator (its true value is the
+// staged value times t.acc), measured once per staged 32 x 32 chunk whatever
+// the number of outputs: this lane's column sum of |acc| over the chunk's rows
+// below `lim` (lane = column c; a grouped tile's rows past its matrix's padded
+// order hold values no consumer reads), added to the product's column sums;
+// and, for a symmetric product, the sums of the mirrored elements, added to
+// the columns they land in (lane = row rbase + lane of the chunk: its elements
+// right of the diagonal). The row maxima are taken where the chunk is staged
+// (sx_row_max).
+__device__ __forceinline__ void sx_chunk_colsum(const EpiParams& P, int mat, const float* stg, int lane, int rbase,
+                                                int cbase, int sym, int lim, float tacc) {
+  float* col = P.sx.acc_col + (int64_t)mat * P.sx.npad;
+  const int c = cbase + lane;
+  float cs = 0.f;
+#pragma unroll 8
+  for (int i = 0; i < 32; ++i)
+    cs += (rbase + i < lim && (sym != 2 || rbase + i <= c)) ? fabsf(stg[i * 33 + lane]) : 0.f;
+  if (cs > 0.f) atomicAdd(col + c, cs * tacc);
+  if (sym) {
+    const int r = rbase + lane;
+    float rs = 0.f;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) rs += (sym == 1 || cbase + l > r) ? fabsf(stg[lane * 33 + l]) : 0.f;
+    if (rs > 0.f) atomicAdd(col + r, rs * tacc);
+  }
+}
+
+// max |x| of the 32 staged values of this lane's row
+__device__ __forceinline__ float sx_row_max(const uint32_t (&v)[32]) {
+  float m = 0.f;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) m = fmaxf(m, fabsf(__uint_as_float(v[j])));
+  return m;
+}
+
+// End of a tile: the warp's max |acc| into the product's record for matrix mat.
+__device__ __forceinline__ void sx_tile_max(const EpiParams& P, int mat, float am, float tacc) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+  if ((threadIdx.x & 31) == 0 && am > 0.f) atomicMax(P.sx.acc_amax + mat, __float_as_uint(am * tacc));
 }
 
 __device__ __forceinline__ void epi_flag(const EpiParams& P, bool bad) {

@@ -104,17 +104,19 @@ struct EpiSplit {
 // maps to at most 2^14: hi never overflows FP16 (65504) and lo stays a normal
 // FP16 number down to |x| ~ 2^-17 of the bound. A product of operands stored
 // with e_A and e_B carries 2^(e_A + e_B), removed exactly in its epilogue.
-// The bound of an output comes from "records" of what earlier launches wrote:
-//   amax    max |x| (IEEE bits; a product's epilogue measures it with atomicMax,
-//           an element-wise pass stores its bound)
-//   colmax  max_j sum_i |x_ij|, the largest column sum (from `col`, the column
-//           sums a product's epilogue accumulates, or an element-wise bound)
-//   exp     the e its split was stored with
-// For out = a (L R) + sum_i c_i in_i + d I:
-//   |out_ij| <= |a| amax(L) colmax(R) + sum_i |c_i| amax(in_i) + |d|
-// (|(L R)_ij| <= max|L| sum_k |R_kj|). fp16_scale_kernel evaluates this before
-// each launch; the input stats kernel measures the caller's matrices.
-constexpr float kFp16SplitScale = 256.0f;  // 2^8 (fixed scale, being replaced)
+// Bounds come from per-matrix "records": every op output, the caller's
+// matrices and every product's accumulator have
+//   amax    a bound on max |x| (IEEE bits)
+//   colmax  a bound on max_j sum_i |x_ij|, the largest column sum
+//   exp     the e of the output's split
+// A product's epilogue measures its accumulator (max |acc| with atomicMax,
+// the column sums of |acc| into `col`), once per staged chunk; the caller's
+// matrices are measured by a pre-pass. For out = a acc + sum_i c_i in_i + d I,
+//   |out| <= |a| amax(acc) + sum_i |c_i| amax(in_i) + |d|, and the same with colmax,
+// and before the product, amax(acc) <= amax(L) colmax(R) (|(L R)_ij| <= max|L|
+// sum_k |R_kj|). fp16_scale_kernel, launched before each op, turns the
+// previous op's measured accumulator into its outputs' records and the bounds
+// into this op's exponents.
 constexpr int kSxTarget = 14;  // the bound is mapped to at most 2^14
 constexpr int kSxMaxExp = 60;  // |e| <= 60 keeps every scale a normal FP32 power of two
 
@@ -122,22 +124,41 @@ struct SxParams {
   int active;        // split-FP16 plan: the fields below are valid
   int nmat;          // matrices per record (1, or the matrices of a grouped pass)
   int npad;          // padded order (column-sum arrays hold npad entries per matrix)
-  unsigned* amax;    // [rec * nmat + m], float bits
-  float* colmax;     // [rec * nmat + m]
   int* exp;          // [rec * nmat + m]
-  float* col;        // column sums: record r at col + col_off[r] (+ m * npad)
-  const int64_t* col_off;  // device [rec]: offset of the record's column sums, -1 if it has none
   int rec_a, rec_b;  // records of a product's operands (-1: element-wise pass)
-  int rec_out[kMaxOut];     // record of each output (-1: the caller's S, no record)
-  int64_t col_out[kMaxOut]; // offset of the output's column sums (-1: none accumulated)
+  int rec_out[kMaxOut];  // record of each output (-1: the caller's S)
+  unsigned* acc_amax;    // a product's accumulator record: max |acc| per matrix (float bits)
+  float* acc_col;        // and its column sums, npad per matrix
+};
+
+// The scale step before op k: finalise op k-1's output records from its
+// measured accumulator (prev_*), then choose op k's exponents (and, for an
+// element-wise pass, record its outputs' bounds). One block per matrix.
+struct SxScaleOp {
+  int nmat, npad;
+  unsigned* amax;     // [rec * nmat + m]
+  float* colmax;
+  int* exp;
+  float* col;         // column-sum arrays (offsets in floats below)
+  // op k
+  int rec_a, rec_b;   // product operands (-1: element-wise pass)
+  int nin, nout;
+  int rec_in[kMaxIn];
+  int rec_out[kMaxOut];   // -1: the caller's S
+  float acc[kMaxOut], id[kMaxOut], in[kMaxOut][kMaxIn];
+  // op k-1, a product whose outputs' records are finalised here (prev_acc < 0: none)
+  int prev_acc;          // its accumulator record
+  int64_t prev_col;      // offset of its column sums
+  int prev_nin, prev_nout;
+  int prev_in[kMaxIn];
+  int prev_out[kMaxOut];
+  float prev_a[kMaxOut], prev_id[kMaxOut], prev_c[kMaxOut][kMaxIn];
 };
 
 // One launch's FP16 scales for one matrix, read at tile start.
 struct SxTile {
   float acc;            // 2^-(e_A + e_B): the accumulator in true units
   float sc[kMaxOut];    // 2^e of each output's split
-  unsigned* amax[kMaxOut];  // where each output's max |x| is recorded (nullptr: not)
-  float* col[kMaxOut];      // its column sums for this matrix (nullptr: not)
 };
 
 // out = acc_coef * acc + sum_i in_coef[i] * in[i] + id_coef * [r == c]
@@ -223,6 +244,13 @@ cudaError_t launch_simt_gemm_f32(const float* A, const float* B, int64_t ld, int
 // Element-wise epilogue with acc = 0: over the npad x npad elements, or (grouped)
 // over ntiles 32 x 32 tiles {matrix, tile row, tile column}.
 cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles = nullptr, int ntiles = 0);
+// Split-FP16 scaling: the scale step of one op, one block for each of the
+// pass's `count` matrices; and the max |x| and largest column sum of a caller's
+// matrix `in` (n x n, or per matrix of a grouped pass through mat_n, n the
+// largest order) into amax[m] and colmax[m] (float bits; must start at 0).
+cudaError_t launch_sx_scale(const SxScaleOp& op, int count, cudaStream_t s);
+cudaError_t launch_sx_input_stats(const EpiIn& in, const int* mat_n, int n, int nmat, unsigned* amax,
+                                  unsigned* colmax, cudaStream_t s);
 
 // ---- launchers (kernels_tc.cu) ----
 // Encode the four tensor maps over padded_n x padded_n BF16 arrays with leading

@@ -209,12 +209,14 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
     tc = t.z;
   }
   const EpiCtx x = epi_ctx(P, mat);
+  SxTile sxt;  // split-FP16 scales of this matrix
+  if (kF16) sx_tile(P, mat, &sxt);
   const int r0 = tr * 32, c0 = tc * 32;
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float tv[kMaxOut];
-    bad |= epi_element_impl<float, true, kF16>(P, x, r0 + ty + 8 * q, c0 + tx, 0.f, tv);
+    bad |= epi_element_impl<float, true, kF16>(P, x, r0 + ty + 8 * q, c0 + tx, 0.f, tv, kF16 ? &sxt : nullptr);
 #pragma unroll
     for (int j = 0; j < kMaxOut; ++j) tile[j][ty + 8 * q][tx] = tv[j];
   }
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(256) ewise_kernel(const int4* __restrict__ til
         // lane tx writes element (r0 + tx, c0 + ty + 8q) at row c, column r of the stored transpose
         const float v = tile[j][tx][ty + 8 * q];
         unsigned short hi, lo;
-        split_bits<kF16>(v, &hi, &lo);
+        split_bits<kF16>(v, kF16 ? sxt.sc[j] : 1.f, &hi, &lo);
         const int64_t off = x.off + (int64_t)(c0 + ty + 8 * q) * sp.ld + (r0 + tx);
         reinterpret_cast<unsigned short*>(sp.hi)[off] = hi;
         reinterpret_cast<unsigned short*>(sp.lo)[off] = lo;
@@ -286,9 +288,10 @@ __device__ __forceinline__ void ew_load(const EpiParams& P, const EpiCtx& x, int
   }
 }
 
+// t: split-FP16 scales of the matrix (nullptr for other dtypes)
 template <int NI, bool kIn64, bool kF16>
 __device__ __forceinline__ bool ew_emit(const EpiParams& P, const EpiCtx& x, int r, int c0,
-                                        const EwIn<NI, kIn64>& in) {
+                                        const EwIn<NI, kIn64>& in, const SxTile* t) {
   constexpr int W = 4;
   if (r >= x.n) {
     epi_row_zero<W, kF16>(P, x, r, c0);
@@ -297,7 +300,7 @@ __device__ __forceinline__ bool ew_emit(const EpiParams& P, const EpiCtx& x, int
   if (c0 + W > x.n) {
     bool bad = false;
 #pragma unroll
-    for (int w = 0; w < W; ++w) bad |= epi_element<float, kF16>(P, x, r, c0 + w, 0.f);
+    for (int w = 0; w < W; ++w) bad |= epi_element<float, kF16>(P, x, r, c0 + w, 0.f, t);
     return bad;
   }
   bool bad = false;
@@ -350,8 +353,9 @@ __device__ __forceinline__ bool ew_emit(const EpiParams& P, const EpiCtx& x, int
       // finite: exponent field not all ones (integer test, no FP64 instruction)
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= (__double2hiint(v[w]) & 0x7ff00000) == 0x7ff00000;
-      bad |= fp16_overflow<W, double, kF16>(o, v);
-      st_row<W, double, kF16>(o, x, r, c0, v);
+      const float sc = kF16 && t ? t->sc[j] : 1.f;
+      bad |= fp16_overflow<W, double, kF16>(o, v, sc);
+      st_row<W, double, kF16>(o, x, r, c0, v, sc);
     } else {
       float v[W];
 #pragma unroll
@@ -363,8 +367,9 @@ __device__ __forceinline__ bool ew_emit(const EpiParams& P, const EpiCtx& x, int
           for (int w = 0; w < W; ++w) v[w] = fmaf(o.in_f[i], (float)in[i][w], v[w]);
 #pragma unroll
       for (int w = 0; w < W; ++w) bad |= !isfinite(v[w]);
-      bad |= fp16_overflow<W, float, kF16>(o, v);
-      st_row<W, float, kF16>(o, x, r, c0, v);
+      const float sc = kF16 && t ? t->sc[j] : 1.f;
+      bad |= fp16_overflow<W, float, kF16>(o, v, sc);
+      st_row<W, float, kF16>(o, x, r, c0, v, sc);
     }
   }
   return bad;
@@ -402,8 +407,13 @@ __global__ void __launch_bounds__(256, NI <= 2 ? 3 : 2) ewise_vec_kernel(const i
     EwIn<NI, kIn64> a, b;
     ew_load<NI, kIn64>(P, xa, ra * 32 + dr, ca * 32 + dc, a);
     if (two) ew_load<NI, kIn64>(P, xb, rb * 32 + dr, cb * 32 + dc, b);
-    bad |= ew_emit<NI, kIn64, kF16>(P, xa, ra * 32 + dr, ca * 32 + dc, a);
-    if (two) bad |= ew_emit<NI, kIn64, kF16>(P, xb, rb * 32 + dr, cb * 32 + dc, b);
+    SxTile sa, sb;  // split-FP16 scales of the two tiles' matrices
+    if (kF16) {
+      sx_tile(P, ma, &sa);
+      if (two) sx_tile(P, mb, &sb);
+    }
+    bad |= ew_emit<NI, kIn64, kF16>(P, xa, ra * 32 + dr, ca * 32 + dc, a, kF16 ? &sa : nullptr);
+    if (two) bad |= ew_emit<NI, kIn64, kF16>(P, xb, rb * 32 + dr, cb * 32 + dc, b, kF16 ? &sb : nullptr);
   }
   epi_flag(P, bad);
 }
@@ -529,6 +539,122 @@ cudaError_t measure_fma_peak(int f64, double* tflops, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// ---- split-FP16 scaling (see SxParams) ----
+
+// Largest column sum of a measured matrix m (column sums at col + off, npad
+// per matrix): a reduction over the block. Every thread of the block calls it.
+__device__ float sx_block_colmax(const SxScaleOp& q, int64_t off, int m, float* red) {
+  const float* c = q.col + off + (int64_t)m * q.npad;
+  float v = 0.f;
+  for (int j = threadIdx.x; j < q.npad; j += blockDim.x) v = fmaxf(v, c[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+  return r;
+}
+
+// e with bound * 2^e <= 2^kSxTarget (0 for a zero or non-finite bound)
+__device__ int sx_exponent(double bound) {
+  if (!(bound > 0.0) || !isfinite(bound)) return 0;
+  int k = 0;
+  frexp(bound, &k);  // bound = f 2^k, 0.5 <= f < 1, so bound < 2^k
+  const int e = kSxTarget - k;
+  return e < -kSxMaxExp ? -kSxMaxExp : e > kSxMaxExp ? kSxMaxExp : e;
+}
+
+// a bound stored a hair above its computed value, so that its own rounding
+// cannot make it smaller than the quantity it bounds
+__device__ __forceinline__ float sx_up(double v) { return (float)v * (1.f + 1e-6f); }
+
+__global__ void __launch_bounds__(256) sx_scale_kernel(const __grid_constant__ SxScaleOp q) {
+  __shared__ float red[8];
+  const int m = blockIdx.x;
+  const int64_t nm = q.nmat;
+  const float prev_colmax = q.prev_acc >= 0 ? sx_block_colmax(q, q.prev_col, m, red) : 0.f;
+  if (threadIdx.x != 0) return;
+  auto amax = [&](int rec) { return (double)__uint_as_float(q.amax[rec * nm + m]); };
+  auto colmax = [&](int rec) { return (double)q.colmax[rec * nm + m]; };
+  // op k-1's outputs from its measured accumulator
+  if (q.prev_acc >= 0) {
+    const double am = amax(q.prev_acc), cm = prev_colmax;
+    for (int j = 0; j < q.prev_nout; ++j) {
+      const int rec = q.prev_out[j];
+      if (rec < 0) continue;
+      double a = fabs((double)q.prev_a[j]) * am + fabs((double)q.prev_id[j]);
+      double c = fabs((double)q.prev_a[j]) * cm + fabs((double)q.prev_id[j]);
+      for (int i = 0; i < q.prev_nin; ++i) {
+        a += fabs((double)q.prev_c[j][i]) * amax(q.prev_in[i]);
+        c += fabs((double)q.prev_c[j][i]) * colmax(q.prev_in[i]);
+      }
+      q.amax[rec * nm + m] = __float_as_uint(sx_up(a));
+      q.colmax[rec * nm + m] = sx_up(c);
+    }
+  }
+  // op k's exponents, from the a priori bound on its accumulator
+  const double acc = q.rec_a >= 0 ? amax(q.rec_a) * colmax(q.rec_b) : 0.0;
+  for (int j = 0; j < q.nout; ++j) {
+    const int rec = q.rec_out[j];
+    if (rec < 0) continue;
+    double a = fabs((double)q.acc[j]) * acc + fabs((double)q.id[j]);
+    double c = fabs((double)q.id[j]);
+    for (int i = 0; i < q.nin; ++i) {
+      a += fabs((double)q.in[j][i]) * amax(q.rec_in[i]);
+      c += fabs((double)q.in[j][i]) * colmax(q.rec_in[i]);
+    }
+    q.exp[rec * nm + m] = sx_exponent(a);
+    if (q.rec_a < 0) {  // an element-wise pass: its bounds are its records
+      q.amax[rec * nm + m] = __float_as_uint(sx_up(a));
+      q.colmax[rec * nm + m] = sx_up(c);
+    }
+  }
+}
+
+// A caller's matrix: max |x| and the largest column sum, into amax[m] and
+// colmax[m] (float bits, atomicMax). Block (panel of 32 columns, matrix m),
+// 32 columns x 8 row lanes; each block sums its columns over all rows.
+template <typename T>
+__global__ void __launch_bounds__(256) sx_input_stats_kernel(const __grid_constant__ EpiIn in, const int* mat_n,
+                                                              int n, unsigned* amax, unsigned* colmax) {
+  __shared__ float ps[8][33];
+  __shared__ float pm[8];
+  const int m = blockIdx.y;
+  const EpiCtx x = {mat_n ? mat_n[m] : n, m, 0};
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  float sum = 0.f, mx = 0.f;
+  if (c < x.n) {
+    int64_t ld;
+    const T* a = in_base<T>(in, x, &ld);
+    for (int r = threadIdx.y; r < x.n; r += 8) {
+      const float v = fabsf((float)a[(int64_t)r * ld + c]);
+      sum += v;
+      mx = fmaxf(mx, v);
+    }
+  }
+  ps[threadIdx.y][threadIdx.x] = sum;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x == 0) pm[threadIdx.y] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) t += ps[y][threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) {
+      float b = 0.f;
+#pragma unroll
+      for (int y = 0; y < 8; ++y) b = fmaxf(b, pm[y]);
+      if (b > 0.f) atomicMax(amax + m, __float_as_uint(b));
+      if (t > 0.f) atomicMax(colmax + m, __float_as_uint(t));
+    }
+  }
+}
+
 int sm_count() {
   static std::atomic<int> cache[kMaxDevices];
   const int n = per_device_value(cache, [] {
@@ -541,6 +667,23 @@ int sm_count() {
     return v;
   });
   return n > 0 ? n : 1;
+}
+
+cudaError_t launch_sx_scale(const SxScaleOp& op, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  sx_scale_kernel<<<count, 256, 0, s>>>(op);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sx_input_stats(const EpiIn& in, const int* mat_n, int n, int nmat, unsigned* amax,
+                                  unsigned* colmax, cudaStream_t s) {
+  if (nmat <= 0 || n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((n + 31) / 32), (unsigned)nmat);
+  if (in.dt == DT_F64)
+    sx_input_stats_kernel<double><<<grid, dim3(32, 8), 0, s>>>(in, mat_n, n, amax, colmax);
+  else
+    sx_input_stats_kernel<float><<<grid, dim3(32, 8), 0, s>>>(in, mat_n, n, amax, colmax);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ewise(const EpiParams& P, cudaStream_t s, const int4* tiles, int ntiles) {

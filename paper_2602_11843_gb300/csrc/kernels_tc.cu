@@ -478,6 +478,8 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
     float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - S::kEpiFirst) * STG_FLOATS;
     bool bad = false;
     int it = 0;
+    SxTile sxt;        // split-FP16: the tile's scales
+    float am = 0.f;    // split-FP16: max |acc| (staged units) of this lane's rows of the tile
     for (int tile = first; tile < ntiles; tile += stride, ++it) {
       const uint32_t buf = it & 1;
       const uint32_t use = (uint32_t)it >> 1;
@@ -490,6 +492,7 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
       int mat, tm, tn, nk;
       tile_of<kGrouped>(tile, tiles, ktiles, tiles_m, tiles_n, group, &mat, &tm, &tn, &nk, sym);
       const EpiCtx x = epi_ctx(P, mat);
+      if constexpr (kF16) sx_tile(P, mat, &sxt);
       const int rbase = tm * S::kTileM + (int)rank * BM + q * 32;
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(q * 32) << 16);
       // A grouped tile writes rows and columns below its matrix's order rounded
@@ -509,9 +512,18 @@ __global__ void __launch_bounds__(EpiShape<kGrouped, kPair>::kThreads, 1)
         tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
+        if constexpr (kF16) {
+          if (rbase + lane < lim) am = fmaxf(am, sx_row_max(v));
+        }
         __syncwarp();
-        bad |= epi_chunk<kF16>(P, x, rbase, tn * BN + chunk * 32 + lane, stg, lane, lim, symc);
+        if constexpr (kF16) sx_chunk_colsum(P, mat, stg, lane, rbase, tn * BN + chunk * 32, symc, lim, sxt.acc);
+        bad |= epi_chunk<kF16>(P, x, rbase, tn * BN + chunk * 32 + lane, stg, lane, lim, symc,
+                               kF16 ? &sxt : nullptr);
         __syncwarp();
+      }
+      if constexpr (kF16) {
+        sx_tile_max(P, mat, am, sxt.acc);
+        am = 0.f;
       }
       tc_fence_before();
       __syncwarp();
@@ -741,6 +753,9 @@ __global__ void __launch_bounds__(PQ_THREADS, 1)
     float* stg = reinterpret_cast<float*>(smem + PQ_STAGES * PQ_STAGE + 256) + (warp - 8) * STG_FLOATS;
     bool bad = false;
     int it = 0;
+    SxTile sxt;
+    float am = 0.f;
+    if constexpr (kF16) sx_tile(P, 0, &sxt);
     for (int tile = first; tile < ntiles; tile += stride, ++it) {
       const uint32_t sb = it & 1;
       const uint32_t su = (uint32_t)it >> 1;
@@ -762,9 +777,16 @@ __global__ void __launch_bounds__(PQ_THREADS, 1)
         tmem_ld32(taddr + (uint32_t)(chunk * 32), v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = __uint_as_float(v[i]);
+        if constexpr (kF16) am = fmaxf(am, sx_row_max(v));
         __syncwarp();
-        bad |= epi_chunk<kF16>(P, x, rbase, tn * PQ_N + chunk * 32 + lane, stg, lane, 1 << 30);
+        if constexpr (kF16) sx_chunk_colsum(P, 0, stg, lane, rbase, tn * PQ_N + chunk * 32, 0, 1 << 30, sxt.acc);
+        bad |= epi_chunk<kF16>(P, x, rbase, tn * PQ_N + chunk * 32 + lane, stg, lane, 1 << 30, 0,
+                               kF16 ? &sxt : nullptr);
         __syncwarp();
+      }
+      if constexpr (kF16) {
+        sx_tile_max(P, 0, am, sxt.acc);
+        am = 0.f;
       }
       tc_fence_before();
       __syncwarp();

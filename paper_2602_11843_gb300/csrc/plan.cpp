@@ -187,6 +187,21 @@ struct neumann_plan_s {
   // tensor-core products read B MN-major from its row-major hi/lo pair, so no
   // transposed pair is ever stored
   bool bmn = false;
+  // Split-FP16 per-matrix scaling (SxParams): every output of every op and
+  // every product's accumulator is a record; records 0 and 1 are the caller's
+  // A and B (measured by a pre-pass). op_sx / mm_sx give each op's operand,
+  // input, output and accumulator records. The stats region
+  // [amax | colmax | exp | column sums of the accumulators] is cleared before each pass.
+  struct OpSx {
+    int rec_a, rec_b, rec_acc;
+    int rec_in[kMaxIn];
+    int rec_out[kMaxOut];
+  };
+  bool sx = false;
+  int sx_nrec = 0, sx_nmat = 1;
+  std::vector<OpSx> op_sx, mm_sx;
+  std::vector<int64_t> sx_col;    // per record: offset (floats) of its column sums (accumulators), or -1
+  size_t off_sx = 0, sx_bytes = 0, off_sx_amax = 0, off_sx_colmax = 0, off_sx_exp = 0, off_sx_col = 0;
   int tune_pair = -1;                    // -1: CTA pairs from padded order 4096; 0 never; 1 always
   int tune_group = kDefaultRasterGroup;  // row tiles per raster group of a single product
   int chunk_run = 0;                     // grouped batches: matrices per pass (0: chunk)
@@ -210,6 +225,7 @@ struct neumann_plan_s {
   const void* cur_stab = nullptr;
   const int4 *cur_tc = nullptr, *cur_simt = nullptr, *cur_ew = nullptr;
   int n_tc = 0, n_simt = 0, n_ew = 0;
+  int cur_count = 0;  // matrices in the pass being launched
   // pinned host image of the tables, the call it was built for, and the event
   // after its upload (the image is rewritten only once that copy is done)
   char* h_tab = nullptr;
@@ -620,6 +636,53 @@ struct Sched {
   }
 };
 
+// ---------------------------------------------------------------- split-FP16 records
+
+// Records of one op list: operands and inputs take the record of the op that
+// last wrote their slot; every output of a workspace slot starts a new record.
+bool assign_records(const std::vector<Op>& ops, int* next, std::vector<neumann_plan_s::OpSx>* out) {
+  std::vector<int> cur(SL_N, -1);
+  auto rec_of = [&](int slot) { return slot == SL_USER_A ? 0 : slot == SL_USER_B ? 1 : slot >= 0 ? cur[slot] : -1; };
+  out->clear();
+  for (const Op& op : ops) {
+    neumann_plan_s::OpSx r;
+    memset(&r, 0xff, sizeof(r));  // -1 everywhere
+    if (op.kind == OP_GEMM) {
+      r.rec_a = rec_of(op.a);
+      r.rec_b = rec_of(op.b);
+      if (r.rec_a < 0 || r.rec_b < 0) return false;
+    }
+    for (int i = 0; i < op.nin; ++i) {
+      r.rec_in[i] = rec_of(op.in[i].slot);
+      if (r.rec_in[i] < 0) return false;
+    }
+    for (int j = 0; j < op.nout; ++j) r.rec_out[j] = op.out[j].slot >= 0 ? (*next)++ : -1;
+    if (op.kind == OP_GEMM) r.rec_acc = (*next)++;
+    for (int j = 0; j < op.nout; ++j)
+      if (op.out[j].slot >= 0) cur[op.out[j].slot] = r.rec_out[j];
+    out->push_back(r);
+  }
+  return true;
+}
+
+bool build_records(neumann_plan_s* p) {
+  p->sx = p->dtype == NEUMANN_SPLIT_FP16;
+  if (!p->sx) return true;
+  int next = 2;
+  if (!assign_records(p->ops, &next, &p->op_sx) || !assign_records(p->mm_ops, &next, &p->mm_sx)) return false;
+  p->sx_nrec = next;
+  p->sx_nmat = p->grouped ? p->chunk : 1;
+  p->sx_col.assign(next, -1);
+  int64_t off = 0;  // accumulators keep column sums, npad per matrix
+  for (const auto* v : {&p->op_sx, &p->mm_sx})
+    for (const neumann_plan_s::OpSx& r : *v)
+      if (r.rec_acc >= 0) {
+        p->sx_col[r.rec_acc] = off;
+        off += (int64_t)p->sx_nmat * p->npad;
+      }
+  return true;
+}
+
 // ---------------------------------------------------------------- layout
 
 // sym: every matrix of the scheme is symmetric, so a product's right operand
@@ -661,6 +724,18 @@ void layout(neumann_plan_s* p) {
     const int t = (int)(p->npad / 256);
     p->nsym = t * (t + 1) / 2;
     p->off_sym = take((size_t)p->nsym * sizeof(int2));
+  }
+  if (p->sx) {  // one contiguous region, cleared before each pass
+    const size_t per = (size_t)p->sx_nrec * (size_t)p->sx_nmat * 4;
+    int64_t ncol = 0;
+    for (int64_t o : p->sx_col) ncol += o >= 0;
+    const size_t cols = (size_t)ncol * (size_t)p->sx_nmat * (size_t)p->npad * 4;
+    p->off_sx = off;
+    p->off_sx_amax = take(per);
+    p->off_sx_colmax = take(per);
+    p->off_sx_exp = take(per);
+    p->off_sx_col = take(cols);
+    p->sx_bytes = off - p->off_sx;
   }
   for (int s = 0; s < SL_N; ++s) {
     SlotBufs& b = p->bufs[s];
@@ -713,6 +788,7 @@ int build(neumann_plan_s* p) {
   };
   if (p->sym || p->bmn) row_major_b(p->ops);
   if (p->bmn) row_major_b(p->mm_ops);
+  if (!build_records(p)) return NEUMANN_ENOTSUP;
   memset(p->reps, 0, sizeof(p->reps));
   note_reps(p, p->ops, p->sym || p->bmn);
   note_reps(p, p->mm_ops, p->bmn);
@@ -910,14 +986,9 @@ EpiOut resolve_out(const neumann_plan_s* p, const OutSpec& s, const EpiIn* ins, 
     o.in_f[i] = (float)s.in[i];
   }
   auto dst = [&](void* ptr, int64_t ld, int dt, int mode) { o.dst[o.ndst++] = EpiDst{ptr, ld, dt, mode}; };
-  const int fp16 = p->dtype == NEUMANN_SPLIT_FP16;
   auto split = [&](size_t hi, size_t lo, int tr) {
     o.split[o.nsplit++] = EpiSplit{p->ws + hi, p->ws + lo, p->npad, tr};
   };
-  if (fp16) {  // both operands of a tensor-core product carry 2^8
-    o.acc_d = s.acc / (double)(kFp16SplitScale * kFp16SplitScale);
-    o.acc_f = (float)o.acc_d;
-  }
   if (s.slot == SL_USER_S) {
     if (p->grouped)
       dst(const_cast<void*>(p->cur_stab), 0, p->dt_io, EPI_TABLE);
@@ -944,8 +1015,24 @@ EpiOut resolve_out(const neumann_plan_s* p, const OutSpec& s, const EpiIn* ins, 
   return o;
 }
 
-void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiParams* P) {
+// sx: the op's split-FP16 records (nullptr for other dtypes).
+void make_params(const neumann_plan_s* p, const Op& op, const UserPtrs& u, EpiParams* P,
+                 const neumann_plan_s::OpSx* sx = nullptr) {
   memset(P, 0, sizeof(*P));
+  if (sx) {
+    SxParams& q = P->sx;
+    q.active = 1;
+    q.nmat = p->sx_nmat;
+    q.npad = (int)p->npad;
+    q.exp = reinterpret_cast<int*>(p->ws + p->off_sx_exp);
+    q.rec_a = sx->rec_a;
+    q.rec_b = sx->rec_b;
+    for (int j = 0; j < kMaxOut; ++j) q.rec_out[j] = j < op.nout ? sx->rec_out[j] : -1;
+    if (sx->rec_acc >= 0) {
+      q.acc_amax = reinterpret_cast<unsigned*>(p->ws + p->off_sx_amax) + (size_t)sx->rec_acc * p->sx_nmat;
+      q.acc_col = reinterpret_cast<float*>(p->ws + p->off_sx_col) + p->sx_col[sx->rec_acc];
+    }
+  }
   P->n = (int)p->n;
   P->npad = (int)p->npad;
   P->status = reinterpret_cast<unsigned*>(p->ws);
@@ -1078,6 +1165,74 @@ int ensure_workspace(neumann_plan_s* p, cudaStream_t s) {
   return rc;
 }
 
+// The split-FP16 scale step before op i of `ops`: op i's records and
+// coefficients, and, when op i-1 is a product, what finalises its outputs.
+SxScaleOp sx_scale_op(const neumann_plan_s* p, const std::vector<Op>& ops,
+                      const std::vector<neumann_plan_s::OpSx>& rs, size_t i) {
+  SxScaleOp q;
+  memset(&q, 0, sizeof(q));
+  q.nmat = p->sx_nmat;
+  q.npad = (int)p->npad;
+  q.amax = reinterpret_cast<unsigned*>(p->ws + p->off_sx_amax);
+  q.colmax = reinterpret_cast<float*>(p->ws + p->off_sx_colmax);
+  q.exp = reinterpret_cast<int*>(p->ws + p->off_sx_exp);
+  q.col = reinterpret_cast<float*>(p->ws + p->off_sx_col);
+  const Op& op = ops[i];
+  const neumann_plan_s::OpSx& r = rs[i];
+  q.rec_a = r.rec_a;
+  q.rec_b = r.rec_b;
+  q.nin = op.nin;
+  for (int k = 0; k < op.nin; ++k) q.rec_in[k] = r.rec_in[k];
+  q.nout = op.nout;
+  for (int j = 0; j < op.nout; ++j) {
+    const OutSpec& o = op.out[j];
+    q.rec_out[j] = r.rec_out[j];
+    q.acc[j] = op.kind == OP_GEMM ? (float)o.acc : 0.f;
+    q.id[j] = (float)o.id;
+    for (int k = 0; k < kMaxIn; ++k) q.in[j][k] = (float)o.in[k];
+  }
+  q.prev_acc = -1;
+  if (i > 0 && ops[i - 1].kind == OP_GEMM) {
+    const Op& pv = ops[i - 1];
+    const neumann_plan_s::OpSx& pr = rs[i - 1];
+    q.prev_acc = pr.rec_acc;
+    q.prev_col = p->sx_col[pr.rec_acc];
+    q.prev_nin = pv.nin;
+    for (int k = 0; k < pv.nin; ++k) q.prev_in[k] = pr.rec_in[k];
+    q.prev_nout = pv.nout;
+    for (int j = 0; j < pv.nout; ++j) {
+      const OutSpec& o = pv.out[j];
+      q.prev_out[j] = pr.rec_out[j];
+      q.prev_a[j] = (float)o.acc;
+      q.prev_id[j] = (float)o.id;
+      for (int k = 0; k < kMaxIn; ++k) q.prev_c[j][k] = (float)o.in[k];
+    }
+  }
+  return q;
+}
+
+// Split-FP16: clear the stats region of this pass and measure the caller's
+// matrices that the ops read (records 0 and 1).
+int sx_begin(neumann_plan_s* p, const std::vector<Op>& ops, const UserPtrs& u, int count, cudaStream_t s) {
+  if (cudaMemsetAsync(p->ws + p->off_sx, 0, p->sx_bytes, s) != cudaSuccess) return NEUMANN_ECUDA;
+  bool need[2] = {false, false};
+  for (const Op& op : ops)
+    for (int i = 0; i < op.nin; ++i) {
+      need[0] |= op.in[i].slot == SL_USER_A;
+      need[1] |= op.in[i].slot == SL_USER_B;
+    }
+  for (int r = 0; r < 2; ++r) {
+    if (!need[r]) continue;
+    const EpiIn in = resolve_in(p, InRef{r == 0 ? SL_USER_A : SL_USER_B, 0}, u);
+    unsigned* amax = reinterpret_cast<unsigned*>(p->ws + p->off_sx_amax) + (size_t)r * p->sx_nmat;
+    unsigned* colmax = reinterpret_cast<unsigned*>(p->ws + p->off_sx_colmax) + (size_t)r * p->sx_nmat;
+    if (launch_sx_input_stats(in, p->grouped ? p->cur_matn : nullptr, (int)p->n, count, amax, colmax, s) !=
+        cudaSuccess)
+      return NEUMANN_ECUDA;
+  }
+  return NEUMANN_OK;
+}
+
 int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcMaps>& maps, const UserPtrs& u,
             cudaStream_t s, bool timing) {
   EpiParams P;
@@ -1102,9 +1257,17 @@ int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcM
         if (ops[i].out[j].slot == SL_USER_S && s_first < 0) s_first = i;
     }
   }
+  // split-FP16: matrices of this pass, and the op list's records
+  const int sx_count = p->grouped ? p->cur_count : 1;
+  const std::vector<neumann_plan_s::OpSx>* sxr = !p->sx ? nullptr : &ops == &p->ops ? &p->op_sx : &p->mm_sx;
+  if (sxr) {
+    const int rc = sx_begin(p, ops, u, sx_count, s);
+    if (rc) return rc;
+  }
   for (size_t i = 0; i < ops.size(); ++i) {
     const Op& op = ops[i];
-    make_params(p, op, u, &P);
+    make_params(p, op, u, &P, sxr ? &(*sxr)[i] : nullptr);
+    if (sxr && launch_sx_scale(sx_scale_op(p, ops, *sxr, i), sx_count, s) != cudaSuccess) return NEUMANN_ECUDA;
     if (p->hook_before_s && (int)i == s_first && cudaStreamWaitEvent(s, p->hook_before_s, 0) != cudaSuccess)
       return NEUMANN_ECUDA;
     cudaError_t err;
@@ -1288,6 +1451,7 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     p->n_tc = ch.ntc;
     p->n_simt = ch.nsimt;
     p->n_ew = ch.new_;
+    p->cur_count = ch.count;
     UserPtrs u{nullptr, 0, nullptr, nullptr, 0};
     int rc = run_ops(p, p->ops, p->maps, u, s, (p->flags & NEUMANN_FLAG_TIMING) != 0);
     if (rc) {

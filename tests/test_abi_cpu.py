@@ -40,11 +40,14 @@ def test_invalid_arguments(n, k, radix, dtype, flags):
 
 
 def test_fp16_plan_has_the_split_layout():
+    """The split-FP16 plan has the BF16 plan's matrices plus its scaling records
+    (max |x|, column-sum bound and exponent per output, column sums of the
+    products' right operands): a few KB at this order."""
     h = C.neumann_plan_create(64, 81, 9, C.SPLIT_FP16, 0)
     hb = C.neumann_plan_create(64, 81, 9, C.SPLIT_BF16, 0)
     try:
         a, b = C.neumann_plan_info(h), C.neumann_plan_info(hb)
-        assert a["workspace_bytes"] == b["workspace_bytes"]
+        assert 0 < a["workspace_bytes"] - b["workspace_bytes"] < 64 * 1024
         assert a["products_executed"] == b["products_executed"] == 8
     finally:
         C.neumann_plan_destroy(h)

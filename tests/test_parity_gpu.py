@@ -7,8 +7,9 @@ scheme: S_k for exact schemes, Lemma 5.7's closed form for radix 15):
   split-BF16  TOL_BF16[rho]; each operand is kept to ~2^-17 relative, so a
               product carries ~1e-5 relative error, amplified by ||S|| <= 1/(1-rho)
               across levels.
-  split-FP16  TOL_FP16[rho]; operands kept to ~2^-22 relative (x 2^8 scaling keeps
-              lo normal for |x| >= 2^-11), the same amplification. A product's
+  split-FP16  TOL_FP16[rho]; operands kept to ~2^-22 relative (each matrix stored
+              as x * 2^e with its own e, which keeps hi in range and lo normal
+              down to ~2^-17 of the matrix's bound), the same amplification. A product's
               FP32 accumulation on the tensor cores is biased toward zero by about
               (3n/16)/4 ulp of the sum (one truncating update per MMA; 2e-6 at
               n = 513, 3-5e-5 at n = 8192), which at n = 8192 exceeds both operand
@@ -171,22 +172,22 @@ def test_nonfinite_status_for_divergent_input():
     reports NEUMANN_STATUS_NONFINITE instead of trapping."""
     nm = _nm()
     m = G.jacobi_batch(1, 4, sizes=(64,), damped=False)[0]
-    for dtype in ("fp32", "split_bf16"):
+    for dtype in ("fp32", "split_bf16", "split_fp16"):
         S, st, _ = _run(m["A"], 15 ** 3, 15, dtype)
-        assert st & nm.STATUS_NONFINITE
+        assert st & nm.STATUS_NONFINITE, dtype
 
 
-def test_fp16_split_overflow_is_reported():
-    """A nilpotent A (rho = 0) with an entry of 300 is outside the scaled FP16
-    range (|x| < 255): its split is flagged NONFINITE instead of silently
-    returning a wrong result; the BF16 split (FP32 exponent range) is exact here."""
-    nm = _nm()
+def test_fp16_split_scales_large_entries():
+    """A nilpotent A (rho = 0, A^2 = 0) with entries of 300 and 3e6: far outside
+    FP16's range, but every split-FP16 matrix is stored with its own power of
+    two (the bound on max |x| mapped to <= 2^14), so S = I + A comes out exact,
+    as with the BF16 split (FP32 exponent range)."""
     A = np.zeros((16, 16))
     A[0, 1] = 300.0
-    S, st, _ = _run(A, 81, 9, "split_fp16")
-    assert st & nm.STATUS_NONFINITE
-    S, st, _ = _run(A, 81, 9, "split_bf16")
-    assert st == 0 and CF.rel_fro(S, np.eye(16) + A) < 1e-12
+    A[2, 5] = 3.0e6
+    for dtype in ("split_fp16", "split_bf16"):
+        S, st, _ = _run(A, 81, 9, dtype)
+        assert st == 0 and CF.rel_fro(S, np.eye(16) + A) < 1e-12, dtype
 
 
 def test_timing_flag_reports_every_product():
