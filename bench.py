@@ -762,7 +762,7 @@ def run_ours(args, wl, sub=False):
         "vs_baseline": None,
         "dtype": {"split_bf16": "bf16", "split_fp16": "f16", "fp32": "f32", "fp64": "f64"}[wl["dtype"]],
         "precision": {"split_bf16": "hi+lo BF16 operands, 3 products, FP32 accumulate, FP64 Y and R",
-                      "split_fp16": "hi+lo FP16 operands of x*2^8, 3 products, FP32 accumulate, FP64 Y and R",
+                      "split_fp16": "hi+lo FP16 operands of x*2^e (e per matrix), 3 products, FP32 accumulate, FP64 Y and R",
                       "fp32": "FP32 products, FP64 Y and R", "fp64": "FP64"}[wl["dtype"]]
                      + ("; K accumulated in chunks of 512 summed with round-to-nearest" if pflags else ""),
         "data": "synthetic",

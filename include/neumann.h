@@ -38,10 +38,13 @@
  *               operands (x = hi + lo, three products hi*hi + hi*lo + lo*hi,
  *               FP32 accumulation in tensor memory); Y and R accumulated in
  *               FP64. A and S are double unless NEUMANN_FLAG_IO_FP32.
- *   SPLIT_FP16  as SPLIT_BF16 with FP16 hi+lo operands of x * 2^8 (x = hi + lo to
- *               ~2^-22 relative for |x| >= 2^-11, ~2^-32 absolute below); every
- *               entry of every intermediate must stay below 255 in magnitude, an
- *               overflow sets NEUMANN_STATUS_NONFINITE.
+ *   SPLIT_FP16  as SPLIT_BF16 with FP16 hi+lo operands of x * 2^e, e chosen per
+ *               matrix (and per matrix of a batch) so that a bound on its max |x|
+ *               maps to 2^14: x = hi + lo to ~2^-22 relative for entries within
+ *               ~2^-17 of that bound, ~2^-39 of the bound absolute below. The
+ *               bound comes from max |x| and column sums measured by the
+ *               producing launches; FP16 overflow cannot occur unless an input
+ *               is not finite.
  *
  * Conventions shared by every call:
  *   - Matrices are dense, row-major, n x n, with a leading dimension (in
