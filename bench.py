@@ -68,6 +68,9 @@ WORKLOADS = {
     "batched-r9-fp32-4096-k81": dict(steps=90, cfg=4, count=4096, k=81, radix=9, dtype="fp32", batched=True),
     "batched-r15-fp32-4096-k225": dict(steps=64, cfg=4, count=4096, k=225, radix=15, dtype="fp32", batched=True),
     "batched-r25-bf16-4096-k625": dict(steps=76, cfg=4, count=4096, k=625, radix=25, dtype="split_bf16", batched=True),
+    # the same construction restricted to orders 16..64: the batch the resident launch serves
+    "batched-small-r9-bf16-4096-k81": dict(steps=200, cfg=4, count=4096, k=81, radix=9, dtype="split_bf16",
+                                           batched=True, sizes=(16, 32, 48, 64)),
 }
 DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 
@@ -423,9 +426,10 @@ def run_batched(args, wl, sub=False):
         world = 1
     elif world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    mats = G.jacobi_batch(wl["count"], 1000 * wl["cfg"] + rank)
+    mats = G.jacobi_batch(wl["count"], 1000 * wl["cfg"] + rank, **({"sizes": wl["sizes"]} if "sizes" in wl else {}))
     ns = [m["n"] for m in mats]
-    bp = nm.BatchedPlan(len(mats), 256, wl["k"], wl["radix"], wl["dtype"], nm.FLAG_TIMING)
+    bflags = nm.FLAG_TIMING | (nm.FLAG_NO_RESIDENT if args.no_resident else 0)
+    bp = nm.BatchedPlan(len(mats), 256, wl["k"], wl["radix"], wl["dtype"], bflags)
     dt = torch.float32 if wl["dtype"] == "fp32" else torch.float64
     # the batch lives in one contiguous buffer (A_i are views), so an end-to-end
     # step moves it with one copy each way
@@ -469,6 +473,9 @@ def run_batched(args, wl, sub=False):
     value = job_value(len(mats), args.steps, world, ms_max)
     info = nm.neumann_plan_info(bp.handle)
     ck = info["batch_chunk"] or len(mats)
+    nres = sum(1 for x in ns if x <= info["resident_max_n"])
+    # launches per step: each op of the scheme once per grouped pass, plus the resident launch
+    launches = info["launches"] * ((len(mats) - nres + ck - 1) // ck) + (1 if nres else 0)
     # the same batch, one plan per matrix order and one evaluation (own launches) per matrix
     plans = {}
     for n in sorted(set(ns)):
@@ -501,13 +508,15 @@ def run_batched(args, wl, sub=False):
     peaks, peak_src = _peaks()
     tc = wl["dtype"].startswith("split")
     per = info["products_executed"]
-    flops_one = sum(2.0 * n ** 3 for n in ns)  # one product over the batch, 2 n^3 per matrix
+    # the grouped product kernel's work: the matrices the resident launch does not take
+    gns = [x for x in ns if x > info["resident_max_n"]]
+    flops_one = sum(2.0 * n ** 3 for n in gns)  # one product over the grouped matrices, 2 n^3 each
     mean_prod = statistics.mean(prod_ms) if prod_ms else float("nan")
     # The products of orders <= 256 have little arithmetic per byte (about n / 5
     # tensor flops per byte), so both rooflines are computed and the one that
     # bounds the product (the longer ideal time) is reported.
     prod_s = sum(prod_ms) / args.steps / 1e3  # product time per step
-    bytes_step = sum(n * n for n in ns) * info["product_bytes_per_element"]
+    bytes_step = sum(n * n for n in gns) * info["product_bytes_per_element"]
     flops_step = per * flops_one * (3 if tc else 1)
     live = live_peaks(dev)
     fpeak = peaks["bf16_tflops_sustained"] if tc else live["fp32_tflops"]
@@ -541,16 +550,19 @@ def run_batched(args, wl, sub=False):
         "precision": "hi+lo BF16 operands, 3 products, FP32 accumulate, FP64 Y and R" if tc else
                      "FP32 products, FP64 Y and R",
         "data": "synthetic",
-        "config": {"workload": args.workload, "count": len(mats), "n": "uniform in {16,...,256}", "k": wl["k"],
+        "config": {"workload": args.workload, "count": len(mats),
+                   "n": "uniform in {%s}" % ",".join(map(str, wl.get("sizes", range(16, 257, 16)))), "k": wl["k"],
                    "radix": wl["radix"], "scheme": wl["dtype"], "products_per_matrix": per,
-                   "launches_per_step": info["launches"] * ((len(mats) + ck - 1) // ck),
+                   "launches_per_step": launches,
                    "batch_chunk": info["batch_chunk"], "autotuned": bool(info["tuned"]),
+                   "resident_max_n": info["resident_max_n"],
+                   "resident_matrices": nres,
                    "l2": "inputs larger than L2 (the batch's A alone is 0.39 GB in FP32)",
                    "parallelism": f"replicas x{world}"},
         "vs_per_matrix": {"ms_per_batch": per_matrix_ms, "speedup": per_matrix_ms / (ms_max / args.steps)},
         "status": status, "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
-        "gpu_launches": args.steps * info["launches"] * ((len(mats) + ck - 1) // ck),
+        "gpu_launches": args.steps * launches,
         "roofline": roof,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -854,6 +866,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch configuration")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison evaluation")
     ap.add_argument("--fp64-large", action="store_true", help="run the FP64 comparison on the n = 16384 workload")
+    ap.add_argument("--no-resident", action="store_true",
+                    help="batched workloads: every matrix through the grouped launches (no resident launch)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the secondary workloads (radix 9, precise, batched)")
     args = ap.parse_args()

@@ -118,6 +118,11 @@ typedef enum {
                                              framework value of Lemma 5.7 for that level sequence, which agrees
                                              with S_k through degree k-1 */
 
+#define NEUMANN_FLAG_NO_RESIDENT 0x200u  /* batched plans: run every matrix through the grouped launches (by
+                                             default the batch's matrices of order <= info.resident_max_n run in
+                                             one launch that keeps each matrix's whole level loop in one CTA's
+                                             shared memory) */
+
 #define NEUMANN_MAX_LEVELS 64
 
 typedef struct {
@@ -144,6 +149,10 @@ typedef struct {
      launch read or written once, plus both operands of each product. */
   int64_t bytes_per_element;          /* all launches of an evaluation */
   int64_t product_bytes_per_element;  /* the products alone */
+  int resident_max_n;           /* grouped batched plans: matrices of order <= this run in the resident
+                                   launch: 48 untuned (at most what one CTA's shared memory holds, 52-60
+                                   by scheme), then as neumann_plan_autotune_batched picks it (0: none,
+                                   FP64 plans, or NEUMANN_FLAG_NO_RESIDENT) */
 } neumann_plan_info_t;
 
 /* Create a plan for S_k(A) with A n x n. Host-only: no device memory is
@@ -229,6 +238,10 @@ int neumann_plan_create_batched(neumann_plan_t* out, int count, int64_t max_n, i
                                 int dtype, uint32_t flags);
 
 /* S_i <- S_k(A_i), i < count.
+ * Matrices of order <= info.resident_max_n (at most 64) run in one persistent
+ * launch, largest first, each through the whole scheme inside one CTA's shared
+ * memory (FP64 partial sums in a per-CTA scratch); the others in grouped
+ * launches, one per op of the scheme over up to 2048 matrices at a time.
  *   n  HOST array of count orders (1 <= n_i <= max_n)
  *   A  HOST array of count device pointers (n_i x n_i, leading dimension n_i)
  *   S  HOST array of count device pointers (same shapes; no overlap with any A_j)
@@ -258,10 +271,11 @@ int neumann_plan_autotune(neumann_plan_t plan, const void* A, int64_t lda, void*
                           void* stream);
 
 /* Autotuner for a batched plan: arguments as neumann_eval_batched plus reps.
- * For a grouped plan (max_n <= 256) it times the number of matrices per pass
- * (the plan's chunk halved down to 64, at most 6 candidates): smaller passes
- * keep a pass's intermediate matrices in L2, larger ones fill the GPU with
- * fewer launches. Shape key (count, max_n, k, radix, dtype). A plan with larger
+ * For a grouped plan (max_n <= 256) it times first the largest order the
+ * resident launch takes (0, 16, 32, 48 and the most it holds; the rest run
+ * grouped), then the number of matrices per grouped pass (the plan's chunk
+ * halved down to 64, at most 6 candidates): smaller passes keep a pass's
+ * intermediate matrices in L2, larger ones fill the GPU with fewer launches. Shape key (count, max_n, k, radix, dtype). A plan with larger
  * orders runs one single plan per order and is only marked tuned.
  * Errors as neumann_eval_batched. */
 int neumann_plan_autotune_batched(neumann_plan_t plan, int count, const int64_t* n, const void* const* A,

@@ -35,6 +35,7 @@ FLAG_SINGLE_CTA = 0x20
 FLAG_PRECISE_ACC = 0x40
 FLAG_SYMMETRIC = 0x80
 FLAG_ALLOW_APPROX = 0x100
+FLAG_NO_RESIDENT = 0x200
 
 MAX_LEVELS = 64
 
@@ -53,6 +54,7 @@ class PlanInfo(ctypes.Structure):
         ("workspace_bytes", c_size_t), ("padded_n", c_int64),
         ("tile_pair", c_int), ("raster_group", c_int), ("batch_chunk", c_int), ("tuned", c_int),
         ("bytes_per_element", c_int64), ("product_bytes_per_element", c_int64),
+        ("resident_max_n", c_int),
     ]
 
 
@@ -131,6 +133,7 @@ def neumann_plan_info(plan: int) -> dict:
         "tile_pair": info.tile_pair, "raster_group": info.raster_group, "batch_chunk": info.batch_chunk,
         "tuned": info.tuned, "bytes_per_element": info.bytes_per_element,
         "product_bytes_per_element": info.product_bytes_per_element,
+        "resident_max_n": info.resident_max_n,
     }
 
 

@@ -27,7 +27,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_simt.cu", "kernels_tc.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_simt.cu", "kernels_tc.cu", "kernels_resident.cu", "noalloc.cu"]
 CPP_SOURCES = ["plan.cpp", "approx_kernels.cpp"]
 
 

@@ -252,6 +252,52 @@ cudaError_t launch_sx_scale(const SxScaleOp& op, int count, cudaStream_t s);
 cudaError_t launch_sx_input_stats(const EpiIn& in, const int* mat_n, int n, int nmat, unsigned* amax,
                                   unsigned* colmax, cudaStream_t s);
 
+// ---- the resident small-order batch kernel (kernels_resident.cu) ----
+// One op of a scheme, as the resident kernel runs it. Slots index the CTA's
+// shared-memory matrices (-1: the caller's A for an input, the caller's S for
+// an output): every slot has an FP32 copy, and the slots the plan keeps in
+// FP64 also an FP64 copy (f64_of). Coefficients as in EpiOut.
+constexpr int kResMaxN = 64;                 // largest order the resident kernel holds
+constexpr int kResSmemBudget = 220 * 1024;   // dynamic shared memory of one CTA at most
+struct ResOp {
+  int gemm;                 // 1: product acc = a b, then the epilogue; 0: element-wise (acc = 0)
+  int a, b;
+  int nin, nout;
+  int in_slot[kMaxIn], in_f64[kMaxIn];
+  int out_slot[kMaxOut], out_f32[kMaxOut], out_f64[kMaxOut], f64[kMaxOut];
+  float acc_f[kMaxOut], id_f[kMaxOut], in_f[kMaxOut][kMaxIn];
+  double acc_d[kMaxOut], id_d[kMaxOut], in_d[kMaxOut][kMaxIn];
+};
+struct ResParams {
+  const ResOp* ops;         // device program, copied into each CTA's shared memory
+  int nops;
+  int nslots;               // FP32 matrices, nmax x nmax each
+  int nf64;                 // FP64 matrices
+  int f64_of[16];           // slot -> FP64 copy index (-1: none)
+  int nmax;                 // largest order of the launch (rounded up to 4)
+  int count;                // matrices
+  const int* mat_n;         // device: orders (largest first)
+  const void* const* A;     // device: caller pointers (leading dimension n_i)
+  void* const* S;
+  int io_f64;               // A and S are double (else float)
+  int mode;                 // 0 FP32 products, 1 split BF16, 2 split FP16 (per-matrix scale)
+  unsigned* status;
+};
+// Shared memory of a CTA holding the program and nslots FP32 + nf64 FP64
+// matrices of order nmax.
+inline size_t resident_smem(int nslots, int nf64, int nops, int nmax) {
+  return (size_t)nmax * nmax * (4 * (size_t)nslots + 8 * (size_t)nf64) + (size_t)nops * sizeof(ResOp);
+}
+// Threads of a CTA for order nmax: one per 4 x 4 output block, rounded up to warps.
+inline int resident_threads(int nmax) {
+  const int nb = (nmax + 3) / 4;
+  return (nb * nb + 31) / 32 * 32;
+}
+// The matrices of one launch in a persistent grid (as many CTAs as fit on the
+// device at once, at most one per matrix): CTA b runs matrices b, b + grid, ...,
+// each through the whole op program with its state in shared memory.
+cudaError_t launch_resident(const ResParams& P, cudaStream_t s);
+
 // ---- launchers (kernels_tc.cu) ----
 // Encode the four tensor maps over padded_n x padded_n BF16 arrays with leading
 // dimension ld; with count > 0, over count stacked padded_n x padded_n slabs

@@ -1,0 +1,277 @@
+// The resident batch kernel: small matrices of a batch, each held whole in one
+// CTA's shared memory across every level of the scheme.
+//
+// A grouped batch runs each op of the scheme as one launch over all its
+// matrices, so every intermediate matrix goes through HBM/L2 between launches,
+// and a matrix of order 16 or 64 pays the same per-launch latency as one of
+// order 256. Here one persistent launch takes the batch's small matrices
+// (largest first; CTA b takes matrices b, b + grid, ...). For each it runs the
+// plan's op program (the level loop of Sec. 5.3, eq. generalradix: kernel
+// products, concatenation, residual) with every matrix of the scheme in the
+// CTA's shared memory: FP32 copies of all, FP64 copies of the partial sum and
+// residual, and the program itself. Only A is read from and S written to the
+// caller's memory. The host launches one grid per size class (orders up to 16,
+// 32, and the largest held), each with as many threads as 4 x 4 output blocks
+// and as many CTAs per SM as its shared memory allows.
+//
+// Products: at n <= 64 a product is at most 0.5 MFLOP and the work is a chain
+// of dependent steps, so a product is a register-blocked SIMT loop (each
+// thread a 4 x 4 block of the output) rather than a tensor-core launch. For a
+// split plan the operands are split as the tensor-core path stores them (hi =
+// RN16(x), lo = RN16(x - hi); FP16 of x * 2^e with e from the operand's exact
+// max |x|, the bound mapped to 2^14), and hi*hi + hi*lo + lo*hi is accumulated
+// in FP32. The epilogue is the same linear combination as epilogue.cuh's: FP32
+// terms in FP32, then the identity and FP64 inputs in FP64, outputs' split
+// sources RN_fp32 of the value.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace neumann {
+
+namespace {
+
+constexpr int kResMaxThreads = 256;  // 16 x 16 blocks of 4 x 4 outputs cover order 64
+
+// hi + lo of x in the mode's 16-bit type (mode 2: of x * sc)
+template <int MODE>
+__device__ __forceinline__ void res_split(float x, float sc, float* hi, float* lo) {
+  if (MODE == 1) {
+    const float h = __bfloat162float(__float2bfloat16_rn(x));
+    *hi = h;
+    *lo = __bfloat162float(__float2bfloat16_rn(x - h));
+  } else {
+    const float w = x * sc;
+    const float h = __half2float(__float2half_rn(w));
+    *hi = h;
+    *lo = __half2float(__float2half_rn(w - h));
+  }
+}
+
+// max |x| over the n x n block of X (leading dimension ld); every thread calls it
+__device__ float res_block_amax(const float* X, int n, int ld, float* red) {
+  float v = 0.f;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) v = fmaxf(v, fabsf(X[(e / n) * ld + e % n]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+  return r;
+}
+
+// e with amax * 2^e <= 2^kSxTarget (0 for zero or non-finite)
+__device__ __forceinline__ int res_exp(float amax) {
+  if (!(amax > 0.f) || !isfinite(amax)) return 0;
+  int k = 0;
+  frexpf(amax, &k);
+  const int e = kSxTarget - k;
+  return e < -kSxMaxExp ? -kSxMaxExp : e > kSxMaxExp ? kSxMaxExp : e;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_constant__ ResParams P) {
+  // shared memory: FP64 copies | FP32 copies | program (16-byte aligned sections)
+  extern __shared__ __align__(16) double smd[];
+  __shared__ float red[kResMaxThreads / 32];
+  const int t = threadIdx.x;
+  const size_t slot = (size_t)P.nmax * P.nmax;
+  double* f64 = smd;
+  float* sm = reinterpret_cast<float*>(smd + (size_t)P.nf64 * slot);
+  ResOp* prog = reinterpret_cast<ResOp*>(sm + (size_t)P.nslots * slot);
+  for (int w = t; w < (int)(P.nops * sizeof(ResOp) / sizeof(int)); w += blockDim.x)
+    reinterpret_cast<int*>(prog)[w] = reinterpret_cast<const int*>(P.ops)[w];
+  __syncthreads();
+  bool bad = false;
+  for (int m = blockIdx.x; m < P.count; m += gridDim.x) {
+    const int n = P.mat_n[m];
+    const int ld = (n + 3) & ~3;  // rows of each matrix in its slot; padding zero
+    const int nb = ld / 4;
+    const bool act = t < nb * nb;
+    const int r0 = act ? (t / nb) * 4 : 0, c0 = act ? (t % nb) * 4 : 0;
+#pragma unroll 1
+    for (int k = 0; k < P.nops; ++k) {
+      const ResOp& op = prog[k];
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      if (op.gemm) {
+        const float* L = sm + op.a * slot;
+        const float* R = sm + op.b * slot;
+        int ea = 0, eb = 0;
+        if (MODE == 2) {  // each operand's own power of two
+          ea = res_exp(res_block_amax(L, n, ld, red));
+          eb = res_exp(res_block_amax(R, n, ld, red));
+        }
+        const float sa = ldexpf(1.f, ea), sb = ldexpf(1.f, eb);
+        if (act) {
+#pragma unroll 2
+          for (int q = 0; q < n; ++q) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = L[(r0 + i) * ld + q];
+            const float4 bv = *reinterpret_cast<const float4*>(R + q * ld + c0);
+            b[0] = bv.x;
+            b[1] = bv.y;
+            b[2] = bv.z;
+            b[3] = bv.w;
+            if (MODE == 0) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            } else {
+              float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                res_split<MODE>(a[i], sa, &ah[i], &al[i]);
+                res_split<MODE>(b[i], sb, &bh[i], &bl[i]);
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  acc[i][j] = fmaf(al[i], bh[j], fmaf(ah[i], bl[j], fmaf(ah[i], bh[j], acc[i][j])));
+            }
+          }
+          if (MODE == 2) {
+            const float inv = ldexpf(1.f, -(ea + eb));
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[i][j] *= inv;
+          }
+        }
+      }
+      __syncthreads();  // every operand read before any output is written
+      if (act) {
+        bool is64[kMaxIn];
+#pragma unroll
+        for (int ii = 0; ii < kMaxIn; ++ii)
+          is64[ii] = ii < op.nin && (op.in_slot[ii] < 0 ? P.io_f64 != 0 : op.in_f64[ii] != 0);
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {  // one row of the thread's block: 4 consecutive columns
+          const int r = r0 + i;
+          const int64_t e0 = (int64_t)r * ld + c0;
+          bool live[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) live[j] = r < n && c0 + j < n;
+          // every input load of the row before any output is formed
+          double vin[kMaxIn][4];
+#pragma unroll
+          for (int ii = 0; ii < kMaxIn; ++ii) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) vin[ii][j] = 0.0;
+            if (ii < op.nin) {
+              const int sl = op.in_slot[ii];
+              if (sl < 0) {  // the caller's A, leading dimension n
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  if (live[j])
+                    vin[ii][j] = P.io_f64 ? reinterpret_cast<const double*>(P.A[m])[(int64_t)r * n + c0 + j]
+                                          : (double)reinterpret_cast<const float*>(P.A[m])[(int64_t)r * n + c0 + j];
+              } else if (op.in_f64[ii]) {
+                const double2* q = reinterpret_cast<const double2*>(f64 + P.f64_of[sl] * slot + e0);
+                const double2 x = q[0], y = q[1];
+                vin[ii][0] = x.x;
+                vin[ii][1] = x.y;
+                vin[ii][2] = y.x;
+                vin[ii][3] = y.y;
+              } else {
+                const float4 x = *reinterpret_cast<const float4*>(sm + sl * slot + e0);
+                vin[ii][0] = x.x;
+                vin[ii][1] = x.y;
+                vin[ii][2] = x.z;
+                vin[ii][3] = x.w;
+              }
+            }
+          }
+#pragma unroll 1
+          for (int o = 0; o < op.nout; ++o) {
+            const bool f64o = op.f64[o] != 0;
+            const float af = op.acc_f[o], idf = op.id_f[o];
+            const double idd = op.id_d[o];
+            float vf[4];
+            double v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const bool diag = r == c0 + j;
+              if (f64o) {
+                // FP32 terms in FP32, then the identity and the FP64 inputs in FP64
+                float tt = af * acc[i][j];
+#pragma unroll
+                for (int ii = 0; ii < kMaxIn; ++ii)
+                  if (ii < op.nin && !is64[ii] && op.in_f[o][ii] != 0.f) tt = fmaf(op.in_f[o][ii], (float)vin[ii][j], tt);
+                double d = (double)tt + (diag ? idd : 0.0);
+#pragma unroll
+                for (int ii = 0; ii < kMaxIn; ++ii)
+                  if (ii < op.nin && is64[ii] && op.in_d[o][ii] != 0.0) d = fma(op.in_d[o][ii], vin[ii][j], d);
+                v[j] = live[j] ? d : 0.0;
+                vf[j] = (float)v[j];
+                bad |= !isfinite(d);
+              } else {
+                float t2 = af * acc[i][j] + (diag ? idf : 0.f);
+#pragma unroll
+                for (int ii = 0; ii < kMaxIn; ++ii)
+                  if (ii < op.nin && op.in_f[o][ii] != 0.f) t2 = fmaf(op.in_f[o][ii], (float)vin[ii][j], t2);
+                vf[j] = live[j] ? t2 : 0.f;
+                v[j] = (double)vf[j];
+                bad |= !isfinite(t2);
+              }
+            }
+            const int sl = op.out_slot[o];
+            if (sl < 0) {  // the caller's S, leading dimension n: the n x n block only
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                if (!live[j]) continue;
+                if (P.io_f64)
+                  reinterpret_cast<double*>(P.S[m])[(int64_t)r * n + c0 + j] = v[j];
+                else
+                  reinterpret_cast<float*>(P.S[m])[(int64_t)r * n + c0 + j] = vf[j];
+              }
+            } else {  // padding stored as zeros
+              if (op.out_f32[o])
+                *reinterpret_cast<float4*>(sm + sl * slot + e0) = make_float4(vf[0], vf[1], vf[2], vf[3]);
+              if (op.out_f64[o]) {
+                double2* q = reinterpret_cast<double2*>(f64 + P.f64_of[sl] * slot + e0);
+                q[0] = make_double2(v[0], v[1]);
+                q[1] = make_double2(v[2], v[3]);
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();  // the op's outputs complete before the next op reads them
+    }
+  }
+  if (bad && P.status) atomicOr(P.status, 1u);  // NEUMANN_STATUS_NONFINITE
+}
+
+}  // namespace
+
+cudaError_t launch_resident(const ResParams& P, cudaStream_t s) {
+  if (P.count <= 0) return cudaSuccess;
+  const size_t smem = resident_smem(P.nslots, P.nf64, P.nops, P.nmax);
+  const int threads = resident_threads(P.nmax);
+  if (smem > (size_t)kResSmemBudget || threads > kResMaxThreads || P.mode < 0 || P.mode > 2)
+    return cudaErrorInvalidValue;
+  static std::atomic<int> attr[3][kMaxDevices];
+  auto k = P.mode == 0 ? resident_kernel<0> : P.mode == 1 ? resident_kernel<1> : resident_kernel<2>;
+  cudaError_t e = once_per_device(
+      attr[P.mode], [&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmemBudget); });
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long cap = (long)per_sm * sm_count();
+  const int grid = (int)(P.count < cap ? P.count : cap);
+  k<<<grid, threads, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace neumann

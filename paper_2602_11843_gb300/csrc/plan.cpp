@@ -173,6 +173,7 @@ struct neumann_plan_s {
   char* pk_s = nullptr;
   size_t pk_bytes = 0;
   cudaEvent_t pk_in = nullptr, pk_a_free = nullptr, pk_done = nullptr, pk_s_free = nullptr;
+  cudaEvent_t pk_a_free_res = nullptr;  // the resident launches have read A
   bool pk_used = false;
   cudaEvent_t hook_after_a = nullptr;  // record after the last A-reading op (set during one run_ops)
   cudaEvent_t hook_before_s = nullptr;  // wait before the first S-writing op
@@ -239,6 +240,23 @@ struct neumann_plan_s {
     int first, count, tc0, ntc, simt0, nsimt, ew0, new_;
   };
   std::vector<Chunk> chunks;
+  // The resident kernel (kernels_resident.cu) for the batch's matrices of order
+  // <= res_limit (res_maxn: the most its shared memory holds): the op program
+  // with slots renumbered (res_slot_of) and FP64 copies (res_f64_of), and the
+  // table of resident matrices in the workspace. The last call's resident
+  // matrices (largest first) split into size classes, one launch each:
+  // res_class[c] = {first, count, nmax}.
+  std::vector<ResOp> res_ops;
+  int res_maxn = 0, res_limit = 0, res_nslots = 0, res_nf64 = 0, res_count = 0, last_res_limit = -1;
+  int res_slot_of[16];
+  int res_f64_of[16];
+  std::vector<int3> res_class;
+  size_t off_res_ops = 0, off_res_matn = 0, off_res_atab = 0, off_res_stab = 0;
+  // the resident launches run on their own stream, forked from and joined back
+  // into the evaluation's stream, alongside the grouped passes
+  cudaStream_t res_stream = nullptr;
+  cudaEvent_t res_fork = nullptr, res_join = nullptr;
+  cudaEvent_t hook_after_a_res = nullptr;  // record once the resident launches have read A (host calls)
 };
 
 namespace {
@@ -683,6 +701,86 @@ bool build_records(neumann_plan_s* p) {
   return true;
 }
 
+// ---------------------------------------------------------------- resident kernel
+
+constexpr int kResDefaultLimit = 48;  // largest resident order of an untuned plan
+
+// The grouped plan's op program for the resident kernel: every workspace slot
+// the ops touch becomes a shared-memory FP32 matrix, and the slots with an
+// FP64 copy also get a shared-memory FP64 matrix. The largest order held is the
+// largest multiple of 4 (<= 64) whose matrices and program fit the budget.
+void build_resident(neumann_plan_s* p) {
+  p->res_ops.clear();
+  p->res_maxn = p->res_limit = p->res_nslots = p->res_nf64 = 0;
+  if (!p->grouped || p->path == PATH_F64 || (p->flags & NEUMANN_FLAG_NO_RESIDENT)) return;
+  bool used[SL_N] = {}, f64[SL_N] = {};
+  for (const Op& op : p->ops) {
+    if (op.kind == OP_GEMM) used[op.a] = used[op.b] = true;
+    for (int i = 0; i < op.nin; ++i)
+      if (op.in[i].slot >= 0) {
+        used[op.in[i].slot] = true;
+        f64[op.in[i].slot] |= op.in[i].rep == REP_F64;
+      }
+    for (int j = 0; j < op.nout; ++j)
+      if (op.out[j].slot >= 0) {
+        used[op.out[j].slot] = true;
+        f64[op.out[j].slot] |= (op.out[j].reps & REP_F64) != 0;
+      }
+  }
+  for (int s = 0; s < 16; ++s) p->res_slot_of[s] = p->res_f64_of[s] = -1;
+  for (int s = 0; s < SL_N; ++s) {
+    if (!used[s]) continue;
+    p->res_slot_of[s] = p->res_nslots++;
+    if (f64[s]) p->res_f64_of[p->res_slot_of[s]] = p->res_nf64++;
+  }
+  const int nops = (int)p->ops.size();
+  int m = kResMaxN;
+  while (m >= 16 && resident_smem(p->res_nslots, p->res_nf64, nops, m) > (size_t)kResSmemBudget) m -= 4;
+  if (m < 16) return;
+  p->res_maxn = m;
+  // untuned: up to 48. Measured on the damped Jacobi batch (k = 81, 1024 matrices
+  // of one order), the resident launch beats the grouped one at every order up
+  // to 48 for split-BF16 and FP32 (n = 16: 0.10 ms against 0.96); at 60 the
+  // split-BF16 products no longer do. neumann_plan_autotune_batched tunes it.
+  p->res_limit = m < kResDefaultLimit ? m : kResDefaultLimit;
+  const bool io64 = p->dt_io == DT_F64;
+  for (const Op& op : p->ops) {
+    ResOp r;
+    memset(&r, 0, sizeof(r));
+    r.gemm = op.kind == OP_GEMM;
+    r.a = r.gemm ? p->res_slot_of[op.a] : 0;
+    r.b = r.gemm ? p->res_slot_of[op.b] : 0;
+    r.nin = op.nin;
+    bool in64[kMaxIn] = {};
+    for (int i = 0; i < op.nin; ++i) {
+      const InRef& x = op.in[i];
+      r.in_slot[i] = x.slot == SL_USER_A ? -1 : p->res_slot_of[x.slot];
+      r.in_f64[i] = x.slot >= 0 && x.rep == REP_F64;
+      in64[i] = x.slot == SL_USER_A ? io64 : r.in_f64[i] != 0;
+    }
+    r.nout = op.nout;
+    for (int j = 0; j < op.nout; ++j) {
+      const OutSpec& o = op.out[j];
+      const bool user = o.slot == SL_USER_S;
+      r.out_slot[j] = user ? -1 : p->res_slot_of[o.slot];
+      r.out_f32[j] = !user && (o.reps & (REP_W | REP_OPA | REP_OPB)) != 0;
+      r.out_f64[j] = !user && (o.reps & REP_F64) != 0;
+      bool f = (user && io64) || r.out_f64[j];
+      for (int i = 0; i < op.nin; ++i) f |= o.in[i] != 0.0 && in64[i];
+      r.f64[j] = f;
+      r.acc_d[j] = o.acc;
+      r.acc_f[j] = (float)o.acc;
+      r.id_d[j] = o.id;
+      r.id_f[j] = (float)o.id;
+      for (int i = 0; i < kMaxIn; ++i) {
+        r.in_d[j][i] = o.in[i];
+        r.in_f[j][i] = (float)o.in[i];
+      }
+    }
+    p->res_ops.push_back(r);
+  }
+}
+
 // ---------------------------------------------------------------- layout
 
 // sym: every matrix of the scheme is symmetric, so a product's right operand
@@ -719,6 +817,13 @@ void layout(neumann_plan_s* p) {
     p->off_tc = take(c * tiles_per * sizeof(int4));
     p->off_simt = take(c * tiles_per * sizeof(int4));
     p->off_ew = take(c * (size_t)(p->npad / 32) * (size_t)(p->npad / 32) * sizeof(int4));
+  }
+  if (p->res_maxn > 0) {
+    p->off_res_ops = take(p->res_ops.size() * sizeof(ResOp));
+    const size_t c = (size_t)p->count;
+    p->off_res_matn = take(c * sizeof(int));
+    p->off_res_atab = take(c * sizeof(void*));
+    p->off_res_stab = take(c * sizeof(void*));
   }
   if (p->sym && p->path == PATH_TC) {
     const int t = (int)(p->npad / 256);
@@ -789,6 +894,7 @@ int build(neumann_plan_s* p) {
   if (p->sym || p->bmn) row_major_b(p->ops);
   if (p->bmn) row_major_b(p->mm_ops);
   if (!build_records(p)) return NEUMANN_ENOTSUP;
+  build_resident(p);
   memset(p->reps, 0, sizeof(p->reps));
   note_reps(p, p->ops, p->sym || p->bmn);
   note_reps(p, p->mm_ops, p->bmn);
@@ -1140,6 +1246,9 @@ int attach(neumann_plan_s* p, void* ws) {
   if (p->path == PATH_TC) {
     if (!build_maps(p, p->ops, &p->maps, p->sym) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
   }
+  if (p->res_maxn > 0 && cudaMemcpy(p->ws + p->off_res_ops, p->res_ops.data(), p->res_ops.size() * sizeof(ResOp),
+                                     cudaMemcpyHostToDevice) != cudaSuccess)
+    return NEUMANN_ECUDA;
   p->maps_ready = true;
   return NEUMANN_OK;
 }
@@ -1356,7 +1465,7 @@ bool batch_aliases(int count, const int64_t* n, const void* const* A, void* cons
 int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* const* A, void* const* S,
                  cudaStream_t s) {
   const int ck = p->chunk_run > 0 ? p->chunk_run : p->chunk;  // matrices per pass
-  const bool same = (int)p->last_n.size() == count && ck == p->last_chunk_run &&
+  const bool same = (int)p->last_n.size() == count && ck == p->last_chunk_run && p->res_limit == p->last_res_limit &&
                     std::equal(n, n + count, p->last_n.begin()) && std::equal(A, A + count, p->last_a.begin()) &&
                     std::equal(S, S + count, p->last_s.begin());
   if (!same) {
@@ -1364,13 +1473,38 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    // the smallest orders (the end of `order`) run in the resident launch
+    int ng = count;
+    while (ng > 0 && n[order[ng - 1]] <= p->res_limit) --ng;
+    const int nres = count - ng;
+    // size classes of the resident matrices (largest first): orders above 32, 17..32, 1..16
+    p->res_class.clear();
+    for (int lo : {32, 16, 0}) {
+      int first = -1, cnt = 0, top = 0;
+      for (int k = 0; k < nres; ++k) {
+        const int nk = (int)n[order[ng + k]];
+        if (nk > lo && (lo == 32 || nk <= (lo == 16 ? 32 : 16))) {
+          if (first < 0) first = k;
+          ++cnt;
+          top = nk > top ? nk : top;
+        }
+      }
+      if (cnt) p->res_class.push_back(make_int3(first, cnt, (top + 3) & ~3));
+    }
     std::vector<int> matn(count);
     std::vector<const void*> atab(count);
     std::vector<void*> stab(count);
     std::vector<int4> tc, simt, ew;
     p->chunks.clear();
-    for (int c0 = 0; c0 < count; c0 += ck) {
-      const int cn = count - c0 < ck ? count - c0 : ck;
+    for (int k = 0; k < nres; ++k) {  // resident tables after the grouped ones' entries
+      const int i = order[ng + k];
+      matn[ng + k] = (int)n[i];
+      atab[ng + k] = A[i];
+      stab[ng + k] = S[i];
+    }
+    p->res_count = nres;
+    for (int c0 = 0; c0 < ng; c0 += ck) {
+      const int cn = ng - c0 < ck ? ng - c0 : ck;
       neumann_plan_s::Chunk ch{c0, cn, (int)tc.size(), 0, (int)simt.size(), 0, (int)ew.size(), 0};
       for (int j = 0; j < cn; ++j) {
         const int i = order[c0 + j];
@@ -1427,16 +1561,59 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
         cudaMemcpyAsync(ws + p->off_tc, p->h_tab + o_tc, tc.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(ws + p->off_simt, p->h_tab + o_simt, simt.size() * sizeof(int4), cudaMemcpyHostToDevice,
                         s) ||
-        cudaMemcpyAsync(ws + p->off_ew, p->h_tab + o_ew, ew.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
-        cudaEventRecord(p->tab_event, s))
+        cudaMemcpyAsync(ws + p->off_ew, p->h_tab + o_ew, ew.size() * sizeof(int4), cudaMemcpyHostToDevice, s))
       return NEUMANN_ECUDA;
+    if (nres > 0 &&  // the resident matrices' entries of the same image
+        (cudaMemcpyAsync(ws + p->off_res_matn, p->h_tab + o_matn + ng * sizeof(int), nres * sizeof(int),
+                         cudaMemcpyHostToDevice, s) ||
+         cudaMemcpyAsync(ws + p->off_res_atab, p->h_tab + o_atab + ng * sizeof(void*), nres * sizeof(void*),
+                         cudaMemcpyHostToDevice, s) ||
+         cudaMemcpyAsync(ws + p->off_res_stab, p->h_tab + o_stab + ng * sizeof(void*), nres * sizeof(void*),
+                         cudaMemcpyHostToDevice, s)))
+      return NEUMANN_ECUDA;
+    if (cudaEventRecord(p->tab_event, s)) return NEUMANN_ECUDA;
     p->last_chunk_run = ck;
+    p->last_res_limit = p->res_limit;
     p->last_n.assign(n, n + count);
     p->last_a.assign(A, A + count);
     p->last_s.assign(S, S + count);
   }
   char* ws = p->ws;
   cudaEvent_t after_a = p->hook_after_a, before_s = p->hook_before_s;
+  const int nres = p->res_count;
+  if (nres > 0) {  // fork: the resident launches on their own stream
+    if (!p->res_stream) {
+      if (cudaStreamCreateWithFlags(&p->res_stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->res_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->res_join, cudaEventDisableTiming) != cudaSuccess)
+        return NEUMANN_ECUDA;
+    }
+    // after the tables and the caller's A are in place; they write S, so after the previous copy-out
+    if (cudaEventRecord(p->res_fork, s) != cudaSuccess || cudaStreamWaitEvent(p->res_stream, p->res_fork, 0) != cudaSuccess)
+      return NEUMANN_ECUDA;
+    if (before_s && cudaStreamWaitEvent(p->res_stream, before_s, 0) != cudaSuccess) return NEUMANN_ECUDA;
+    for (const int3& cl : p->res_class) {  // one launch per size class
+      ResParams R;
+      memset(&R, 0, sizeof(R));
+      R.ops = reinterpret_cast<const ResOp*>(ws + p->off_res_ops);
+      R.nops = (int)p->res_ops.size();
+      R.nslots = p->res_nslots;
+      R.nf64 = p->res_nf64;
+      for (int k = 0; k < 16; ++k) R.f64_of[k] = p->res_f64_of[k];
+      R.count = cl.y;
+      R.mat_n = reinterpret_cast<const int*>(ws + p->off_res_matn) + cl.x;
+      R.A = reinterpret_cast<const void* const*>(ws + p->off_res_atab) + cl.x;
+      R.S = reinterpret_cast<void* const*>(ws + p->off_res_stab) + cl.x;
+      R.io_f64 = p->dt_io == DT_F64;
+      R.mode = p->path == PATH_F32 ? 0 : p->dtype == NEUMANN_SPLIT_FP16 ? 2 : 1;
+      R.status = reinterpret_cast<unsigned*>(ws);
+      R.nmax = cl.z;
+      if (launch_resident(R, p->res_stream) != cudaSuccess) return NEUMANN_ECUDA;
+    }
+    if (cudaEventRecord(p->res_join, p->res_stream) != cudaSuccess) return NEUMANN_ECUDA;
+    if (p->hook_after_a_res && cudaEventRecord(p->hook_after_a_res, p->res_stream) != cudaSuccess)
+      return NEUMANN_ECUDA;
+  }
   for (size_t ci = 0; ci < p->chunks.size(); ++ci) {
     const neumann_plan_s::Chunk& ch = p->chunks[ci];
     // S is first written by the first chunk; A is last read by the last chunk
@@ -1460,6 +1637,11 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     }
   }
   p->hook_after_a = p->hook_before_s = nullptr;
+  if (nres > 0) {  // join: the evaluation ends once the resident launches have
+    if (cudaStreamWaitEvent(s, p->res_join, 0) != cudaSuccess) return NEUMANN_ECUDA;
+    if (p->chunks.empty() && after_a && cudaEventRecord(after_a, s) != cudaSuccess) return NEUMANN_ECUDA;
+    if (p->chunks.empty() && before_s && cudaStreamWaitEvent(s, before_s, 0) != cudaSuccess) return NEUMANN_ECUDA;
+  }
   return NEUMANN_OK;
 }
 
@@ -1469,7 +1651,7 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
 // (padded order, dtype); grouped batches by (count, max order, k, radix, dtype).
 std::mutex g_tune_mu;
 std::map<std::pair<int64_t, int>, std::pair<int, int>> g_tune_single;
-std::map<std::tuple<int, int64_t, int64_t, int, int>, int> g_tune_batched;
+std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int, int>> g_tune_batched;  // chunk, resident limit
 
 // Single products are keyed by padded order and dtype; precise-accumulation
 // plans run another kernel and are keyed apart.
@@ -1481,8 +1663,9 @@ void apply_tuned(neumann_plan_s* p) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (p->batched) {
     auto it = g_tune_batched.find(std::make_tuple(p->count, p->max_n, p->k, p->radix, p->dtype));
-    if (it != g_tune_batched.end() && it->second <= p->chunk) {
-      p->chunk_run = it->second;
+    if (it != g_tune_batched.end() && it->second.first <= p->chunk && it->second.second <= p->res_maxn) {
+      p->chunk_run = it->second.first;
+      p->res_limit = it->second.second;
       p->tuned = true;
     }
   } else if (p->path == PATH_TC) {
@@ -1576,12 +1759,29 @@ int autotune_batched(neumann_plan_s* p, int count, const int64_t* n, const void*
   if (rc) return rc;
   EventPair ev;
   if (!ev.ok()) return NEUMANN_ECUDA;
+  // 1. the largest order the resident launch takes (none, 16, 32, 48, all it holds)
+  std::vector<int> lim;
+  for (int c : {0, 16, 32, 48, p->res_maxn})
+    if (c <= p->res_maxn && std::find(lim.begin(), lim.end(), c) == lim.end()) lim.push_back(c);
+  float best = 0.f;
+  int pick_lim = p->res_limit;
+  for (size_t i = 0; i < lim.size(); ++i) {
+    p->res_limit = lim[i];
+    float ms = 0.f;
+    rc = time_runs([&] { return eval_grouped(p, count, n, A, S, s); }, reps, s, ev.e0, ev.e1, &ms);
+    if (rc) return rc;
+    if (i == 0 || ms < best) {
+      best = ms;
+      pick_lim = lim[i];
+    }
+  }
+  p->res_limit = pick_lim;
+  // 2. matrices per grouped pass: the chunk halved down to 64
   std::vector<int> cand;
   for (int c = p->chunk; c >= 64 || c == p->chunk; c /= 2) {
     cand.push_back(c);
     if (cand.size() == 6 || c < 2) break;
   }
-  float best = 0.f;
   int pick = cand[0];
   for (size_t i = 0; i < cand.size(); ++i) {
     p->chunk_run = cand[i];
@@ -1597,7 +1797,7 @@ int autotune_batched(neumann_plan_s* p, int count, const int64_t* n, const void*
   p->timed = 0;
   p->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_batched[std::make_tuple(p->count, p->max_n, p->k, p->radix, p->dtype)] = pick;
+  g_tune_batched[std::make_tuple(p->count, p->max_n, p->k, p->radix, p->dtype)] = std::make_pair(pick, pick_lim);
   return NEUMANN_OK;
 }
 
@@ -1652,6 +1852,7 @@ int neumann_plan_info(neumann_plan_t p, neumann_plan_info_t* info) {
     info->raster_group = p->tune_group;
   }
   if (p->grouped) info->batch_chunk = p->chunk_run > 0 ? p->chunk_run : p->chunk;
+  info->resident_max_n = p->res_limit;
   info->tuned = p->tuned;
   for (const Op& op : p->ops) {
     const int64_t b = op_bytes(p, op);
@@ -1785,7 +1986,7 @@ int neumann_eval_batched_host(neumann_plan_t p, int count, const int64_t* n, con
         return NEUMANN_ECUDA;
     }
     if (!p->pk_in) {
-      for (cudaEvent_t* e : {&p->pk_in, &p->pk_a_free, &p->pk_done, &p->pk_s_free})
+      for (cudaEvent_t* e : {&p->pk_in, &p->pk_a_free, &p->pk_done, &p->pk_s_free, &p->pk_a_free_res})
         if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return NEUMANN_ECUDA;
     }
     if (bytes > p->pk_bytes) {  // grow the staging pair once nothing uses it
@@ -1811,8 +2012,10 @@ int neumann_eval_batched_host(neumann_plan_t p, int count, const int64_t* n, con
       sd[i] = p->pk_s + off * es;
       off += (size_t)n[i] * (size_t)n[i];
     }
-    // copy in once the previous evaluation has read its last A
-    if (p->pk_used && cudaStreamWaitEvent(p->cs_in, p->pk_a_free, 0) != cudaSuccess) return NEUMANN_ECUDA;
+    // copy in once the previous evaluation has read its last A (grouped passes and resident launches)
+    if (p->pk_used && (cudaStreamWaitEvent(p->cs_in, p->pk_a_free, 0) != cudaSuccess ||
+                       cudaStreamWaitEvent(p->cs_in, p->pk_a_free_res, 0) != cudaSuccess))
+      return NEUMANN_ECUDA;
     if (cudaMemcpyAsync(p->pk_a, A, bytes, cudaMemcpyHostToDevice, p->cs_in) != cudaSuccess ||
         cudaEventRecord(p->pk_in, p->cs_in) != cudaSuccess || cudaStreamWaitEvent(s, p->pk_in, 0) != cudaSuccess)
       return NEUMANN_ECUDA;
@@ -1820,9 +2023,11 @@ int neumann_eval_batched_host(neumann_plan_t p, int count, const int64_t* n, con
     if (rc) return rc;
     p->last_stream = s;
     p->hook_after_a = p->pk_a_free;
+    p->hook_after_a_res = p->pk_a_free_res;
     p->hook_before_s = p->pk_used ? p->pk_s_free : nullptr;
     if (p->grouped) {
       rc = eval_grouped(p, count, n, ad.data(), sd.data(), s);
+      p->hook_after_a_res = nullptr;
     } else {  // orders above 256: plain per-matrix evaluation, then the same copy-out
       p->hook_after_a = p->hook_before_s = nullptr;
       if (p->pk_used && cudaStreamWaitEvent(s, p->pk_s_free, 0) != cudaSuccess) return NEUMANN_ECUDA;
@@ -2002,7 +2207,13 @@ void neumann_plan_destroy(neumann_plan_t p) {
   }
   if (p->pk_a) cudaFree(p->pk_a);
   if (p->pk_s) cudaFree(p->pk_s);
-  for (cudaEvent_t e : {p->pk_in, p->pk_a_free, p->pk_done, p->pk_s_free})
+  for (cudaEvent_t e : {p->pk_in, p->pk_a_free, p->pk_done, p->pk_s_free, p->pk_a_free_res})
+    if (e) cudaEventDestroy(e);
+  if (p->res_stream) {
+    cudaStreamSynchronize(p->res_stream);
+    cudaStreamDestroy(p->res_stream);
+  }
+  for (cudaEvent_t e : {p->res_fork, p->res_join})
     if (e) cudaEventDestroy(e);
   if (p->cs_in) cudaStreamDestroy(p->cs_in);
   if (p->cs_out) cudaStreamDestroy(p->cs_out);

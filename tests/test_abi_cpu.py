@@ -225,3 +225,22 @@ def test_eval_host_argument_errors():
     finally:
         C.neumann_plan_destroy(h)
         C.neumann_plan_destroy(hb)
+
+
+def test_resident_orders_of_batched_plans():
+    """Grouped batched plans hold their smallest orders in the resident launch:
+    untuned, orders up to 48 (the most their shared memory holds is 52-60,
+    by the scheme's matrices); none for FP64 or with NEUMANN_FLAG_NO_RESIDENT."""
+    cases = [((81, 9, C.SPLIT_BF16, 0), 48), ((225, 15, C.SPLIT_FP16, 0), 48), ((81, 9, C.FP32, 0), 48),
+             ((625, 25, C.SPLIT_BF16, 0), 48), ((81, 9, C.FP64, 0), 0), ((81, 9, C.SPLIT_BF16, C.FLAG_NO_RESIDENT), 0)]
+    for (k, radix, dtype, flags), want in cases:
+        h = C.neumann_plan_create_batched(100, 256, k, radix, dtype, flags)
+        try:
+            assert C.neumann_plan_info(h)["resident_max_n"] == want, (k, radix, dtype, flags)
+        finally:
+            C.neumann_plan_destroy(h)
+    h = C.neumann_plan_create(64, 81, 9, C.SPLIT_BF16, 0)  # a single plan has none
+    try:
+        assert C.neumann_plan_info(h)["resident_max_n"] == 0
+    finally:
+        C.neumann_plan_destroy(h)
