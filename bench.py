@@ -476,6 +476,27 @@ def run_batched(args, wl, sub=False):
     nres = sum(1 for x in ns if x <= info["resident_max_n"])
     # launches per step: each op of the scheme once per grouped pass, plus the resident launch
     launches = info["launches"] * ((len(mats) - nres + ck - 1) // ck) + (1 if nres else 0)
+    # the same step captured once in a CUDA graph and replayed (resident and grouped launches)
+    graph = None
+    try:
+        gs = torch.cuda.Stream(dev)
+        with torch.cuda.stream(gs):
+            bp.launch()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            bp.launch()
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1) / args.steps
+        graph = {"ms_per_step": gms, "value": job_value(len(mats), args.steps, 1, gms * args.steps), "unit": UNIT}
+    except Exception as ex:  # noqa: BLE001 - reported, not fatal
+        graph = {"error": str(ex)[:200]}
     # the same batch, one plan per matrix order and one evaluation (own launches) per matrix
     plans = {}
     for n in sorted(set(ns)):
@@ -560,6 +581,7 @@ def run_batched(args, wl, sub=False):
                    "l2": "inputs larger than L2 (the batch's A alone is 0.39 GB in FP32)",
                    "parallelism": f"replicas x{world}"},
         "vs_per_matrix": {"ms_per_batch": per_matrix_ms, "speedup": per_matrix_ms / (ms_max / args.steps)},
+        "graph_replay": graph,
         "status": status, "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
         "gpu_launches": args.steps * launches,
@@ -849,6 +871,8 @@ def run_extras(args):
             d["vs_squaring"] = vq
         if "vs_per_matrix" in ln:
             d["vs_per_matrix"] = ln["vs_per_matrix"]
+            d["graph_replay"] = ln.get("graph_replay")
+            d["resident_matrices"] = ln["config"].get("resident_matrices")
         out[key] = d
         torch.cuda.empty_cache()
     return out
