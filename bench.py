@@ -52,6 +52,9 @@ WORKLOADS = {
     # five-product kernels (radix 24, 25: 7 products per level) on the same input
     "precision-r25-bf16-n8192-k15625": dict(steps=48, cfg=3, n=8192, k=15625, radix=25, dtype="split_bf16", sq_k=16384),
     "precision-r24-bf16-n8192-k13824": dict(steps=48, cfg=3, n=8192, k=13824, radix=24, dtype="split_bf16", sq_k=16384),
+    # approximate-prefix five-product kernels (App. C, Table approx): k = 27^3, 31^3
+    "precision-r27-bf16-n8192-k19683": dict(steps=48, cfg=3, n=8192, k=19683, radix=27, dtype="split_bf16", sq_k=16384),
+    "precision-r31-bf16-n8192-k29791": dict(steps=48, cfg=3, n=8192, k=29791, radix=31, dtype="split_bf16", sq_k=32768),
     # cfg 5: n = 16384, planted spectrum U[-0.95, 0.95] + rank-32 nonsymmetric term of norm 0.01;
     # the FP64 comparison (about two minutes at this size) runs only with --fp64-large
     "large-r15-fp16-n16384-k3375": dict(steps=8, cfg=5, n=16384, k=3375, radix=15, dtype="split_fp16", sq_k=4096,

@@ -11,11 +11,12 @@
  *   radix 9   exact 3-product radix-9 kernel, k = 9^t          (Thm 3.1)
  *   radix 15  approximate 4-product radix-15 kernel inside the residual
  *             framework, k = 15^t                             (Sec. 4, Sec. 5.3)
- *   radix 24, 25  approximate 5-product kernels inside the residual framework,
- *             k = 24^t or 25^t: the Sec. 4.1 circuit with a fifth product, at
+ *   radix 24, 25, 27, 31, 33  approximate 5-product kernels inside the residual
+ *             framework, k = m^t: the Sec. 4.1 circuit with a fifth product, at
  *             the 5-product budget of App. C (Table approx). The circuits are the
- *             library's own, with exact prefix [T~]_j = 1 for j < m
- *             (neumann_radix_p5_coefficients)
+ *             library's own: exact prefix [T~]_j = 1 for j < m at 24 and 25,
+ *             least-squares prefixes at 27, 31, 33 (neumann_radix_p5_coefficients).
+ *             Radix 33 converges for real eigenvalues in (-0.925, 1) only
  *   radix 0   exact kernels over the factorisation of k into 9, 5, 3, 2
  *             (block concatenation, Sec. 2.2, eq. decomposition); with
  *             NEUMANN_FLAG_ALLOW_APPROX also radix-15 levels (Lemma 5.7 holds
@@ -26,7 +27,7 @@
  * kernel f = T_m this residual is the next power A^{m n} (telescoping,
  * Sec. 2.2), so all schemes share one level loop.
  *
- * Result of radix 15, 24 and 25: the residual-framework value
+ * Result of radix 15, 24, 25, 27, 31 and 33: the residual-framework value
  * Y_t = (I-A)^{-1}(I - E^[t](A)) of Lemma 5.7, which agrees with S_k through the
  * degree-(k-1) term.
  *
@@ -161,10 +162,10 @@ typedef struct {
  * neumann_plan_set_workspace.
  *   out    receives the plan (set to NULL on error)
  *   n      matrix order, >= 1
- *   k      number of series terms, >= 1; for radix 3, 5, 9, 15, 24, 25 a power of the radix;
+ *   k      number of series terms, >= 1; for radix 3, 5, 9, 15, 24, 25, 27, 31, 33 a power of the radix;
  *          for radix 2 a power of two unless NEUMANN_FLAG_EXACT_K; for radix 0 of the
  *          form 2^a 3^b 5^c (levels as NEUMANN_FLAG_ALLOW_APPROX says)
- *   radix  0, 1, 2, 3, 5, 9, 15, 24 or 25 (see above)
+ *   radix  0, 1, 2, 3, 5, 9, 15, 24, 25, 27, 31 or 33 (see above)
  *   dtype  neumann_dtype_t
  *   flags  NEUMANN_FLAG_*
  * Errors: NEUMANN_EINVAL, NEUMANN_ENOTSUP, NEUMANN_ENOMEM (host). */
@@ -306,19 +307,22 @@ int neumann_plan_selftest_timeout(neumann_plan_t plan, uint64_t limit_ns, void* 
 int neumann_radix15_coefficients(int set, double* coef28, double* prefix_error, double* spill15,
                                  double* spill16);
 
-/* The 41 parameters of the five-product kernel of radix m = 24 or 25 that the
- * library uses. Circuit: P1 = B^2; for i = 2..5, L_i and R_i are linear
+/* The 41 parameters of the five-product kernel of radix m = 24, 25, 27, 31 or 33
+ * that the library uses. Circuit: P1 = B^2; for i = 2..5, L_i and R_i are linear
  * combinations over (I, B, P1, ..., P_{i-1}) and P_i = L_i R_i;
  * T~ = I + g1 B + g2 P1 + g3 P2 + g4 P3 + g5 P4 + P5 (Sec. 4.1 structure, one more
  * product; App. C, Table approx). Order: l2[3], r2[3], l3[4], r3[4], l4[5], r4[5],
  * l5[6], r5[6], gamma[5]. The values are the minimum-norm Gauss-Newton solution
  * of the m prefix equations [T~]_j = 1, j < m, from the library's published
- * six-decimal circuit, refined on the host on first use.
+ * six-decimal circuit, refined on the host on first use (m = 24, 25: exact
+ * prefix); for m = 27, 31, 33 no exact prefix exists in the library's search and
+ * the kernel is a published least-squares point used as it is (kernel residual
+ * sum_{j<m} ([T~]_j - 1)^2 = 4.7e-4, 0.109, 0.554; App. C, Table approx).
  *   coef41        receives the parameters (caller-owned, 41 doubles)
  *   prefix_error  receives max_{j<m} |[T~]_j - 1| (may be NULL)
  *   spill         receives the spillover [T~]_m (may be NULL)
- * Errors: NEUMANN_EINVAL (m not 24 or 25, coef41 NULL), NEUMANN_ENOTSUP (the
- * refinement did not reach rounding level). */
+ * Errors: NEUMANN_EINVAL (m not 24, 25, 27, 31 or 33; coef41 NULL), NEUMANN_ENOTSUP
+ * (the refinement of 24 / 25 did not reach rounding level). */
 int neumann_radix_p5_coefficients(int m, double* coef41, double* prefix_error, double* spill);
 
 /* C <- A B without any device allocation. The paper has no counterpart to this

@@ -4,8 +4,8 @@ radix 1  naive (Sec. 2.1)
 radix 2  repeated squaring for k = 2^t, binary digits of k otherwise (Sec. 2.1)
 radix 3, 5, 9  exact radix-m splitting with kernels T_3, T_5, T_9 (Sec. 2.2, Thm 3.1)
 radix 15 residual framework with the approximate T~_15 (Sec. 5.3, App. B)
-radix 24, 25  residual framework with the five-product approximate kernels
-         (App. C, Table approx; circuits of radix_p5.py)
+radix 24, 25, 27, 31, 33  residual framework with the five-product approximate
+         kernels (App. C, Table approx; circuits of radix_p5.py)
 radix 0  exact kernels over the factorisation of k into 9, 5, 3 and 2 (block
          concatenation holds for any factor order, Sec. 2.2); with approx=True
          the radix-15 kernel may take part too (mixed_levels), and the whole
@@ -27,11 +27,13 @@ def kernels(coef15: str = "refined") -> dict:
     coef = R15.load_refined(float) if coef15 == "refined" else R15.printed(float)
     return {2: C.kernel_t2, 3: C.kernel_t3, 5: C.kernel_t5, 9: C.kernel_t9,
             15: C.kernel_t15(coef),
-            24: C.kernel_p5(RP5.load_refined(24)), 25: C.kernel_p5(RP5.load_refined(25))}
+            24: C.kernel_p5(RP5.load_refined(24)), 25: C.kernel_p5(RP5.load_refined(25)),
+            27: C.kernel_p5(RP5.load_approx(27)), 31: C.kernel_p5(RP5.load_approx(31)),
+            33: C.kernel_p5(RP5.load_approx(33))}
 
 
 #: Radices whose kernels are approximate: they run in the residual framework (Sec. 5.3).
-APPROX = (15, 24, 25)
+APPROX = (15, 24, 25, 27, 31, 33)
 
 
 def auto_levels(k: int) -> list:

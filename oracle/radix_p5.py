@@ -1,4 +1,4 @@
-"""Five-product approximate radix kernels, radix 24 and 25 (this project's circuits).
+"""Five-product approximate radix kernels, radix 24, 25, 27, 31 and 33 (this project's circuits).
 
 Test infrastructure: only tests, the smoke check and the benchmark's CPU legs use it.
 
@@ -35,7 +35,25 @@ Both kernels converge on the whole real interval (-1, 1): |E(x)| < |x| there,
 with E(x) = 1 - (1 - x) T~_m(x) (Sec. 5.3). Radix 15 converges only to about
 |x| = 0.972.
 
+Approximate prefixes: radix 27, 31 and 33. From m = 26 on no start reaches an
+exact prefix, so these kernels are least-squares solutions of the same m
+prefix equations, with a nonzero kernel residual: App. C's "Kern. Res.", the
+objective sum_{j<m} ([T~]_j - 1)^2 (its radix-31 and radix-33 values, 1e-1 and
+6e-1, are what this search's minima come to: 8.8e-2 and 5.5e-1). Search:
+damped Gauss-Newton (gauss_newton, 1000 iterations) from SEARCH_APPROX_STARTS
+seeded N(0, 0.7^2) starts, start s drawn from default_rng([m, s]). Kept: the
+least objective among the solutions of growth <= 25 (within a relative 1e-6 of
+it, the least growth); a few larger objectives have a growth of 90 to 1800,
+which would enlarge the intermediate matrices as much. These minima are not
+isolated points (41 parameters, m < 41 equations), so there is no unique
+refinement: the kernel is the published float64 point itself (APPROX, 17
+significant digits, exact float64 round trip), on both sides. Both residual
+iterations still satisfy Lemma 5.7; with a nonzero prefix, E(z) = 1 - (1 - z)
+T~(z) has terms below degree m, and the framework value differs from S_k in
+those degrees by the kernel residual.
+
 `python -m oracle.radix_p5 --search 24` repeats the search and selection.
+`python -m oracle.radix_p5 --search-approx 27` repeats the approximate search.
 `python -m oracle.radix_p5 --write` regenerates radix_p5_refined.json (it needs
 mpmath). The stored file is what the oracle loads at run time.
 """
@@ -55,6 +73,11 @@ LAYOUT = (("l2", 3), ("r2", 3), ("l3", 4), ("r3", 4), ("l4", 5), ("r4", 5), ("l5
           ("gamma", 5))
 NPARAM = sum(n for _, n in LAYOUT)  # 41
 RADICES = (24, 25)
+#: approximate-prefix kernels: the published points are the kernels (no refinement)
+RADICES_APPROX = (27, 31, 33)
+SEARCH_APPROX_STARTS = 400
+SEARCH_APPROX_ITERS = 1000
+GROWTH_CAP = 25.0
 
 #: Search settings that produced STARTS: seed = m, N(0, 0.7^2) starts, and the
 #: start index of the kept (least-growth) exact solution among SEARCH_STARTS[m].
@@ -85,6 +108,46 @@ STARTS: dict = {
         "l5": ("-0.668592", "0.604396", "0.237796", "-0.142351", "-1.506913", "0.319748"),
         "r5": ("0.787637", "0.932110", "0.649669", "0.074046", "0.410067", "0.814745"),
         "gamma": ("0.938507", "0.999565", "-1.343732", "0.221997", "1.042277"),
+    },
+}
+
+#: Published approximate kernels (float64 points, 17 significant digits; see the module docstring).
+#: SEARCH_APPROX_PICK: the start each was taken from; SEARCH_APPROX_OBJECTIVE its kernel residual.
+SEARCH_APPROX_PICK = {27: 327, 31: 366, 33: 316}
+SEARCH_APPROX_OBJECTIVE = {27: 4.653915e-04, 31: 1.092148e-01, 33: 5.538754e-01}
+APPROX: dict = {
+    27: {
+        "l2": ("-0.2021484853654988", "1.7989425766047642", "1.4561412418359208"),
+        "r2": ("-0.0006080711007399042", "0.05426869601162476", "2.2613387247045935"),
+        "l3": ("-0.4265090898692607", "-1.4481292280060363", "0.7437802738035864", "0.3624012073537941"),
+        "r3": ("0.2911357044094076", "0.8015377400435508", "0.12070651440051255", "0.17040134374481075"),
+        "l4": ("0.3402072089340234", "-1.2306940425159345", "-1.617350884555378", "-0.020318879256120748", "0.556486490861503"),
+        "r4": ("-0.15945810527422183", "1.0056705878158259", "1.904087591026132", "-0.026013410660540692", "0.3106924383237238"),
+        "l5": ("-0.1532858746238227", "0.44190297815079815", "-1.740088212803465", "-0.49131608745192307", "-0.606805870061178", "-0.517937731805811"),
+        "r5": ("-1.289023892234788", "0.9029563627542537", "-0.20325172766345723", "-0.8223994948547484", "0.5337028287067901", "-0.6892370198152029"),
+        "gamma": ("0.516429565026994", "1.2908010739620663", "2.429652098636357", "-0.34485693381889965", "2.035622021577141"),
+    },
+    31: {
+        "l2": ("2.0453316479484163", "0.1688694324140469", "1.51953154352176"),
+        "r2": ("1.8168056762629776", "-0.4377776328419424", "-1.2359823428282803"),
+        "l3": ("-2.1864759523932897", "0.042273868229550836", "0.23454119259756298", "0.5567316265235517"),
+        "r3": ("1.575586508643876", "-0.9447520571083244", "1.0978971885367017", "-0.7937150593479639"),
+        "l4": ("-2.009269142248639", "0.6697975995983408", "-0.11408838861144101", "0.9351846765560184", "0.7052518479262201"),
+        "r4": ("0.9547864887358997", "0.1621881584151054", "-0.10567316014402432", "-0.4765502938981948", "-1.337162256540647"),
+        "l5": ("-2.081621580389158", "0.34942705629252474", "-0.11662395096113196", "0.4968904615284165", "0.6208520514369882", "0.044768134599075436"),
+        "r5": ("-1.0578840216769585", "-0.8421768163922988", "-0.6365877241141186", "-1.7315963541732742", "-2.215946746398454", "0.47026724516004614"),
+        "gamma": ("2.7016831112493125", "-0.3812489692334058", "-1.086805394216333", "-2.425467849004155", "-1.6186504451075652"),
+    },
+    33: {
+        "l2": ("0.2662305730114173", "-0.27541153036655625", "1.221435682555819"),
+        "r2": ("-0.10655865273379003", "0.386422004237438", "0.9252910966750612"),
+        "l3": ("0.10315644120288367", "-0.16350327407817775", "0.8843692848882467", "1.274655510590627"),
+        "r3": ("-0.048582401348742366", "-0.10061966978937412", "0.9164584103664615", "-1.4918620886387703"),
+        "l4": ("0.2288344936652722", "-0.025384941503025726", "-0.013708459171602683", "1.0915680907035115", "-0.41164698653232373"),
+        "r4": ("0.5164971269730494", "0.17653476382050737", "0.10792645729397232", "-0.6620928376534649", "-0.4624104696585189"),
+        "l5": ("1.5384882243042697", "0.07193390361184127", "0.09407185181801819", "0.21677467686617422", "-0.6128331509153844", "0.49797524620007366"),
+        "r5": ("-0.24390167959492054", "-0.03727319375048299", "0.39007636954769365", "-0.5078209953742294", "0.9598470894397494", "1.0730966491942626"),
+        "gamma": ("0.7244687252010907", "0.3789588239300521", "0.929628474171689", "-2.2422795531448374", "1.9755595070785952"),
     },
 }
 
@@ -361,11 +424,67 @@ def _write():
         f.write("\n")
 
 
+# --------------------------------------------------------------------------
+# Approximate-prefix kernels (radix 27, 31, 33)
+# --------------------------------------------------------------------------
+
+def prefix_objective(m: int, x) -> float:
+    """App. C's kernel residual: sum_{j<m} ([T~]_j - 1)^2, float64."""
+    T = circuit_np(x, jacobian=False)
+    F = T[:m] - 1.0
+    return float(F @ F)
+
+
+def _approx_start(args):
+    m, s = args
+    rng = np.random.default_rng([m, s])
+    x, f = gauss_newton(m, rng.standard_normal(NPARAM) * SEARCH_SCALE, iters=SEARCH_APPROX_ITERS)
+    return s, x, f, growth(x)
+
+
+def search_approx(m: int, starts: int = SEARCH_APPROX_STARTS, workers: int = 0):
+    """Least-squares Gauss-Newton from `starts` seeded points: [(start, x, objective, growth)]."""
+    args = [(m, s) for s in range(starts)]
+    if workers > 1:
+        import multiprocessing as mproc
+
+        with mproc.get_context("spawn").Pool(workers) as pool:
+            return pool.map(_approx_start, args)
+    return [_approx_start(a) for a in args]
+
+
+def select_approx(results):
+    """Least objective among growth <= GROWTH_CAP; within a relative 1e-6 of it, least growth."""
+    ok = [r for r in results if r[3] <= GROWTH_CAP]
+    fmin = min(r[2] for r in ok)
+    tie = [r for r in ok if r[2] <= fmin * (1.0 + 1e-6)]
+    return min(tie, key=lambda r: r[3])
+
+
+def approx_start_point(m: int, s: int):
+    """The Gauss-Newton solution from start s (what the published point was taken from)."""
+    return _approx_start((m, s))
+
+
+def load_approx(m: int, num=float) -> dict:
+    """The published approximate kernel of radix m (27, 31, 33) in `num`."""
+    return {k: [num(v) for v in vals] for k, vals in APPROX[m].items()}
+
+
+def to_full_strings(x) -> dict:
+    return {name: [repr(float(v)) for v in vals] for name, vals in unflatten(list(x)).items()}
+
+
 if __name__ == "__main__":
     import sys
 
     if "--write" in sys.argv:
         _write()
+    elif "--search-approx" in sys.argv:
+        m = int(sys.argv[sys.argv.index("--search-approx") + 1])
+        s, x, f, g = select_approx(search_approx(m, workers=8))
+        print(f"radix {m}: start {s}, objective {f:.6e}, growth {g:.4f}")
+        print(json.dumps(to_full_strings(x)))
     elif "--search" in sys.argv:
         m = int(sys.argv[sys.argv.index("--search") + 1])
         s, x, g = select(m)

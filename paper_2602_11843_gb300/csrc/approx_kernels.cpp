@@ -1,5 +1,5 @@
 // Parameters of the approximate radix kernels: radix 15 (four products) and
-// radix 24 and 25 (five products).
+// radix 24, 25, 27, 31 and 33 (five products).
 //
 // Circuit (Sec. 4.1, eq. factors / radix15kernel; one more product for the
 // five-product kernels of App. C, Table approx):
@@ -72,6 +72,48 @@ const double kRadix25[41] = {
     0.787637, 0.932110, 0.649669, 0.074046, 0.410067, 0.814745,      // r5
     0.938507, 0.999565, -1.343732, 0.221997, 1.042277,           // gamma
 };
+
+// Radix 27, 31 and 33: approximate-prefix circuits (least-squares solutions of
+// the m prefix equations, kernel residual sum_{j<m} ([T~]_j - 1)^2 of 4.7e-4,
+// 0.109 and 0.554). They are used exactly as published, to float64's 17
+// significant digits: least-squares minima are not isolated points, so a
+// refinement would not single one out.
+const double kRadix27[41] = {
+    -0.2021484853654988, 1.7989425766047642, 1.4561412418359208,  // l2
+    -0.0006080711007399042, 0.05426869601162476, 2.2613387247045935,  // r2
+    -0.4265090898692607, -1.4481292280060363, 0.7437802738035864, 0.3624012073537941,  // l3
+    0.2911357044094076, 0.8015377400435508, 0.12070651440051255, 0.17040134374481075,  // r3
+    0.3402072089340234, -1.2306940425159345, -1.617350884555378, -0.020318879256120748, 0.556486490861503,  // l4
+    -0.15945810527422183, 1.0056705878158259, 1.904087591026132, -0.026013410660540692, 0.3106924383237238,  // r4
+    -0.1532858746238227, 0.44190297815079815, -1.740088212803465, -0.49131608745192307, -0.606805870061178, -0.517937731805811,  // l5
+    -1.289023892234788, 0.9029563627542537, -0.20325172766345723, -0.8223994948547484, 0.5337028287067901, -0.6892370198152029,  // r5
+    0.516429565026994, 1.2908010739620663, 2.429652098636357, -0.34485693381889965, 2.035622021577141,  // gamma
+};
+
+const double kRadix31[41] = {
+    2.0453316479484163, 0.1688694324140469, 1.51953154352176,  // l2
+    1.8168056762629776, -0.4377776328419424, -1.2359823428282803,  // r2
+    -2.1864759523932897, 0.042273868229550836, 0.23454119259756298, 0.5567316265235517,  // l3
+    1.575586508643876, -0.9447520571083244, 1.0978971885367017, -0.7937150593479639,  // r3
+    -2.009269142248639, 0.6697975995983408, -0.11408838861144101, 0.9351846765560184, 0.7052518479262201,  // l4
+    0.9547864887358997, 0.1621881584151054, -0.10567316014402432, -0.4765502938981948, -1.337162256540647,  // r4
+    -2.081621580389158, 0.34942705629252474, -0.11662395096113196, 0.4968904615284165, 0.6208520514369882, 0.044768134599075436,  // l5
+    -1.0578840216769585, -0.8421768163922988, -0.6365877241141186, -1.7315963541732742, -2.215946746398454, 0.47026724516004614,  // r5
+    2.7016831112493125, -0.3812489692334058, -1.086805394216333, -2.425467849004155, -1.6186504451075652,  // gamma
+};
+
+const double kRadix33[41] = {
+    0.2662305730114173, -0.27541153036655625, 1.221435682555819,  // l2
+    -0.10655865273379003, 0.386422004237438, 0.9252910966750612,  // r2
+    0.10315644120288367, -0.16350327407817775, 0.8843692848882467, 1.274655510590627,  // l3
+    -0.048582401348742366, -0.10061966978937412, 0.9164584103664615, -1.4918620886387703,  // r3
+    0.2288344936652722, -0.025384941503025726, -0.013708459171602683, 1.0915680907035115, -0.41164698653232373,  // l4
+    0.5164971269730494, 0.17653476382050737, 0.10792645729397232, -0.6620928376534649, -0.4624104696585189,  // r4
+    1.5384882243042697, 0.07193390361184127, 0.09407185181801819, 0.21677467686617422, -0.6128331509153844, 0.49797524620007366,  // l5
+    -0.24390167959492054, -0.03727319375048299, 0.39007636954769365, -0.5078209953742294, 0.9598470894397494, 1.0730966491942626,  // r5
+    0.7244687252010907, 0.3789588239300521, 0.929628474171689, -2.2422795531448374, 1.9755595070785952,  // gamma
+};
+
 
 // The circuit with NPROD products as a polynomial in z, with the derivative of
 // every coefficient with respect to every parameter (forward mode).
@@ -281,6 +323,15 @@ bool radix15_coefficients(int set, double coef[28], double* prefix_err, double* 
 }
 
 bool radix_p5_coefficients(int m, double coef[kApproxP5Params], double* prefix_err, double* spill) {
+  if (m == 27 || m == 31 || m == 33) {  // approximate prefix: the published point as it is
+    const double* x = m == 27 ? kRadix27 : m == 31 ? kRadix31 : kRadix33;
+    std::vector<Circuit<5>::DPoly> work, T(1);
+    Circuit<5>::eval(x, &T[0], work);
+    memcpy(coef, x, kApproxP5Params * sizeof(double));
+    if (prefix_err) *prefix_err = Circuit<5>::prefix_error(T[0], m);
+    if (spill) *spill = m <= Circuit<5>::DEG ? T[0].v[m] : 0.0;
+    return true;
+  }
   if (m != 24 && m != 25) return false;
   static Refined refined[2];
   static std::once_flag once[2];

@@ -117,7 +117,10 @@ int mu_of(int m) {
     case 9: return 3;
     case 15: return 4;
     case 24:
-    case 25: return 5;
+    case 25:
+    case 27:
+    case 31:
+    case 33: return 5;
   }
   return -1;
 }
@@ -381,7 +384,7 @@ struct Sched {
       add_in(op4, SL_C, REP_W);
       tail(op4, 1.0, {1.0});
       ops().push_back(op4);
-    } else if (m == 24 || m == 25) {  // five-product circuit (App. C, Table approx; Sec. 4.1 structure)
+    } else if (m == 24 || m == 25 || m == 27 || m == 31 || m == 33) {  // five-product circuit (App. C, Table approx)
       const double* x = p->cp5;
       const double *l2 = x, *r2 = x + 3, *l3 = x + 6, *r3 = x + 10, *l4 = x + 14, *r4 = x + 19;
       const double *l5 = x + 24, *r5 = x + 30, *g = x + 36;
@@ -984,6 +987,9 @@ int validate_and_levels(neumann_plan_s* p) {
     case 15:
     case 24:
     case 25:
+    case 27:
+    case 31:
+    case 33:
       if (!pure_power(k, p->radix, &p->levels)) return NEUMANN_EINVAL;
       break;
     case 0: {
@@ -1031,7 +1037,7 @@ int init_plan(neumann_plan_s* p, int64_t n, int64_t k, int radix, int dtype, uin
     if (!radix15_coefficients((flags & NEUMANN_FLAG_PRINTED_COEFFS) ? 1 : 0, p->c15, &e, &s15, &s16))
       return NEUMANN_ENOTSUP;
   }
-  if (radix == 24 || radix == 25) {
+  if (mu_of(radix) == 5) {
     double e, sp;
     if (!radix_p5_coefficients(radix, p->cp5, &e, &sp)) return NEUMANN_ENOTSUP;
   }
@@ -2182,7 +2188,7 @@ int neumann_radix15_coefficients(int set, double* coef28, double* prefix_error, 
 }
 
 int neumann_radix_p5_coefficients(int m, double* coef41, double* prefix_error, double* spill) {
-  if ((m != 24 && m != 25) || !coef41) return NEUMANN_EINVAL;
+  if ((m != 24 && m != 25 && m != 27 && m != 31 && m != 33) || !coef41) return NEUMANN_EINVAL;
   double e = 0, a = 0;
   const bool ok = radix_p5_coefficients(m, coef41, &e, &a);
   if (prefix_error) *prefix_error = e;
