@@ -482,13 +482,16 @@ def run_batched(args, wl, sub=False):
     # the same step captured once in a CUDA graph and replayed (resident and grouped launches)
     graph = None
     try:
+        gp = nm.BatchedPlan(len(mats), 256, wl["k"], wl["radix"], wl["dtype"],
+                            nm.FLAG_NO_RESIDENT if args.no_resident else 0)
+        gp.bind(As, outs)  # created after bp's tuning: it starts from the same tuned configuration
         gs = torch.cuda.Stream(dev)
         with torch.cuda.stream(gs):
-            bp.launch()
+            gp.launch()
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=gs):
-            bp.launch()
+            gp.launch()
         g.replay()
         torch.cuda.synchronize()
         e0.record(stream)

@@ -283,7 +283,8 @@ int neumann_plan_autotune_batched(neumann_plan_t plan, int count, const int64_t*
                                   void* const* S, int reps, void* stream);
 
 /* With NEUMANN_FLAG_TIMING every product launched by neumann_eval is bracketed
- * by two CUDA events on the evaluation's stream. This call synchronises on the
+ * by two CUDA events on the evaluation's stream (not while the stream is being
+ * captured into a CUDA graph: a captured evaluation records nothing). This call synchronises on the
  * last of them, copies the device time (ms) of each product recorded since the
  * previous call into ms[0..cap-1] (in launch order), sets *count to the number
  * recorded, and starts a new record. At most 65536 products are kept; an

@@ -1352,6 +1352,11 @@ int run_ops(neumann_plan_s* p, const std::vector<Op>& ops, const std::vector<TcM
             cudaStream_t s, bool timing) {
   EpiParams P;
   int gi = p->timed;  // timing accumulates over evaluations until neumann_plan_timing reads it
+  if (timing) {  // events recorded into a CUDA graph capture cannot be timed: no record then
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return NEUMANN_ECUDA;
+    timing = cs == cudaStreamCaptureStatusNone;
+  }
   if (timing) {
     int ng = 0;
     for (const Op& op : ops) ng += op.kind == OP_GEMM;

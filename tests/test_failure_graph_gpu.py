@@ -59,6 +59,32 @@ def test_graph_capture_single(dtype, tol):
     assert CF.rel_fro(S.cpu().numpy(), ref) < tol
 
 
+def test_timing_flag_records_nothing_under_capture():
+    """A plan with NEUMANN_FLAG_TIMING captured into a CUDA graph: the captured
+    evaluation records no events (they could not be timed); an evaluation
+    outside the capture still records one interval per product."""
+    import paper_2602_11843_gb300 as nm
+
+    n = 256
+    p = nm.Plan(n, 81, 9, "split_bf16", nm.FLAG_TIMING)
+    pl = G.planted_symmetric(n, 0.9, 33)
+    A = torch.tensor(pl["A"], dtype=torch.float64, device="cuda")
+    S = torch.empty_like(A)
+    p(A, out=S)
+    torch.cuda.synchronize()
+    assert len(p.timing()) == p.info["products_executed"]
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        p(A, out=S)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert p.timing() == []
+    assert p.status() == 0
+    ref = EV.planted_reference(pl["V"], pl["lam"], 81, 9)
+    assert CF.rel_fro(S.cpu().numpy(), ref) < 1e-3
+
+
 def test_graph_capture_grouped_batch():
     import paper_2602_11843_gb300 as nm
 
