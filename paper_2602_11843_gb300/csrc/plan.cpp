@@ -415,9 +415,17 @@ struct Sched {
       // P3 = L3 R3; L4, R4 over (I, B, P1, P2, P3); C += g4 P3. The parts of L5,
       // R5 over (I, B, P1, P2, P3) come from this epilogue in a grouped batch,
       // whose products are bound by their epilogues anyway. A single product's
-      // epilogue with five outputs would no longer hide behind its main loop,
-      // so there P3 is stored and an element-wise pass forms them.
+      // epilogue with five outputs would no longer hide behind its main loop.
+      // There, after P3, C = g1 B + g2 P1 + g3 P2 + g4 P3 holds P3's share, so
+      //   sum_j l5_j X_j = l5_0 I + sum_{j=1..3} (l5_j - l5_4 g_j / g4) X_j + (l5_4 / g4) C
+      // over X = (I, B, P1, P2, P3), and P4's epilogue forms L5 and R5 from
+      // (B, P1, P2, C) and P4: P3 is not stored and no element-wise pass runs.
+      // The substitution multiplies C's FP32 rounding by |l5_4 / g4| (6.8 at
+      // most over radix 24-33); above 16, P3 is stored and a pass forms the parts.
       const bool fold = p->grouped;
+      const double kSubMax = 16.0;
+      const bool subst = !fold && std::fabs(g[3]) > 0.0 && std::fabs(l5[4] / g[3]) <= kSubMax &&
+                         std::fabs(r5[4] / g[3]) <= kSubMax;
       Op op3 = mk_gemm(SL_LF1, SL_RF1);
       add_in(op3, R, REP_W);
       add_in(op3, SL_P1, REP_W);
@@ -440,11 +448,33 @@ struct Sched {
             L5.in[j] = l5[1 + j];
             R5.in[j] = r5[1 + j];
           }
-        } else {
+        } else if (!subst) {
           add_out(op3, SL_P3, REP_W, 1.0, 0.0);
         }
       }
       ops().push_back(op3);
+      if (subst) {
+        // P4 = L4 R4; L5, R5 over (I, B, P1, P2, C) and P4; C += g5 P4
+        Op op4 = mk_gemm(SL_LF0, SL_RF0);
+        add_in(op4, R, REP_W);
+        add_in(op4, SL_P1, REP_W);
+        add_in(op4, SL_P2, REP_W);
+        add_in(op4, SL_C, REP_W);
+        for (int side = 0; side < 2; ++side) {
+          const double* c5 = side ? r5 : l5;
+          OutSpec& o = add_out(op4, side ? SL_RF1 : SL_LF1, side ? REP_OPB : REP_OPA, c5[5], c5[0]);
+          const double t = c5[4] / g[3];
+          for (int j = 0; j < 3; ++j) o.in[j] = c5[1 + j] - t * g[j];
+          o.in[3] = t;
+        }
+        add_out(op4, SL_C, REP_W, g[4], 0.0).in[3] = 1.0;
+        ops().push_back(op4);
+        Op op5 = mk_gemm(SL_LF1, SL_RF1);
+        add_in(op5, SL_C, REP_W);
+        tail(op5, 1.0, {1.0});
+        ops().push_back(op5);
+        return;
+      }
       if (!fold) {  // element-wise: the parts of L5, R5 over (I, B, P1, P2, P3)
         Op ew = mk_ewise();
         add_in(ew, R, REP_W);

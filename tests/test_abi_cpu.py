@@ -131,19 +131,20 @@ def test_library_radix_p5_coefficients_match_oracle(m):
         assert e.value.code == C.EINVAL
 
 
-@pytest.mark.parametrize("radix,k", [(24, 576), (25, 15625)])
+@pytest.mark.parametrize("radix,k", [(24, 576), (25, 15625), (27, 729), (31, 961), (33, 1089)])
 def test_five_product_levels_pass_count(radix, k):
-    """A single radix-24/25 plan forms the fifth factors' parts in one element-wise
-    pass per level (after the split of A); a grouped batch folds them into the
-    third product's epilogue, so it launches only the split and the products."""
-    levels = {576: 2, 15625: 3}[k]
+    """A single five-product plan forms the fifth factors in the fourth product's
+    epilogue, with the third power's share read from C (no element-wise pass);
+    a grouped batch folds their parts into the third product's epilogue. Both
+    launch only the split of A and the products."""
+    levels = {576: 2, 15625: 3, 729: 2, 961: 2, 1089: 2}[k]
     h = C.neumann_plan_create(1024, k, radix, C.SPLIT_BF16, 0)
     try:
         i = C.neumann_plan_info(h)
     finally:
         C.neumann_plan_destroy(h)
     assert i["products_executed"] == 7 * levels - 2
-    assert i["launches"] == i["products_executed"] + 1 + levels
+    assert i["launches"] == i["products_executed"] + 1
     hb = C.neumann_plan_create_batched(64, 256, k, radix, C.SPLIT_BF16, 0)
     try:
         ib = C.neumann_plan_info(hb)
