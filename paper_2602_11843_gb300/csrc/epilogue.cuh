@@ -943,6 +943,7 @@ __device__ __forceinline__ bool epi_chunk_fast(const EpiParams& P, const EpiCtx&
                                                int lane, int sym, bool edge, const SxTile* t) {
   if (P.f64_in < 0 && P.nf32 <= 1) return epi_chunk_lean<kF16, 32, 1, false>(P, x, rbase, c, stg, lane, sym, edge, t);
   if (P.f64_in < 0 && P.nf32 == 2) return epi_chunk_lean<kF16, 16, 2, false>(P, x, rbase, c, stg, lane, sym, edge, t);
+  if (P.f64_in < 0) return epi_chunk_lean<kF16, 8, kMaxIn, false>(P, x, rbase, c, stg, lane, sym, edge, t);
   return epi_chunk_lean<kF16, 8, kMaxIn, true>(P, x, rbase, c, stg, lane, sym, edge, t);
 }
 
