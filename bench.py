@@ -658,7 +658,9 @@ def run_ours(args, wl, sub=False):
     A = torch.tensor(A_np, dtype=io, device=dev)
     S = torch.empty_like(A)
     stream = torch.cuda.current_stream(dev)
-    if not args.no_autotune:
+    if args.launch:
+        plan.set_launch(*args.launch)  # a hand-set launch configuration instead of the autotuner's
+    elif not args.no_autotune:
         plan.autotune(A, out=S, reps=2)  # the library's autotuner picks tiles and raster
     for _ in range(args.warmup):
         plan(A, out=S)
@@ -689,6 +691,8 @@ def run_ours(args, wl, sub=False):
 
     # repeated squaring on the same input and arithmetic (the paper's binary comparator)
     sq = nm.Plan(n, wl["sq_k"], 2, wl["dtype"], pflags)
+    if args.launch:
+        sq.set_launch(*args.launch)
     for _ in range(args.warmup):
         sq(A, out=S)
     torch.cuda.synchronize()
@@ -813,7 +817,8 @@ def run_ours(args, wl, sub=False):
                             "2-CTA 256x256, upper triangle mirrored" if wl.get("symmetric") else
                             "2-CTA 256x128, chunked accumulation" if pflags else
                             ("2-CTA 256x256" if info["tile_pair"] else "1-CTA 128x256"),
-                   "raster_group": info["raster_group"] or None, "autotuned": bool(info["tuned"]),
+                   "raster_group": info["raster_group"] or None,
+                   "autotuned": bool(info["tuned"]) and not args.launch,
                    "parallelism": f"replicas x{world}"},
         "vs_squaring": {"k": wl["sq_k"], "ms_per_step": sq_ms, "speedup": sq_ms / (ms_max / args.steps),
                         "products_executed": sq.info["products_executed"],
@@ -895,6 +900,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch configuration")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison evaluation")
+    ap.add_argument("--launch", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    metavar="PAIR,GROUP",
+                    help="split single workloads: set the tile pair (-1/0/1) and raster group by hand")
     ap.add_argument("--fp64-large", action="store_true", help="run the FP64 comparison on the n = 16384 workload")
     ap.add_argument("--no-resident", action="store_true",
                     help="batched workloads: every matrix through the grouped launches (no resident launch)")

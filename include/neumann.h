@@ -271,6 +271,17 @@ int neumann_last_status(neumann_plan_t plan, unsigned* status);
 int neumann_plan_autotune(neumann_plan_t plan, const void* A, int64_t lda, void* S, int64_t lds, int reps,
                           void* stream);
 
+/* Set a split-dtype single plan's launch configuration by hand, as
+ * neumann_plan_autotune would: tile_pair -1 (CTA pairs from padded order 4096),
+ * 0 (1-CTA tiles) or 1 (2-CTA pairs; ignored under NEUMANN_FLAG_SINGLE_CTA,
+ * and precise or symmetric plans always use pairs); raster_group 1 .. 65535
+ * row tiles. Marks the plan tuned without recording the choice for other
+ * plans. Host-only (re-encodes the tensor maps of an attached workspace; no
+ * launch, no synchronisation).
+ * Errors: NEUMANN_EINVAL (batched, FP32 or FP64 plans; values out of range),
+ * NEUMANN_ECUDA (tensor-map encoding). */
+int neumann_plan_set_launch(neumann_plan_t plan, int tile_pair, int raster_group);
+
 /* Autotuner for a batched plan: arguments as neumann_eval_batched plus reps.
  * For a grouped plan (max_n <= 256) it times first the largest order the
  * resident launch takes (0, 16, 32, 48 and the most it holds; the rest run

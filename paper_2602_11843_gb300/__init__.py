@@ -86,6 +86,12 @@ class Plan:
         self.info = neumann_plan_info(self.handle)
         return self.info
 
+    def set_launch(self, tile_pair: int, raster_group: int):
+        """Set the launch configuration by hand (split dtypes): see neumann_plan_set_launch."""
+        neumann_plan_set_launch(self.handle, tile_pair, raster_group)
+        self.info = neumann_plan_info(self.handle)
+        return self.info
+
     def status(self) -> int:
         return neumann_last_status(self.handle)
 

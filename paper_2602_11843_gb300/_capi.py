@@ -84,6 +84,7 @@ def _load():
                                            c_void_p]),
         "neumann_matmul_noalloc_status": (c_int, [c_void_p, POINTER(c_uint32)]),
         "neumann_plan_autotune": (c_int, [P, c_void_p, c_int64, c_void_p, c_int64, c_int, c_void_p]),
+        "neumann_plan_set_launch": (c_int, [P, c_int, c_int]),
         "neumann_plan_autotune_batched": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_void_p), POINTER(c_void_p),
                                                   c_int, c_void_p]),
         "neumann_measure_fma_peak": (c_int, [c_int, POINTER(c_double), POINTER(c_int), c_void_p]),
@@ -173,6 +174,10 @@ def neumann_eval_batched(plan: int, n, A, S, stream: int = 0) -> None:
 
 def neumann_plan_autotune(plan: int, A: int, lda: int, S: int, lds: int, reps: int = 3, stream: int = 0) -> None:
     _check(_lib.neumann_plan_autotune(plan, A, lda, S, lds, reps, stream), "neumann_plan_autotune")
+
+
+def neumann_plan_set_launch(plan: int, tile_pair: int, raster_group: int) -> None:
+    _check(_lib.neumann_plan_set_launch(plan, tile_pair, raster_group), "neumann_plan_set_launch")
 
 
 def neumann_plan_autotune_batched(plan: int, n, A, S, reps: int = 3, stream: int = 0) -> None:

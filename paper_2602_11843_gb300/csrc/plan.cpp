@@ -1691,7 +1691,10 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
 // plans of the same shape start from them: single tensor-core products by
 // (padded order, dtype); grouped batches by (count, max order, k, radix, dtype).
 std::mutex g_tune_mu;
-std::map<std::pair<int64_t, int>, std::pair<int, int>> g_tune_single;
+struct TuneSingle {
+  int pair, group;
+};
+std::map<std::pair<int64_t, int>, TuneSingle> g_tune_single;
 std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int, int>> g_tune_batched;  // chunk, resident limit
 
 // Single products are keyed by padded order and dtype; precise-accumulation
@@ -1712,8 +1715,8 @@ void apply_tuned(neumann_plan_s* p) {
   } else if (p->path == PATH_TC) {
     auto it = g_tune_single.find(tune_key(p));
     if (it != g_tune_single.end()) {
-      p->tune_pair = it->second.first;
-      p->tune_group = it->second.second;
+      p->tune_pair = it->second.pair;
+      p->tune_group = it->second.group;
       p->tuned = true;
     }
   }
@@ -1760,17 +1763,17 @@ int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t
   if (rc) return rc;
   EventPair ev;
   if (!ev.ok()) return NEUMANN_ECUDA;
-  std::vector<std::pair<int, int>> cand;
+  std::vector<TuneSingle> cand;
   const bool precise = (p->flags & NEUMANN_FLAG_PRECISE_ACC) != 0 || p->sym;  // always CTA pairs
   for (int pair = precise ? 1 : 0; pair <= 1; ++pair) {
     if (pair && (p->flags & NEUMANN_FLAG_SINGLE_CTA) && !precise) continue;
-    for (int g : {4, 8, 16}) cand.emplace_back(pair, g);
+    for (int g : {4, 8, 16}) cand.push_back({pair, g});
   }
   float best = 0.f;
-  std::pair<int, int> pick = cand[0];
+  TuneSingle pick = cand[0];
   for (size_t i = 0; i < cand.size(); ++i) {
-    p->tune_pair = cand[i].first;
-    p->tune_group = cand[i].second;
+    p->tune_pair = cand[i].pair;
+    p->tune_group = cand[i].group;
     if (!build_maps(p, p->ops, &p->maps, p->sym) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
     float ms = 0.f;
     rc = time_runs([&] { return eval_one(p, A, lda, S, lds, s); }, reps, s, ev.e0, ev.e1, &ms);
@@ -1780,8 +1783,8 @@ int autotune_one(neumann_plan_s* p, const void* A, int64_t lda, void* S, int64_t
       pick = cand[i];
     }
   }
-  p->tune_pair = pick.first;
-  p->tune_group = pick.second;
+  p->tune_pair = pick.pair;
+  p->tune_group = pick.group;
   if (!build_maps(p, p->ops, &p->maps, p->sym) || !build_maps(p, p->mm_ops, &p->mm_maps)) return NEUMANN_ECUDA;
   p->timed = 0;  // tuning runs are not part of a NEUMANN_FLAG_TIMING record
   p->tuned = true;
@@ -1914,6 +1917,18 @@ int neumann_plan_autotune(neumann_plan_t p, const void* A, int64_t lda, void* S,
   } catch (...) {
     return NEUMANN_ENOMEM;
   }
+}
+
+int neumann_plan_set_launch(neumann_plan_t p, int tile_pair, int raster_group) {
+  if (!p || p->batched || p->path != PATH_TC || tile_pair < -1 || tile_pair > 1 || raster_group < 1 ||
+      raster_group > 65535)
+    return NEUMANN_EINVAL;
+  p->tune_pair = tile_pair;
+  p->tune_group = raster_group;
+  p->tuned = true;
+  if (p->ws && (!build_maps(p, p->ops, &p->maps, p->sym) || !build_maps(p, p->mm_ops, &p->mm_maps)))
+    return NEUMANN_ECUDA;
+  return NEUMANN_OK;
 }
 
 int neumann_plan_autotune_batched(neumann_plan_t p, int count, const int64_t* n, const void* const* A,

@@ -181,6 +181,31 @@ def test_launch_configuration_defaults():
         C.neumann_plan_destroy(h)
 
 
+def test_set_launch_host_only():
+    """A hand-set launch configuration shows in the plan's info; out-of-range
+    values and plans without tensor-core products are refused. No workspace is
+    attached, so nothing touches a device."""
+    h = C.neumann_plan_create(8192, 3375, 15, C.SPLIT_BF16, 0)
+    h32 = C.neumann_plan_create(64, 81, 9, C.FP32, 0)
+    hb = C.neumann_plan_create_batched(4, 64, 81, 9, C.SPLIT_BF16, 0)
+    try:
+        i = C.neumann_plan_info(h)
+        assert (i["tile_pair"], i["raster_group"], i["tuned"]) == (1, 8, 0)
+        C.neumann_plan_set_launch(h, 0, 4)
+        i = C.neumann_plan_info(h)
+        assert (i["tile_pair"], i["raster_group"], i["tuned"]) == (0, 4, 1)
+        C.neumann_plan_set_launch(h, -1, 16)
+        i = C.neumann_plan_info(h)
+        assert (i["tile_pair"], i["raster_group"]) == (1, 16)
+        for args in [(h, 2, 8), (h, 1, 0), (h, 1, 1 << 16), (h, -2, 8), (h32, 1, 8), (hb, 1, 8)]:
+            with pytest.raises(C.NeumannError) as e:
+                C.neumann_plan_set_launch(*args)
+            assert e.value.code == C.EINVAL
+    finally:
+        for x in (h, h32, hb):
+            C.neumann_plan_destroy(x)
+
+
 def test_autotune_argument_errors():
     """Rejected before any device work."""
     h = C.neumann_plan_create(64, 81, 9, C.SPLIT_BF16, 0)
