@@ -233,8 +233,10 @@ int sm_count();
 // The CUDA cores' FMA rate (FP32, or FP64 when f64), TFLOP/s: the best of three
 // timed launches of independent FMA chains on every SM (synchronises `s`).
 cudaError_t measure_fma_peak(int f64, double* tflops, cudaStream_t s);
+// K depth of one shared-memory stage of the SIMT product: 16 (FP32) or 8 (FP64).
+constexpr int simt_bk(bool f64) { return f64 ? 8 : 16; }
 // tiles == nullptr: one padded npad x npad product. Otherwise a grouped launch
-// over a batch: ntiles entries {matrix, tile row, tile column, K steps of 8}.
+// over a batch: ntiles entries {matrix, tile row, tile column, K steps of simt_bk}.
 // sym (single products only): the product is symmetric; only the 128 x 128
 // tiles on or above the diagonal run, writing their transposes too.
 cudaError_t launch_simt_gemm_f64(const double* A, const double* B, int64_t ld, int64_t npad, const int4* tiles,

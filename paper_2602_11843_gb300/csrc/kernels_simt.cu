@@ -16,7 +16,8 @@ namespace neumann {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 8, TPB = 256;
+constexpr int BM = 128, BN = 128, TPB = 256;
+static_assert(simt_bk(true) == 8 && simt_bk(false) == 16, "SIMT stage depth differs from the tile tables");
 
 __device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
   float4 t = *reinterpret_cast<const float4*>(p);
@@ -27,6 +28,17 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
   double2 t1 = reinterpret_cast<const double2*>(p)[1];
   v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
 }
+// Four consecutive shared-memory elements: one 16-byte store for FP32 (a warp's
+// 32 consecutive runs then fill 512 bytes without a bank conflict).
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) p[j] = v[j];
+}
+
+constexpr int kFlushK = 128;  // FP32: k per partial sum of the two-level accumulation
 
 // tiles == nullptr: one matrix, CTA (blockIdx.y, blockIdx.x) computes tile
 // (tm, tn) over `ktiles` K steps. Otherwise (grouped launch over a batch) CTA b
@@ -38,11 +50,18 @@ template <typename T>
 __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
     simt_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, int64_t ld, int ktiles,
                      const int4* __restrict__ tiles, int sym, const __grid_constant__ EpiParams P) {
+  // K depth of a shared-memory stage: 16 for FP32 (fewer barriers per FMA), 8
+  // for FP64 (static shared memory is limited to 48 KB)
+  constexpr int BK = sizeof(T) == 8 ? 8 : 16;
+  constexpr int V = BK / 8;  // 4-element runs a thread loads per operand and stage
   __shared__ __align__(16) T As[2][BK][BM + 4];
   __shared__ __align__(16) T Bs[2][BK][BN];
   extern __shared__ float acc_smem[];  // FP32: running sums, [64][TPB] (element e of thread t at e * TPB + t)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
+  // FP32: two-level accumulation (below); kFlush K steps per partial sum
+  constexpr bool kTwoLevel = sizeof(T) == 4;
+  constexpr int kFlush = kFlushK / BK;
   int mat = 0, tm = blockIdx.y, tn = blockIdx.x;
   if (sym) {
     // a symmetric product (every matrix of the scheme is a polynomial in the
@@ -67,34 +86,48 @@ __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
   }
   const EpiCtx x = epi_ctx(P, mat);
   const int m0 = tm * BM, n0 = tn * BN;
-  const int a_row = tid >> 1, a_col = (tid & 1) * 4;   // A tile: 128 rows x 8
-  const int b_row = tid >> 5, b_col = (tid & 31) * 4;  // B tile: 8 rows x 128
+  // A tile: 128 rows x BK as runs of 4 k; run v of a thread is row tid % 128,
+  // k from 4 (tid / 128 + 2 v), stored transposed (As[k][row]): a warp's 32
+  // consecutive rows land in 32 banks. B tile: BK rows x 128 as runs of 4
+  // columns; run v of a thread is row tid / 32 + 8 v, columns 4 (tid % 32) ..:
+  // a warp reads and stores 512 contiguous bytes of one row.
+  const int a_row = tid & (BM - 1), a_col = 4 * (tid / BM);
+  const int b_row = tid >> 5, b_col = (tid & 31) * 4;
   const T* Ap = A + (int64_t)(m0 + a_row) * ld + a_col;
   const T* Bp = B + (int64_t)b_row * ld + n0 + b_col;
 
+  // next stage's operands: one 4-element run of A and of B at a time (V runs a
+  // stage), stored into the free buffer before the next run is fetched, which
+  // keeps 8 registers in flight whatever BK is
   T ra[4], rb[4];
-  load4(Ap, ra);
-  load4(Bp, rb);
+  auto fetch = [&](int kt, int v) {
+    load4(Ap + (int64_t)kt * BK + 8 * v, ra);
+    load4(Bp + ((int64_t)kt * BK + 8 * v) * ld, rb);
+  };
+  auto stash = [&](int buf, int v) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    As[0][a_col + j][a_row] = ra[j];
-    Bs[0][b_row][b_col + j] = rb[j];
+    for (int j = 0; j < 4; ++j) As[buf][a_col + 8 * v + j][a_row] = ra[j];
+    store4(&Bs[buf][b_row + 8 * v][b_col], rb);
+  };
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    fetch(0, v);
+    stash(0, v);
   }
   __syncthreads();
 
-  // FP32: two-level accumulation. Products are summed into `part` for 64
+  // FP32: two-level accumulation. Products are summed into `prt` for 128
   // consecutive k and then added to the running sum, so each rounding error
-  // grows with sqrt(64) + sqrt(K/64) instead of sqrt(K) (K = 4096: 16 vs 64
-  // units). The running sums live in shared memory (touched once per 64 k),
-  // which keeps the kernel within 128 registers.
-  constexpr bool kTwoLevel = sizeof(T) == 4;
-  constexpr int kFlush = 64 / BK;  // k tiles per partial sum
-  T acc[kTwoLevel ? 1 : 8][kTwoLevel ? 1 : 8], part[8][8];
+  // grows with sqrt(128) + sqrt(K/128) instead of sqrt(K) (K = 4096: 17 vs 64
+  // units; 64 k per partial sum gave 16 and took 3.6 % longer). The running
+  // sums live in shared memory (touched once per 128 k), which keeps the
+  // kernel within 128 registers.
+  T acc[kTwoLevel ? 1 : 8][kTwoLevel ? 1 : 8], prt[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      part[i][j] = T(0);
+      prt[i][j] = T(0);
       if constexpr (kTwoLevel)
         acc_smem[(i * 8 + j) * TPB + tid] = 0.f;
       else
@@ -104,12 +137,14 @@ __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
   for (int kt = 0; kt < ktiles; ++kt) {
     const int cur = kt & 1;
     const bool more = kt + 1 < ktiles;
-    if (more) {
-      load4(Ap + (int64_t)(kt + 1) * BK, ra);
-      load4(Bp + (int64_t)(kt + 1) * BK * ld, rb);
-    }
+    // buffer cur ^ 1 was last read before the previous barrier: free to fill
+    if (more) fetch(kt + 1, 0);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
+      if (V > 1 && kk > 0 && kk % 8 == 0 && more) {
+        stash(cur ^ 1, kk / 8 - 1);
+        fetch(kt + 1, kk / 8);
+      }
       T a[8], b[8];
       T t[4];
       load4(&As[cur][kk][ty * 4], t);
@@ -129,7 +164,7 @@ __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           if constexpr (kTwoLevel)
-            part[i][j] = fma(a[i], b[j], part[i][j]);
+            prt[i][j] = fma(a[i], b[j], prt[i][j]);
           else
             acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
@@ -140,18 +175,12 @@ __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 2 : 1)
         for (int i = 0; i < 8; ++i)
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            acc_smem[(i * 8 + j) * TPB + tid] += part[i][j];
-            part[i][j] = T(0);
+            acc_smem[(i * 8 + j) * TPB + tid] += prt[i][j];
+            prt[i][j] = T(0);
           }
       }
     }
-    if (more) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        As[cur ^ 1][a_col + j][a_row] = ra[j];
-        Bs[cur ^ 1][b_row][b_col + j] = rb[j];
-      }
-    }
+    if (more) stash(cur ^ 1, V - 1);
     __syncthreads();
   }
 
@@ -450,15 +479,16 @@ cudaError_t launch_simt(const T* A, const T* B, int64_t ld, int64_t npad, const 
     });
     if (attr != cudaSuccess) return attr;
   }
+  const int ktiles = (int)(npad / simt_bk(sizeof(T) == 8));
   if (tiles) {
     if (ntiles <= 0) return cudaSuccess;
     simt_gemm_kernel<T><<<ntiles, TPB, dyn, s>>>(A, B, ld, 0, tiles, 0, P);
   } else if (sym) {
     const int t = (int)(npad / BM);
-    simt_gemm_kernel<T><<<t * (t + 1) / 2, TPB, dyn, s>>>(A, B, ld, (int)(npad / BK), nullptr, t, P);
+    simt_gemm_kernel<T><<<t * (t + 1) / 2, TPB, dyn, s>>>(A, B, ld, ktiles, nullptr, t, P);
   } else {
     dim3 grid((unsigned)(npad / BN), (unsigned)(npad / BM));
-    simt_gemm_kernel<T><<<grid, TPB, dyn, s>>>(A, B, ld, (int)(npad / BK), nullptr, 0, P);
+    simt_gemm_kernel<T><<<grid, TPB, dyn, s>>>(A, B, ld, ktiles, nullptr, 0, P);
   }
   return cudaGetLastError();
 }

@@ -1536,6 +1536,7 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
     std::vector<const void*> atab(count);
     std::vector<void*> stab(count);
     std::vector<int4> tc, simt, ew;
+    const int kbk = simt_bk(p->path == PATH_F64);  // K depth of a SIMT stage
     p->chunks.clear();
     for (int k = 0; k < nres; ++k) {  // resident tables after the grouped ones' entries
       const int i = order[ng + k];
@@ -1556,7 +1557,7 @@ int eval_grouped(neumann_plan_s* p, int count, const int64_t* n, const void* con
         const int mt = (ni + 127) / 128;  // 128-row tiles
         for (int tm = 0; tm < mt; ++tm) tc.push_back(make_int4(j, tm, (ni + 31) / 32, 0));
         for (int tm = 0; tm < mt; ++tm)
-          for (int tn = 0; tn < mt; ++tn) simt.push_back(make_int4(j, tm, tn, (ni + 7) / 8));
+          for (int tn = 0; tn < mt; ++tn) simt.push_back(make_int4(j, tm, tn, (ni + kbk - 1) / kbk));
         // element-wise passes, like the products, write rows and columns below the
         // order rounded up to 32: the K padding every later product reads
         for (int tr = 0; tr < (ni + 31) / 32; ++tr)
