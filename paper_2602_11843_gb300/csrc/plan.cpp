@@ -275,6 +275,32 @@ struct Sched {
   // Kernel ops for G = f(R) - I. The last product also writes G (with greps)
   // and, when ytarget != SL_NONE, the first partial sum Y = I + G.
   void kernel(int m, int R, uint32_t greps, int ytarget, uint32_t yreps) {
+    // The radix-15 and five-product circuits: after P2, C = g1 B + g2 P1 + g3 P2
+    // holds P2's share, so a combination c1 B + c2 P1 + c3 P2 that P3's
+    // epilogue forms equals (c1 - t g1) B + (c2 - t g2) P1 + t C with t = c3 / g3,
+    // and P3 reads (B, P1, C) instead of (B, P1, P2, C). This multiplies C's FP32
+    // rounding by |t| (at most 4.8 over the kernels built, 0.21 for radix 15);
+    // where some |t| would exceed kSubMax, P3 reads P2 as stored.
+    constexpr double kSubMax = 16.0;
+    auto p2_via_c = [&](const double* g, std::initializer_list<double> c3) {
+      if (g[2] == 0.0) return false;
+      for (double c : c3)
+        if (std::fabs(c / g[2]) > kSubMax) return false;
+      return true;
+    };
+    // in[0..2] of an output of P3 over the inputs (B, P1, C) or (B, P1, P2, C)
+    auto comb3 = [](OutSpec& o, bool via_c, const double* g, double c1, double c2, double c3) {
+      if (via_c) {
+        const double t = c3 / g[2];
+        o.in[0] = c1 - t * g[0];
+        o.in[1] = c2 - t * g[1];
+        o.in[2] = t;
+      } else {
+        o.in[0] = c1;
+        o.in[1] = c2;
+        o.in[2] = c3;
+      }
+    };
     auto tail = [&](Op& op, double acc, std::initializer_list<double> ins) {
       // G = sum ins * inputs + acc * product; Y = I + G
       if (greps) {
@@ -336,6 +362,7 @@ struct Sched {
     } else if (m == 15) {  // Sec. 4.1, eq. factors / radix15kernel
       const double* x = p->c15;
       const double *l2 = x, *r2 = x + 3, *l3 = x + 6, *r3 = x + 10, *l4 = x + 14, *r4 = x + 19, *g = x + 24;
+      const bool via_c = p2_via_c(g, {l4[3], r4[3]});
       // P1 = B B; L2, R2 over (I, B, P1)
       Op op1 = mk_gemm(R, R);
       add_in(op1, R, REP_W);
@@ -343,11 +370,12 @@ struct Sched {
       add_out(op1, SL_LF0, REP_OPA, l2[2], l2[0]).in[0] = l2[1];
       add_out(op1, SL_RF0, REP_OPB, r2[2], r2[0]).in[0] = r2[1];
       ops().push_back(op1);
-      // P2 = L2 R2; L3, R3 over (I, B, P1, P2); C = g1 B + g2 P1 + g3 P2
+      // P2 = L2 R2; L3, R3 over (I, B, P1, P2); C = g1 B + g2 P1 + g3 P2 (P2
+      // itself is stored only when P3 cannot read its share from C)
       Op op2 = mk_gemm(SL_LF0, SL_RF0);
       add_in(op2, R, REP_W);
       add_in(op2, SL_P1, REP_W);
-      add_out(op2, SL_P2, REP_W, 1.0, 0.0);
+      if (!via_c) add_out(op2, SL_P2, REP_W, 1.0, 0.0);
       {
         OutSpec& L = add_out(op2, SL_LF1, REP_OPA, l3[3], l3[0]);
         L.in[0] = l3[1];
@@ -364,19 +392,12 @@ struct Sched {
       Op op3 = mk_gemm(SL_LF1, SL_RF1);
       add_in(op3, R, REP_W);
       add_in(op3, SL_P1, REP_W);
-      add_in(op3, SL_P2, REP_W);
+      if (!via_c) add_in(op3, SL_P2, REP_W);
       add_in(op3, SL_C, REP_W);
       {
-        OutSpec& L = add_out(op3, SL_LF0, REP_OPA, l4[4], l4[0]);
-        L.in[0] = l4[1];
-        L.in[1] = l4[2];
-        L.in[2] = l4[3];
-        OutSpec& Rr = add_out(op3, SL_RF0, REP_OPB, r4[4], r4[0]);
-        Rr.in[0] = r4[1];
-        Rr.in[1] = r4[2];
-        Rr.in[2] = r4[3];
-        OutSpec& C = add_out(op3, SL_C, REP_W, g[3], 0.0);
-        C.in[3] = 1.0;
+        comb3(add_out(op3, SL_LF0, REP_OPA, l4[4], l4[0]), via_c, g, l4[1], l4[2], l4[3]);
+        comb3(add_out(op3, SL_RF0, REP_OPB, r4[4], r4[0]), via_c, g, r4[1], r4[2], r4[3]);
+        add_out(op3, SL_C, REP_W, g[3], 0.0).in[via_c ? 2 : 3] = 1.0;
       }
       ops().push_back(op3);
       // P4 = L4 R4; G = C + P4 (T~15 = I + G)
@@ -388,6 +409,8 @@ struct Sched {
       const double* x = p->cp5;
       const double *l2 = x, *r2 = x + 3, *l3 = x + 6, *r3 = x + 10, *l4 = x + 14, *r4 = x + 19;
       const double *l5 = x + 24, *r5 = x + 30, *g = x + 36;
+      const bool fold = p->grouped;
+      const bool via_c = fold ? p2_via_c(g, {l4[3], r4[3], l5[3], r5[3]}) : p2_via_c(g, {l4[3], r4[3]});
       // P1 = B B; L2, R2 over (I, B, P1)
       Op op1 = mk_gemm(R, R);
       add_in(op1, R, REP_W);
@@ -395,11 +418,13 @@ struct Sched {
       add_out(op1, SL_LF0, REP_OPA, l2[2], l2[0]).in[0] = l2[1];
       add_out(op1, SL_RF0, REP_OPB, r2[2], r2[0]).in[0] = r2[1];
       ops().push_back(op1);
-      // P2 = L2 R2; L3, R3 over (I, B, P1, P2); C = g1 B + g2 P1 + g3 P2
+      // P2 = L2 R2; L3, R3 over (I, B, P1, P2); C = g1 B + g2 P1 + g3 P2. A
+      // single plan's fourth product (or element-wise pass) reads P2; a grouped
+      // batch's reads it only through C.
       Op op2 = mk_gemm(SL_LF0, SL_RF0);
       add_in(op2, R, REP_W);
       add_in(op2, SL_P1, REP_W);
-      add_out(op2, SL_P2, REP_W, 1.0, 0.0);
+      if (!(fold && via_c)) add_out(op2, SL_P2, REP_W, 1.0, 0.0);
       {
         OutSpec& L = add_out(op2, SL_LF1, REP_OPA, l3[3], l3[0]);
         L.in[0] = l3[1];
@@ -422,32 +447,20 @@ struct Sched {
       // (B, P1, P2, C) and P4: P3 is not stored and no element-wise pass runs.
       // The substitution multiplies C's FP32 rounding by |l5_4 / g4| (6.8 at
       // most over radix 24-33); above 16, P3 is stored and a pass forms the parts.
-      const bool fold = p->grouped;
-      const double kSubMax = 16.0;
       const bool subst = !fold && std::fabs(g[3]) > 0.0 && std::fabs(l5[4] / g[3]) <= kSubMax &&
                          std::fabs(r5[4] / g[3]) <= kSubMax;
       Op op3 = mk_gemm(SL_LF1, SL_RF1);
       add_in(op3, R, REP_W);
       add_in(op3, SL_P1, REP_W);
-      add_in(op3, SL_P2, REP_W);
+      if (!via_c) add_in(op3, SL_P2, REP_W);
       add_in(op3, SL_C, REP_W);
       {
-        OutSpec& L = add_out(op3, SL_LF0, REP_OPA, l4[4], l4[0]);
-        L.in[0] = l4[1];
-        L.in[1] = l4[2];
-        L.in[2] = l4[3];
-        OutSpec& Rr = add_out(op3, SL_RF0, REP_OPB, r4[4], r4[0]);
-        Rr.in[0] = r4[1];
-        Rr.in[1] = r4[2];
-        Rr.in[2] = r4[3];
-        add_out(op3, SL_C, REP_W, g[3], 0.0).in[3] = 1.0;
+        comb3(add_out(op3, SL_LF0, REP_OPA, l4[4], l4[0]), via_c, g, l4[1], l4[2], l4[3]);
+        comb3(add_out(op3, SL_RF0, REP_OPB, r4[4], r4[0]), via_c, g, r4[1], r4[2], r4[3]);
+        add_out(op3, SL_C, REP_W, g[3], 0.0).in[via_c ? 2 : 3] = 1.0;
         if (fold) {
-          OutSpec& L5 = add_out(op3, SL_Q5L, REP_W, l5[4], l5[0]);
-          OutSpec& R5 = add_out(op3, SL_Q5R, REP_W, r5[4], r5[0]);
-          for (int j = 0; j < 3; ++j) {
-            L5.in[j] = l5[1 + j];
-            R5.in[j] = r5[1 + j];
-          }
+          comb3(add_out(op3, SL_Q5L, REP_W, l5[4], l5[0]), via_c, g, l5[1], l5[2], l5[3]);
+          comb3(add_out(op3, SL_Q5R, REP_W, r5[4], r5[0]), via_c, g, r5[1], r5[2], r5[3]);
         } else if (!subst) {
           add_out(op3, SL_P3, REP_W, 1.0, 0.0);
         }
