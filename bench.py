@@ -79,10 +79,10 @@ DEFAULT_WORKLOAD = "precision-r15-bf16-n8192-k3375"
 
 # DRAM bytes (read + write) per launch of the tensor-core product, the mean over
 # the 16 launches of one evaluation of the named workload, from one ncu capture
-# (profiles/tc_split_gemm_n8192_r15_bench.md). Valid for the kernel sources
-# whose SHA-1 prefix (of the code without comments) is recorded beside it;
-# reported as null otherwise.
-TC_TRAFFIC = {"sha1": "90a87fb7ce26", "workload": "precision-r15-bf16-n8192-k3375", "bytes_per_launch": 4.0957e9}
+# (profiles/tc_split_gemm_n8192_r15_bench.md). Valid for the kernel and schedule
+# sources whose SHA-1 prefix (of the code without comments) is recorded beside
+# it; reported as null otherwise.
+TC_TRAFFIC = {"sha1": "24f939c55b3e", "workload": "precision-r15-bf16-n8192-k3375", "bytes_per_launch": 3.7544e9}
 
 
 def _peaks():
@@ -775,7 +775,7 @@ def run_ours(args, wl, sub=False):
             r = live_peaks(dev)["fp16_over_bf16"]
             peak *= r
             peak_source += f" x {r:.3f} (cuBLAS FP16 / BF16 GEMM rate measured in this run)"
-        sha = _src_sha("kernels_tc.cu", "epilogue.cuh")
+        sha = _src_sha("kernels_tc.cu", "epilogue.cuh", "plan.cpp")  # plan.cpp: the ops' inputs and outputs
         traffic = (TC_TRAFFIC["bytes_per_launch"]
                    if TC_TRAFFIC["sha1"] == sha and args.workload == TC_TRAFFIC["workload"] else None)
         roof = {"bound": "tensor", "achieved": flops / (mean_prod_ms / 1e3) / 1e12, "peak": peak,
