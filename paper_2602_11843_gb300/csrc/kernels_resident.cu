@@ -110,33 +110,44 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
         }
         const float sa = ldexpf(1.f, ea), sb = ldexpf(1.f, eb);
         if (act) {
-#pragma unroll 2
-          for (int q = 0; q < n; ++q) {
-            float a[4], b[4];
+          // k in steps of 4: the left operand as one 16-byte run of each of the
+          // block's 4 rows (at ld = 32 a warp's 4 row groups share one set of
+          // banks, so scalar loads of a column conflict 4 ways); the padding
+          // columns n .. ld-1 hold zeros and add nothing
+#pragma unroll 1
+          for (int q4 = 0; q4 < ld; q4 += 4) {
+            float4 av[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = L[(r0 + i) * ld + q];
-            const float4 bv = *reinterpret_cast<const float4*>(R + q * ld + c0);
-            b[0] = bv.x;
-            b[1] = bv.y;
-            b[2] = bv.z;
-            b[3] = bv.w;
-            if (MODE == 0) {
+            for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(L + (r0 + i) * ld + q4);
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              float a[4], b[4];
 #pragma unroll
               for (int i = 0; i < 4; ++i)
+                a[i] = qq == 0 ? av[i].x : qq == 1 ? av[i].y : qq == 2 ? av[i].z : av[i].w;
+              const float4 bv = *reinterpret_cast<const float4*>(R + (q4 + qq) * ld + c0);
+              b[0] = bv.x;
+              b[1] = bv.y;
+              b[2] = bv.z;
+              b[3] = bv.w;
+              if (MODE == 0) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            } else {
-              float ah[4], al[4], bh[4], bl[4];
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                res_split<MODE>(a[i], sa, &ah[i], &al[i]);
-                res_split<MODE>(b[i], sb, &bh[i], &bl[i]);
+                  for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+              } else {
+                float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  res_split<MODE>(a[i], sa, &ah[i], &al[i]);
+                  res_split<MODE>(b[i], sb, &bh[i], &bl[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                  for (int j = 0; j < 4; ++j)
+                    acc[i][j] = fmaf(al[i], bh[j], fmaf(ah[i], bl[j], fmaf(ah[i], bh[j], acc[i][j])));
               }
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                  acc[i][j] = fmaf(al[i], bh[j], fmaf(ah[i], bl[j], fmaf(ah[i], bh[j], acc[i][j])));
             }
           }
           if (MODE == 2) {
@@ -207,13 +218,16 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
 #pragma unroll
                 for (int ii = 0; ii < kMaxIn; ++ii)
                   if (ii < op.nin && !is64[ii] && op.in_f[o][ii] != 0.f) tt = fmaf(op.in_f[o][ii], (float)vin[ii][j], tt);
-                double d = (double)tt + (diag ? idd : 0.0);
+                // (FP64 runs at 1/64 of FP32: the identity is added on the
+                // diagonal only, and finiteness is read from the FP32 copy)
+                double d = (double)tt;
+                if (diag) d += idd;
 #pragma unroll
                 for (int ii = 0; ii < kMaxIn; ++ii)
                   if (ii < op.nin && is64[ii] && op.in_d[o][ii] != 0.0) d = fma(op.in_d[o][ii], vin[ii][j], d);
                 v[j] = live[j] ? d : 0.0;
                 vf[j] = (float)v[j];
-                bad |= !isfinite(d);
+                bad |= !isfinite(vf[j]);
               } else {
                 float t2 = af * acc[i][j] + (diag ? idf : 0.f);
 #pragma unroll
