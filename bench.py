@@ -63,6 +63,8 @@ WORKLOADS = {
                                                 sq_k=4096, fp64=False, precise=True),
     "plain-r9-fp32-n4096-k729": dict(steps=50, cfg=2, n=4096, k=729, radix=9, dtype="fp32", sq_k=1024),
     "plain-r15-fp32-n4096-k225": dict(steps=64, cfg=2, n=4096, k=225, radix=15, dtype="fp32", sq_k=256),
+    # the default workload's input and k through the plain FP32 path (SIMT products)
+    "plain-r15-fp32-n8192-k3375": dict(steps=3, cfg=3, n=8192, k=3375, radix=15, dtype="fp32", sq_k=4096),
     "plain-r9-fp64-n4096-k729": dict(steps=3, cfg=2, n=4096, k=729, radix=9, dtype="fp64", sq_k=1024),
     # cfg 4: 4096 damped-Jacobi matrices, n uniform in {16, 32, ..., 256}; a step is one
     # grouped evaluation of the whole batch
@@ -845,6 +847,7 @@ def run_ours(args, wl, sub=False):
         del plan, sq, A, S, A_host, S_host
         torch.cuda.empty_cache()
         line.update(run_extras(args))
+        line["vs_fp32"] = vs_fp32(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -854,7 +857,26 @@ def run_ours(args, wl, sub=False):
 # Secondary workloads of the default run, each timed like its own --workload run
 # over a shorter region (steps), reported as keys of the default line.
 EXTRAS = (("radix9", "precision-r9-bf16-n8192-k6561", 20), ("precise", "precise-r15-bf16-n8192-k3375", 16),
-          ("batched", "batched-r9-bf16-4096-k81", 48))
+          ("batched", "batched-r9-bf16-4096-k81", 48), ("fp32", "plain-r15-fp32-n8192-k3375", 3))
+
+
+def vs_fp32(line):
+    """The split forms against the plain FP32 path on the same input and k, each
+    with its error against the oracle: whether they are faster at an error no
+    larger than the FP32 path's."""
+    f = line.get("fp32")
+    if not f:
+        return None
+
+    def err(d):
+        return (d.get("vs_oracle") or {}).get("rel_fro")
+
+    pr = line.get("precise", {})
+    return {"fp32_value": f["value"], "fp32_rel_fro": err(f),
+            "split_value": line["value"], "split_rel_fro": err(line),
+            "precise_value": pr.get("value"), "precise_rel_fro": err(pr),
+            "speedup_split": line["value"] / f["value"],
+            "speedup_precise": pr["value"] / f["value"] if pr.get("value") else None}
 
 
 def run_extras(args):
@@ -907,7 +929,7 @@ def main():
     ap.add_argument("--no-resident", action="store_true",
                     help="batched workloads: every matrix through the grouped launches (no resident launch)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="default workload only: skip the secondary workloads (radix 9, precise, batched)")
+                    help="default workload only: skip the secondary workloads (radix 9, precise, batched, FP32)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.steps is None:
