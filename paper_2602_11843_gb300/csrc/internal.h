@@ -290,10 +290,14 @@ struct ResParams {
 inline size_t resident_smem(int nslots, int nf64, int nops, int nmax) {
   return (size_t)nmax * nmax * (4 * (size_t)nslots + 8 * (size_t)nf64) + (size_t)nops * sizeof(ResOp);
 }
-// Threads of a CTA for order nmax: one per 4 x 4 output block, rounded up to warps.
+// Columns of a thread's output block for order nmax (its rows are 4): 1 up to
+// order 16, 2 up to 32, else 4.
+inline int resident_cw(int nmax) { return nmax <= 16 ? 1 : nmax <= 32 ? 2 : 4; }
+// Threads of a CTA for order nmax: one per 4 x resident_cw output block,
+// rounded up to warps.
 inline int resident_threads(int nmax) {
-  const int nb = (nmax + 3) / 4;
-  return (nb * nb + 31) / 32 * 32;
+  const int ld = (nmax + 3) / 4 * 4;
+  return ((ld / 4) * (ld / resident_cw(nmax)) + 31) / 32 * 32;
 }
 // The matrices of one launch in a persistent grid (as many CTAs as fit on the
 // device at once, at most one per matrix): CTA b runs matrices b, b + grid, ...,

@@ -72,7 +72,62 @@ __device__ __forceinline__ int res_exp(float amax) {
   return e < -kSxMaxExp ? -kSxMaxExp : e > kSxMaxExp ? kSxMaxExp : e;
 }
 
-template <int MODE>
+// CW consecutive elements of a row: vector loads and stores of 4, 2 or 1 values
+template <int CW>
+__device__ __forceinline__ void ld_row(const float* p, float (&v)[CW]) {
+  if constexpr (CW == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  } else if constexpr (CW == 2) {
+    const float2 x = *reinterpret_cast<const float2*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+  } else {
+    v[0] = *p;
+  }
+}
+template <int CW>
+__device__ __forceinline__ void ld_row(const double* p, double (&v)[CW]) {
+#pragma unroll
+  for (int j = 0; j < CW; j += 2) {
+    if (j + 1 < CW) {
+      const double2 x = *reinterpret_cast<const double2*>(p + j);
+      v[j] = x.x;
+      v[j + 1] = x.y;
+    } else {
+      v[j] = p[j];
+    }
+  }
+}
+template <int CW>
+__device__ __forceinline__ void st_row(float* p, const float (&v)[CW]) {
+  if constexpr (CW == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else if constexpr (CW == 2)
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  else
+    *p = v[0];
+}
+template <int CW>
+__device__ __forceinline__ void st_row(double* p, const double (&v)[CW]) {
+#pragma unroll
+  for (int j = 0; j < CW; j += 2) {
+    if (j + 1 < CW)
+      *reinterpret_cast<double2*>(p + j) = make_double2(v[j], v[j + 1]);
+    else
+      p[j] = v[j];
+  }
+}
+
+// Each thread holds a 4 x CW block of every output: CW = 4 for the largest
+// size class, 2 for orders up to 32 and 1 up to 16, so that a CTA runs 64-256
+// threads whatever the order (with 4 x 4 blocks an order-32 matrix had 64
+// threads, and the SM, at 3 CTAs for its shared memory, 6 warps: too few to
+// cover the latency of one matrix's chain of dependent steps).
+template <int MODE, int CW>
 __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_constant__ ResParams P) {
   // shared memory: FP64 copies | FP32 copies | program (16-byte aligned sections)
   extern __shared__ __align__(16) double smd[];
@@ -89,17 +144,17 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
   for (int m = blockIdx.x; m < P.count; m += gridDim.x) {
     const int n = P.mat_n[m];
     const int ld = (n + 3) & ~3;  // rows of each matrix in its slot; padding zero
-    const int nb = ld / 4;
-    const bool act = t < nb * nb;
-    const int r0 = act ? (t / nb) * 4 : 0, c0 = act ? (t % nb) * 4 : 0;
+    const int nbr = ld / 4, nbc = ld / CW;  // row and column blocks
+    const bool act = t < nbr * nbc;
+    const int r0 = act ? (t / nbc) * 4 : 0, c0 = act ? (t % nbc) * CW : 0;
 #pragma unroll 1
     for (int k = 0; k < P.nops; ++k) {
       const ResOp& op = prog[k];
-      float acc[4][4];
+      float acc[4][CW];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < CW; ++j) acc[i][j] = 0.f;
       if (op.gemm) {
         const float* L = sm + op.a * slot;
         const float* R = sm + op.b * slot;
@@ -111,9 +166,9 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
         const float sa = ldexpf(1.f, ea), sb = ldexpf(1.f, eb);
         if (act) {
           // k in steps of 4: the left operand as one 16-byte run of each of the
-          // block's 4 rows (at ld = 32 a warp's 4 row groups share one set of
-          // banks, so scalar loads of a column conflict 4 ways); the padding
-          // columns n .. ld-1 hold zeros and add nothing
+          // block's 4 rows (at ld = 32 a warp's row groups share one set of
+          // banks, so scalar loads of a column conflict); the padding columns
+          // n .. ld-1 hold zeros and add nothing
 #pragma unroll 1
           for (int q4 = 0; q4 < ld; q4 += 4) {
             float4 av[4];
@@ -121,31 +176,26 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
             for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(L + (r0 + i) * ld + q4);
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
-              float a[4], b[4];
+              float a[4], b[CW];
 #pragma unroll
               for (int i = 0; i < 4; ++i)
                 a[i] = qq == 0 ? av[i].x : qq == 1 ? av[i].y : qq == 2 ? av[i].z : av[i].w;
-              const float4 bv = *reinterpret_cast<const float4*>(R + (q4 + qq) * ld + c0);
-              b[0] = bv.x;
-              b[1] = bv.y;
-              b[2] = bv.z;
-              b[3] = bv.w;
+              ld_row<CW>(R + (q4 + qq) * ld + c0, b);
               if (MODE == 0) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                  for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                  for (int j = 0; j < CW; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
               } else {
-                float ah[4], al[4], bh[4], bl[4];
+                float ah[4], al[4], bh[CW], bl[CW];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                  res_split<MODE>(a[i], sa, &ah[i], &al[i]);
-                  res_split<MODE>(b[i], sb, &bh[i], &bl[i]);
-                }
+                for (int i = 0; i < 4; ++i) res_split<MODE>(a[i], sa, &ah[i], &al[i]);
+#pragma unroll
+                for (int j = 0; j < CW; ++j) res_split<MODE>(b[j], sb, &bh[j], &bl[j]);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                  for (int j = 0; j < 4; ++j)
+                  for (int j = 0; j < CW; ++j)
                     acc[i][j] = fmaf(al[i], bh[j], fmaf(ah[i], bl[j], fmaf(ah[i], bh[j], acc[i][j])));
               }
             }
@@ -155,7 +205,7 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-              for (int j = 0; j < 4; ++j) acc[i][j] *= inv;
+              for (int j = 0; j < CW; ++j) acc[i][j] *= inv;
           }
         }
       }
@@ -166,39 +216,33 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
         for (int ii = 0; ii < kMaxIn; ++ii)
           is64[ii] = ii < op.nin && (op.in_slot[ii] < 0 ? P.io_f64 != 0 : op.in_f64[ii] != 0);
 #pragma unroll 1
-        for (int i = 0; i < 4; ++i) {  // one row of the thread's block: 4 consecutive columns
+        for (int i = 0; i < 4; ++i) {  // one row of the thread's block: CW consecutive columns
           const int r = r0 + i;
           const int64_t e0 = (int64_t)r * ld + c0;
-          bool live[4];
+          bool live[CW];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) live[j] = r < n && c0 + j < n;
+          for (int j = 0; j < CW; ++j) live[j] = r < n && c0 + j < n;
           // every input load of the row before any output is formed
-          double vin[kMaxIn][4];
+          double vin[kMaxIn][CW];
 #pragma unroll
           for (int ii = 0; ii < kMaxIn; ++ii) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) vin[ii][j] = 0.0;
+            for (int j = 0; j < CW; ++j) vin[ii][j] = 0.0;
             if (ii < op.nin) {
               const int sl = op.in_slot[ii];
               if (sl < 0) {  // the caller's A, leading dimension n
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < CW; ++j)
                   if (live[j])
                     vin[ii][j] = P.io_f64 ? reinterpret_cast<const double*>(P.A[m])[(int64_t)r * n + c0 + j]
                                           : (double)reinterpret_cast<const float*>(P.A[m])[(int64_t)r * n + c0 + j];
               } else if (op.in_f64[ii]) {
-                const double2* q = reinterpret_cast<const double2*>(f64 + P.f64_of[sl] * slot + e0);
-                const double2 x = q[0], y = q[1];
-                vin[ii][0] = x.x;
-                vin[ii][1] = x.y;
-                vin[ii][2] = y.x;
-                vin[ii][3] = y.y;
+                ld_row<CW>(f64 + P.f64_of[sl] * slot + e0, vin[ii]);
               } else {
-                const float4 x = *reinterpret_cast<const float4*>(sm + sl * slot + e0);
-                vin[ii][0] = x.x;
-                vin[ii][1] = x.y;
-                vin[ii][2] = x.z;
-                vin[ii][3] = x.w;
+                float x[CW];
+                ld_row<CW>(sm + sl * slot + e0, x);
+#pragma unroll
+                for (int j = 0; j < CW; ++j) vin[ii][j] = x[j];
               }
             }
           }
@@ -207,10 +251,10 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
             const bool f64o = op.f64[o] != 0;
             const float af = op.acc_f[o], idf = op.id_f[o];
             const double idd = op.id_d[o];
-            float vf[4];
-            double v[4];
+            float vf[CW];
+            double v[CW];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < CW; ++j) {
               const bool diag = r == c0 + j;
               if (f64o) {
                 // FP32 terms in FP32, then the identity and the FP64 inputs in FP64
@@ -241,7 +285,7 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
             const int sl = op.out_slot[o];
             if (sl < 0) {  // the caller's S, leading dimension n: the n x n block only
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
+              for (int j = 0; j < CW; ++j) {
                 if (!live[j]) continue;
                 if (P.io_f64)
                   reinterpret_cast<double*>(P.S[m])[(int64_t)r * n + c0 + j] = v[j];
@@ -249,13 +293,8 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
                   reinterpret_cast<float*>(P.S[m])[(int64_t)r * n + c0 + j] = vf[j];
               }
             } else {  // padding stored as zeros
-              if (op.out_f32[o])
-                *reinterpret_cast<float4*>(sm + sl * slot + e0) = make_float4(vf[0], vf[1], vf[2], vf[3]);
-              if (op.out_f64[o]) {
-                double2* q = reinterpret_cast<double2*>(f64 + P.f64_of[sl] * slot + e0);
-                q[0] = make_double2(v[0], v[1]);
-                q[1] = make_double2(v[2], v[3]);
-              }
+              if (op.out_f32[o]) st_row<CW>(sm + sl * slot + e0, vf);
+              if (op.out_f64[o]) st_row<CW>(f64 + P.f64_of[sl] * slot + e0, v);
             }
           }
         }
@@ -274,10 +313,17 @@ cudaError_t launch_resident(const ResParams& P, cudaStream_t s) {
   const int threads = resident_threads(P.nmax);
   if (smem > (size_t)kResSmemBudget || threads > kResMaxThreads || P.mode < 0 || P.mode > 2)
     return cudaErrorInvalidValue;
-  static std::atomic<int> attr[3][kMaxDevices];
-  auto k = P.mode == 0 ? resident_kernel<0> : P.mode == 1 ? resident_kernel<1> : resident_kernel<2>;
-  cudaError_t e = once_per_device(
-      attr[P.mode], [&] { return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmemBudget); });
+  using K = void (*)(ResParams);
+  static const K kernels[3][3] = {{resident_kernel<0, 1>, resident_kernel<0, 2>, resident_kernel<0, 4>},
+                                  {resident_kernel<1, 1>, resident_kernel<1, 2>, resident_kernel<1, 4>},
+                                  {resident_kernel<2, 1>, resident_kernel<2, 2>, resident_kernel<2, 4>}};
+  const int cw = resident_cw(P.nmax);
+  const int ci = cw == 1 ? 0 : cw == 2 ? 1 : 2;
+  const K k = kernels[P.mode][ci];
+  static std::atomic<int> attr[3][3][kMaxDevices];
+  cudaError_t e = once_per_device(attr[P.mode][ci], [&] {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmemBudget);
+  });
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem)) != cudaSuccess) return e;
