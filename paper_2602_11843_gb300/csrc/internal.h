@@ -286,13 +286,15 @@ struct ResParams {
   unsigned* status;
 };
 // Shared memory of a CTA holding the program and nslots FP32 + nf64 FP64
-// matrices of order nmax.
-inline size_t resident_smem(int nslots, int nf64, int nops, int nmax) {
-  return (size_t)nmax * nmax * (4 * (size_t)nslots + 8 * (size_t)nf64) + (size_t)nops * sizeof(ResOp);
+// matrices of order nmax; split modes add the current product's two operands
+// as packed hi/lo words (4 bytes an element each).
+inline size_t resident_smem(int nslots, int nf64, int nops, int nmax, bool split = false) {
+  return (size_t)nmax * nmax * (4 * (size_t)nslots + 8 * (size_t)nf64 + (split ? 8 : 0)) +
+         (size_t)nops * sizeof(ResOp);
 }
 // Columns of a thread's output block for order nmax (its rows are 4): 1 up to
-// order 16, 2 up to 32, else 4.
-inline int resident_cw(int nmax) { return nmax <= 16 ? 1 : nmax <= 32 ? 2 : 4; }
+// order 16, else 2.
+inline int resident_cw(int nmax) { return nmax <= 16 ? 1 : 2; }
 // Threads of a CTA for order nmax: one per 4 x resident_cw output block,
 // rounded up to warps.
 inline int resident_threads(int nmax) {

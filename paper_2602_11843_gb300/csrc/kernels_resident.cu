@@ -11,16 +11,18 @@
 // CTA's shared memory: FP32 copies of all, FP64 copies of the partial sum and
 // residual, and the program itself. Only A is read from and S written to the
 // caller's memory. The host launches one grid per size class (orders up to 16,
-// 32, and the largest held), each with as many threads as 4 x 4 output blocks
-// and as many CTAs per SM as its shared memory allows.
+// 32, and the largest held), each with as many threads as 4 x 1 (up to order
+// 16) or 4 x 2 output blocks and as many CTAs per SM as its shared memory
+// allows.
 //
 // Products: at n <= 64 a product is at most 0.5 MFLOP and the work is a chain
 // of dependent steps, so a product is a register-blocked SIMT loop (each
-// thread a 4 x 4 block of the output) rather than a tensor-core launch. For a
-// split plan the operands are split as the tensor-core path stores them (hi =
-// RN16(x), lo = RN16(x - hi); FP16 of x * 2^e with e from the operand's exact
-// max |x|, the bound mapped to 2^14), and hi*hi + hi*lo + lo*hi is accumulated
-// in FP32. The epilogue is the same linear combination as epilogue.cuh's: FP32
+// thread a 4 x 1 or 4 x 2 block of the output) rather than a tensor-core
+// launch. For a split plan the operands are split once per product, as the
+// tensor-core path stores them (hi = RN16(x), lo = RN16(x - hi); FP16 of
+// x * 2^e with e from the operand's exact max |x|, the bound mapped to 2^14),
+// into packed words in shared memory, and hi*hi + hi*lo + lo*hi is
+// accumulated in FP32. The epilogue is the same linear combination as epilogue.cuh's: FP32
 // terms in FP32, then the identity and FP64 inputs in FP64, outputs' split
 // sources RN_fp32 of the value.
 #include <cuda_bf16.h>
@@ -32,7 +34,7 @@ namespace neumann {
 
 namespace {
 
-constexpr int kResMaxThreads = 256;  // 16 x 16 blocks of 4 x 4 outputs cover order 64
+constexpr int kResMaxThreads = 512;  // 16 x 32 blocks of 4 x 2 outputs cover order 64
 
 // hi + lo of x in the mode's 16-bit type (mode 2: of x * sc)
 template <int MODE>
@@ -46,6 +48,29 @@ __device__ __forceinline__ void res_split(float x, float sc, float* hi, float* l
     const float h = __half2float(__float2half_rn(w));
     *hi = h;
     *lo = __half2float(__float2half_rn(w - h));
+  }
+}
+
+// The pair as one word: hi in the upper 16 bits, lo in the lower (the 16-bit
+// type's bits). Unpacking a BF16 pair is two bit operations, where splitting
+// takes conversions on the XU pipe (16 lanes per clock per SM).
+template <int MODE>
+__device__ __forceinline__ uint32_t res_pack(float x, float sc) {
+  float h, l;
+  res_split<MODE>(x, sc, &h, &l);
+  if (MODE == 1)
+    return ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(h)) << 16) |
+           (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(l));
+  return ((uint32_t)__half_as_ushort(__float2half_rn(h)) << 16) | (uint32_t)__half_as_ushort(__float2half_rn(l));
+}
+template <int MODE>
+__device__ __forceinline__ void res_unpack(uint32_t w, float* hi, float* lo) {
+  if (MODE == 1) {
+    *hi = __uint_as_float(w & 0xffff0000u);
+    *lo = __uint_as_float(w << 16);
+  } else {
+    *hi = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+    *lo = __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
   }
 }
 
@@ -122,21 +147,24 @@ __device__ __forceinline__ void st_row(double* p, const double (&v)[CW]) {
   }
 }
 
-// Each thread holds a 4 x CW block of every output: CW = 4 for the largest
-// size class, 2 for orders up to 32 and 1 up to 16, so that a CTA runs 64-256
-// threads whatever the order (with 4 x 4 blocks an order-32 matrix had 64
-// threads, and the SM, at 3 CTAs for its shared memory, 6 warps: too few to
-// cover the latency of one matrix's chain of dependent steps).
+// Each thread holds a 4 x CW block of every output: CW = 1 up to order 16, else
+// 2, so that a CTA runs 64-512 threads (with 4 x 4 blocks an order-32 matrix
+// had 64 threads, and the SM, at 3 CTAs for its shared memory, 6 warps; an
+// order-48 matrix 144 threads at 1 CTA: too few to cover the latency of one
+// matrix's chain of dependent steps).
 template <int MODE, int CW>
 __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_constant__ ResParams P) {
-  // shared memory: FP64 copies | FP32 copies | program (16-byte aligned sections)
+  // shared memory: FP64 copies | FP32 copies | packed operands (split modes) |
+  // program (16-byte aligned sections)
   extern __shared__ __align__(16) double smd[];
   __shared__ float red[kResMaxThreads / 32];
   const int t = threadIdx.x;
   const size_t slot = (size_t)P.nmax * P.nmax;
   double* f64 = smd;
   float* sm = reinterpret_cast<float*>(smd + (size_t)P.nf64 * slot);
-  ResOp* prog = reinterpret_cast<ResOp*>(sm + (size_t)P.nslots * slot);
+  // split modes: the current product's operands as packed hi/lo words (2 slots)
+  uint32_t* pk = reinterpret_cast<uint32_t*>(sm + (size_t)P.nslots * slot);
+  ResOp* prog = reinterpret_cast<ResOp*>(pk + (MODE != 0 ? 2 * slot : 0));
   for (int w = t; w < (int)(P.nops * sizeof(ResOp) / sizeof(int)); w += blockDim.x)
     reinterpret_cast<int*>(prog)[w] = reinterpret_cast<const int*>(P.ops)[w];
   __syncthreads();
@@ -164,6 +192,16 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
           eb = res_exp(res_block_amax(R, n, ld, red));
         }
         const float sa = ldexpf(1.f, ea), sb = ldexpf(1.f, eb);
+        if (MODE != 0) {
+          // split each operand element once, into the two packed slots, not
+          // once for every thread that reads it: done in the product loop, the
+          // conversions (one per three FMAs) bound the largest size class
+          for (int e = t; e < ld * ld; e += blockDim.x) {
+            pk[e] = res_pack<MODE>(L[e], sa);
+            pk[slot + e] = res_pack<MODE>(R[e], sb);
+          }
+          __syncthreads();
+        }
         if (act) {
           // k in steps of 4: the left operand as one 16-byte run of each of the
           // block's 4 rows (at ld = 32 a warp's row groups share one set of
@@ -171,27 +209,33 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
           // n .. ld-1 hold zeros and add nothing
 #pragma unroll 1
           for (int q4 = 0; q4 < ld; q4 += 4) {
-            float4 av[4];
+            if (MODE == 0) {
+              float4 av[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(L + (r0 + i) * ld + q4);
+              for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4*>(L + (r0 + i) * ld + q4);
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-              float a[4], b[CW];
+              for (int qq = 0; qq < 4; ++qq) {
+                float b[CW];
+                ld_row<CW>(R + (q4 + qq) * ld + c0, b);
 #pragma unroll
-              for (int i = 0; i < 4; ++i)
-                a[i] = qq == 0 ? av[i].x : qq == 1 ? av[i].y : qq == 2 ? av[i].z : av[i].w;
-              ld_row<CW>(R + (q4 + qq) * ld + c0, b);
-              if (MODE == 0) {
+                for (int i = 0; i < 4; ++i) {
+                  const float a = qq == 0 ? av[i].x : qq == 1 ? av[i].y : qq == 2 ? av[i].z : av[i].w;
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                  for (int j = 0; j < CW; ++j) acc[i][j] = fmaf(a, b[j], acc[i][j]);
+                }
+              }
+            } else {
+              uint4 aw[4];
 #pragma unroll
-                  for (int j = 0; j < CW; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-              } else {
+              for (int i = 0; i < 4; ++i) aw[i] = *reinterpret_cast<const uint4*>(pk + (r0 + i) * ld + q4);
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
                 float ah[4], al[4], bh[CW], bl[CW];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) res_split<MODE>(a[i], sa, &ah[i], &al[i]);
+                for (int i = 0; i < 4; ++i)
+                  res_unpack<MODE>(qq == 0 ? aw[i].x : qq == 1 ? aw[i].y : qq == 2 ? aw[i].z : aw[i].w, &ah[i], &al[i]);
 #pragma unroll
-                for (int j = 0; j < CW; ++j) res_split<MODE>(b[j], sb, &bh[j], &bl[j]);
+                for (int j = 0; j < CW; ++j) res_unpack<MODE>(pk[slot + (q4 + qq) * ld + c0 + j], &bh[j], &bl[j]);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -309,18 +353,17 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
 
 cudaError_t launch_resident(const ResParams& P, cudaStream_t s) {
   if (P.count <= 0) return cudaSuccess;
-  const size_t smem = resident_smem(P.nslots, P.nf64, P.nops, P.nmax);
+  const size_t smem = resident_smem(P.nslots, P.nf64, P.nops, P.nmax, P.mode != 0);
   const int threads = resident_threads(P.nmax);
   if (smem > (size_t)kResSmemBudget || threads > kResMaxThreads || P.mode < 0 || P.mode > 2)
     return cudaErrorInvalidValue;
   using K = void (*)(ResParams);
-  static const K kernels[3][3] = {{resident_kernel<0, 1>, resident_kernel<0, 2>, resident_kernel<0, 4>},
-                                  {resident_kernel<1, 1>, resident_kernel<1, 2>, resident_kernel<1, 4>},
-                                  {resident_kernel<2, 1>, resident_kernel<2, 2>, resident_kernel<2, 4>}};
-  const int cw = resident_cw(P.nmax);
-  const int ci = cw == 1 ? 0 : cw == 2 ? 1 : 2;
+  static const K kernels[3][2] = {{resident_kernel<0, 1>, resident_kernel<0, 2>},
+                                  {resident_kernel<1, 1>, resident_kernel<1, 2>},
+                                  {resident_kernel<2, 1>, resident_kernel<2, 2>}};
+  const int ci = resident_cw(P.nmax) == 1 ? 0 : 1;
   const K k = kernels[P.mode][ci];
-  static std::atomic<int> attr[3][3][kMaxDevices];
+  static std::atomic<int> attr[3][2][kMaxDevices];
   cudaError_t e = once_per_device(attr[P.mode][ci], [&] {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmemBudget);
   });

@@ -781,7 +781,8 @@ void build_resident(neumann_plan_s* p) {
   }
   const int nops = (int)p->ops.size();
   int m = kResMaxN;
-  while (m >= 16 && resident_smem(p->res_nslots, p->res_nf64, nops, m) > (size_t)kResSmemBudget) m -= 4;
+  while (m >= 16 && resident_smem(p->res_nslots, p->res_nf64, nops, m, p->path != PATH_F32) > (size_t)kResSmemBudget)
+    m -= 4;
   if (m < 16) return;
   p->res_maxn = m;
   // untuned: up to 48. Measured on the damped Jacobi batch (k = 81, 1024 matrices
