@@ -407,7 +407,10 @@ def run_reference(args, wl):
         "config": {"workload": args.workload, "n": wl["n"], "k": wl["k"], "radix": wl["radix"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"each step: one radix-{wl['radix']} kernel ({info_products} products) at "
-                                   f"n={wl['n']}, scaled to a full evaluation ({calg.products} products)"},
+                                   f"n={wl['n']}, scaled to a full evaluation ({calg.products} products)",
+                         "extrapolated": f"{info_products} of {calg.products} products timed, scaled to "
+                                         f"{calg.products}"},
+        "extrapolated": f"{info_products} of {calg.products} products timed per step, scaled to {calg.products}",
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
