@@ -60,3 +60,18 @@ def test_traffic_key_ignores_comments_only():
     other = "int f(int x) {\n  return 3 * x;\n}\n"
     assert b._code_only(code) == b._code_only(same)
     assert b._code_only(code) != b._code_only(other)
+
+
+def test_vs_fp32_compares_each_split_form_with_the_fp32_path():
+    """The default line's FP32 comparison: speedups over the plain FP32 path and
+    each form's error against the oracle, from the extras' own keys."""
+    b = _bench()
+    assert b.vs_fp32({"value": 30.0}) is None  # no FP32 extra (--no-extras)
+    line = {"value": 30.0, "vs_oracle": {"rel_fro": 1e-3},
+            "precise": {"value": 20.0, "vs_oracle": {"rel_fro": 8e-5}},
+            "fp32": {"value": 3.0, "vs_oracle": {"rel_fro": 5e-6}}}
+    v = b.vs_fp32(line)
+    assert v["speedup_split"] == 10.0 and v["speedup_precise"] == 20.0 / 3.0
+    assert (v["split_rel_fro"], v["precise_rel_fro"], v["fp32_rel_fro"]) == (1e-3, 8e-5, 5e-6)
+    assert any(name == "plain-r15-fp32-n8192-k3375" for _, name, _ in b.EXTRAS)
+    assert b.WORKLOADS["plain-r15-fp32-n8192-k3375"]["n"] == b.WORKLOADS[b.DEFAULT_WORKLOAD]["n"]
