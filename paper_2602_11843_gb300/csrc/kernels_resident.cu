@@ -266,27 +266,35 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
           bool live[CW];
 #pragma unroll
           for (int j = 0; j < CW; ++j) live[j] = r < n && c0 + j < n;
-          // every input load of the row before any output is formed
-          double vin[kMaxIn][CW];
+          // every input load of the row before any output is formed: FP32
+          // inputs stay in FP32 registers, FP64 inputs in FP64 ones (GB300
+          // converts between the two on its FP64 pipe, at 1/64 of the FP32
+          // rate; with the operand splits out of the product loop those
+          // conversions were the binding unit)
+          float vf32[kMaxIn][CW];
+          double vf64[kMaxIn][CW];
 #pragma unroll
           for (int ii = 0; ii < kMaxIn; ++ii) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) vin[ii][j] = 0.0;
+            for (int j = 0; j < CW; ++j) {
+              vf32[ii][j] = 0.f;
+              vf64[ii][j] = 0.0;
+            }
             if (ii < op.nin) {
               const int sl = op.in_slot[ii];
               if (sl < 0) {  // the caller's A, leading dimension n
 #pragma unroll
                 for (int j = 0; j < CW; ++j)
-                  if (live[j])
-                    vin[ii][j] = P.io_f64 ? reinterpret_cast<const double*>(P.A[m])[(int64_t)r * n + c0 + j]
-                                          : (double)reinterpret_cast<const float*>(P.A[m])[(int64_t)r * n + c0 + j];
+                  if (live[j]) {
+                    if (P.io_f64)
+                      vf64[ii][j] = reinterpret_cast<const double*>(P.A[m])[(int64_t)r * n + c0 + j];
+                    else
+                      vf32[ii][j] = reinterpret_cast<const float*>(P.A[m])[(int64_t)r * n + c0 + j];
+                  }
               } else if (op.in_f64[ii]) {
-                ld_row<CW>(f64 + P.f64_of[sl] * slot + e0, vin[ii]);
+                ld_row<CW>(f64 + P.f64_of[sl] * slot + e0, vf64[ii]);
               } else {
-                float x[CW];
-                ld_row<CW>(sm + sl * slot + e0, x);
-#pragma unroll
-                for (int j = 0; j < CW; ++j) vin[ii][j] = x[j];
+                ld_row<CW>(sm + sl * slot + e0, vf32[ii]);
               }
             }
           }
@@ -305,14 +313,14 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
                 float tt = af * acc[i][j];
 #pragma unroll
                 for (int ii = 0; ii < kMaxIn; ++ii)
-                  if (ii < op.nin && !is64[ii] && op.in_f[o][ii] != 0.f) tt = fmaf(op.in_f[o][ii], (float)vin[ii][j], tt);
+                  if (ii < op.nin && !is64[ii] && op.in_f[o][ii] != 0.f) tt = fmaf(op.in_f[o][ii], vf32[ii][j], tt);
                 // (FP64 runs at 1/64 of FP32: the identity is added on the
                 // diagonal only, and finiteness is read from the FP32 copy)
                 double d = (double)tt;
                 if (diag) d += idd;
 #pragma unroll
                 for (int ii = 0; ii < kMaxIn; ++ii)
-                  if (ii < op.nin && is64[ii] && op.in_d[o][ii] != 0.0) d = fma(op.in_d[o][ii], vin[ii][j], d);
+                  if (ii < op.nin && is64[ii] && op.in_d[o][ii] != 0.0) d = fma(op.in_d[o][ii], vf64[ii][j], d);
                 v[j] = live[j] ? d : 0.0;
                 vf[j] = (float)v[j];
                 bad |= !isfinite(vf[j]);
@@ -320,13 +328,17 @@ __global__ void __launch_bounds__(kResMaxThreads) resident_kernel(const __grid_c
                 float t2 = af * acc[i][j] + (diag ? idf : 0.f);
 #pragma unroll
                 for (int ii = 0; ii < kMaxIn; ++ii)
-                  if (ii < op.nin && op.in_f[o][ii] != 0.f) t2 = fmaf(op.in_f[o][ii], (float)vin[ii][j], t2);
+                  if (ii < op.nin && op.in_f[o][ii] != 0.f)
+                    t2 = fmaf(op.in_f[o][ii], is64[ii] ? (float)vf64[ii][j] : vf32[ii][j], t2);
                 vf[j] = live[j] ? t2 : 0.f;
-                v[j] = (double)vf[j];
                 bad |= !isfinite(t2);
               }
             }
             const int sl = op.out_slot[o];
+            if (!f64o && ((sl < 0 && P.io_f64) || (sl >= 0 && op.out_f64[o]))) {  // an FP64 copy of an FP32 value
+#pragma unroll
+              for (int j = 0; j < CW; ++j) v[j] = (double)vf[j];
+            }
             if (sl < 0) {  // the caller's S, leading dimension n: the n x n block only
 #pragma unroll
               for (int j = 0; j < CW; ++j) {
